@@ -1,0 +1,234 @@
+/*
+ * ptrace.h -- C ABI of the GB300 library for the displacement-probed
+ * estimator of Tr(P A^{-1}) on 4D toroidal lattices.
+ *
+ * Method: Switzer, Stathopoulos, Romero, Laeuchli, Orginos, "Probing for the
+ * trace estimation of a permuted matrix inverse corresponding to a lattice
+ * displacement" (arXiv 2106.01275).  Each entry point cites the passage
+ * that defines the operation it performs.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Return value: PT_OK (0) or a negative PT_ERR_* code.  After an error,
+ *   pt_last_error() returns a one-line message (thread-local).
+ * - Lattice: dims[4] = (D_0, D_1, D_2, D_3) = (x, y, z, t).  Sites are stored
+ *   in the order idx = x_0 + D_0 (x_1 + D_1 (x_2 + D_2 x_3)), x_0 fastest;
+ *   N = D_0 D_1 D_2 D_3.  Every D_i >= 1 (the kernels take any size, no
+ *   power-of-two or tile-multiple requirement).
+ * - Displacement (Sec. 3): P is the permutation (P f)(x) = f(x + p e_mu) with
+ *   periodic wrap and no boundary sign, so Tr(P A^{-1}) = sum_x A^{-1}(x+p, x).
+ * - Fields in the ABI layout ("user layout"), all on the device:
+ *     scalar (Laplacian, dof 1): float64 [nrhs][N]
+ *     spinor (Wilson, dof 12):   complex128 [nrhs][N][4 spin][3 colour],
+ *                                interleaved (re, im); component a = 3 spin + colour
+ *     links:                     complex128 [N][4 mu][3][3] (row, column)
+ * - Ownership: the caller allocates and frees every buffer whose pointer it
+ *   passes.  A context owns its work space (device memory, streams, graphs);
+ *   an operator owns its packed copy of the links.  Pointers marked "host"
+ *   are host memory; all others are device memory of the context's device.
+ * - Streams: work is enqueued on the context's stream.  Entry points that
+ *   return host results synchronise that stream before returning; the others
+ *   are asynchronous with respect to the host.
+ * - Contexts are not thread-safe: one host thread per context at a time.
+ */
+#ifndef PTRACE_H
+#define PTRACE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PT_API __attribute__((visibility("default")))
+#else
+#define PT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define PT_OK            0
+#define PT_ERR_ARG      (-1)  /* invalid argument (size, pointer, mode)            */
+#define PT_ERR_CUDA     (-2)  /* a CUDA runtime call failed                        */
+#define PT_ERR_NOCONV   (-3)  /* a solve did not reach tol within maxit            */
+#define PT_ERR_TIMEOUT  (-4)  /* a bounded device wait or host loop gave up        */
+#define PT_ERR_NUMERIC  (-5)  /* NaN/Inf or a Krylov breakdown (zero denominator)  */
+#define PT_ERR_OOM      (-6)  /* device allocation of the work space failed        */
+
+/* ---- precision modes of the solver (BASELINE precision form) ---- */
+#define PT_PREC_FP64        0 /* all vectors and arithmetic FP64                     */
+#define PT_PREC_MIXED_FP32  1 /* FP32 inner Krylov inside FP64 defect correction      */
+#define PT_PREC_MIXED_BF16  2 /* as MIXED_FP32, inner vectors stored in BF16          */
+
+/* ---- noise and visit orders ---- */
+#define PT_NOISE_Z2        0  /* +-1            (Sec. 1, Rademacher)                 */
+#define PT_NOISE_Z4        1  /* +-1, +-i       (Sec. 1, complex case)               */
+#define PT_ORDER_NATURAL   0  /* storage order (Sec. 3.1)                            */
+#define PT_ORDER_REDBLACK  1  /* even-parity sites, then odd, each in storage order   */
+
+typedef struct pt_ctx pt_ctx;
+typedef struct pt_op pt_op;
+
+/* Solver statistics of one pt_solve / pt_trace_PAinv / pt_grad call. */
+typedef struct pt_stats {
+    int64_t n_rhs;            /* right-hand sides solved                                 */
+    int64_t inner_iters;      /* Krylov iterations summed over right-hand sides          */
+    int64_t outer_iters;      /* FP64 true-residual evaluations summed over RHS          */
+    int64_t site_rhs_applies; /* operator applications x sites, summed over RHS          */
+    int64_t engine_iters;     /* batched engine iterations (each = one graph body)       */
+    int64_t graph_launches;   /* CUDA graph launches                                    */
+    int64_t kernel_launches;  /* kernels launched by the library in this call           */
+    double  max_relres;       /* largest final FP64 true relative residual               */
+    int32_t n_slots;          /* right-hand sides resident at once                      */
+    int32_t n_noconv;         /* right-hand sides that hit maxit                         */
+} pt_stats;
+
+/* ------------------------------------------------------------------ context */
+
+/* Library version (major*10000 + minor*100 + patch). */
+PT_API int pt_version(void);
+
+/* Copy the calling thread's last error message into buf (always NUL-terminated). */
+PT_API int pt_last_error(char *buf, size_t n);
+
+/* Create a context on CUDA device `device`.  `stream` is a cudaStream_t to
+ * enqueue on, or NULL for a library-owned non-blocking stream (to use the
+ * legacy default stream pass cudaStreamLegacy, i.e. (void *)0x1).  *ctx
+ * receives the handle (NULL on failure). */
+PT_API int pt_create(pt_ctx **ctx, int device, void *stream);
+
+/* Release the context, its work space, graphs and (if owned) stream. */
+PT_API int pt_destroy(pt_ctx *ctx);
+
+/* Block until all work enqueued by the context has finished. */
+PT_API int pt_synchronize(pt_ctx *ctx);
+
+/* Cap on the device bytes the solver engine may hold for resident
+ * right-hand sides (default 16 GiB).  Larger budgets keep more RHS in flight. */
+PT_API int pt_set_memory_budget(pt_ctx *ctx, size_t bytes);
+
+/* Enable (1) or disable (0) per-kernel CUDA-event timing inside the engine.
+ * pt_profile_read returns, for the kernel class `which` (0 = the operator
+ * apply of the inner Krylov iteration), the launches and the summed
+ * device milliseconds since the last reset. */
+PT_API int pt_profile_enable(pt_ctx *ctx, int on);
+PT_API int pt_profile_read(pt_ctx *ctx, int which, int64_t *launches, double *ms, int reset);
+
+/* ---------------------------------------------------------------- operators */
+
+/* Shifted scalar Laplacian, periodic in all four dimensions:
+ *   (A f)(x) = (8 + m2) f(x) - sum_mu [ f(x + mu) + f(x - mu) ].
+ * The paper abstracts its operator to a non-singular lattice matrix (Sec. 2);
+ * this is the scalar instance used for its Fig. 1 and Fig. 2 examples. */
+PT_API int pt_op_laplacian(pt_ctx *ctx, const int dims[4], double m2, pt_op **op);
+
+/* Wilson-Dirac operator (the LQCD operator family of Sec. 4.2, without the
+ * clover term):
+ *   (A psi)(x) = psi(x) - kappa sum_mu [ (1 - g_mu) U_mu(x) psi(x + mu) eta
+ *                                       + (1 + g_mu) U_mu(x - mu)^+ psi(x - mu) eta ]
+ * chiral Euclidean gamma basis g_k = [[0, -i s_k], [i s_k, 0]], g_4 = [[0,1],[1,0]];
+ * eta = -1 on hops across the t boundary when antiperiodic_t, else +1.
+ * U_dev: links in the user layout (device, read once; the operator keeps a
+ * packed FP64 and FP32 copy, so the caller may free U_dev afterwards). */
+PT_API int pt_op_wilson(pt_ctx *ctx, const int dims[4], const double *U_dev, double kappa,
+                 int antiperiodic_t, pt_op **op);
+
+/* Degrees of freedom per site of the operator (1 or 12), or a negative error. */
+PT_API int pt_op_dof(const pt_op *op);
+
+PT_API int pt_op_destroy(pt_op *op);
+
+/* y = A x for nrhs fields in the user layout (device).  prec: PT_PREC_FP64
+ * applies in FP64; PT_PREC_MIXED_FP32 rounds x to FP32, applies the FP32
+ * kernel of the inner solver and widens the result; PT_PREC_MIXED_BF16 rounds
+ * x to BF16 storage first.  x and y must not overlap. */
+PT_API int pt_apply(pt_ctx *ctx, const pt_op *op, const double *x_dev, double *y_dev, int nrhs, int prec);
+
+/* ---------------------------------------------------------------- colouring */
+
+/* Host-side stencil of the displaced distance-k neighbourhood (Eq. (9), and
+ * the union over several displacements of Sec. 3.4):
+ *   O = { o != 0 : ||o - p_n e_mu||_1 <= k  or  ||o + p_n e_mu||_1 <= k, some n }
+ * sorted lexicographically in (o_0, o_1, o_2, o_3).  offsets_out (host) receives
+ * up to max_offsets rows of 4 ints; *n_offsets the full count.  Returns
+ * PT_ERR_ARG if max_offsets is too small (after writing *n_offsets). */
+PT_API int pt_stencil(int mu, const int *p_list, int n_p, int k, int *offsets_out, int max_offsets,
+               int *n_offsets);
+
+/* Greedy displaced distance-k colouring (Algorithm 1, Sec. 3.1): nodes are
+ * visited in `order`; each takes the smallest colour (0-based) not held by an
+ * already coloured node of N(x, p, k) (x itself excluded).  Bit-exact with the
+ * sequential definition.  col_dev: int32 [N] (device, written); *n_colours
+ * (host) receives m.  Synchronises the context stream. */
+PT_API int pt_colour(pt_ctx *ctx, const int dims[4], int mu, const int *p_list, int n_p, int k,
+              int order, int32_t *col_dev, int *n_colours);
+
+/* Count ordered pairs (x, y), y in N(x,p,k), y != x, with equal colours: zero
+ * for a valid colouring (Sec. 3.1).  *n_conflicts is host.  Synchronises. */
+PT_API int pt_colour_conflicts(pt_ctx *ctx, const int dims[4], int mu, const int *p_list, int n_p,
+                        int k, const int32_t *col_dev, int64_t *n_conflicts);
+
+/* ------------------------------------------------------------------- probes */
+
+/* Materialise one probing vector (Eq. (3) with the noise of Eq. (5) and the
+ * spin-colour dilution of Sec. 4.2):
+ *   v(x, b) = z0_set(x) [col(x) = colour] delta_{b, component}
+ * z0 from SplitMix64: h = mix64(key + (x+1) G), key = mix64(seed + (set+1) G),
+ * G = 0x9E3779B97F4A7C15; Z2: 1 - 2 (h >> 63); Z4: i^(h >> 62).
+ * dof 1 -> v_dev float64 [N] (Z2 only); dof 12 -> complex128 [N][12].
+ * The solver regenerates probes in-kernel; this call exists for checks. */
+PT_API int pt_make_probes(pt_ctx *ctx, const int32_t *col_dev, int64_t N, int colour, int noise,
+                   uint64_t seed, int set, int dof, int component, double *v_dev);
+
+/* ------------------------------------------------------------------ solves */
+
+/* Solve A X = B for nrhs right-hand sides in the user layout (device; X is
+ * written, initial guess zero).  Stops each RHS when its FP64 true relative
+ * residual ||b - A x|| / ||b|| < tol.  Laplacian: CG; Wilson: BiCGStab.
+ * Mixed modes run the Krylov iteration in FP32 (or BF16 storage) inside an
+ * FP64 defect-correction loop.  iters_out / relres_out: host arrays [nrhs]
+ * or NULL.  stats: host or NULL.  Returns PT_ERR_NOCONV if any RHS hit maxit
+ * (X still holds its last iterate).  Synchronises. */
+PT_API int pt_solve(pt_ctx *ctx, const pt_op *op, const double *B_dev, double *X_dev, int nrhs,
+             int prec, double tol, int maxit, int *iters_out, double *relres_out, pt_stats *stats);
+
+/* ------------------------------------------------------------------ traces */
+
+/* Probed estimates of Tr(P_n A^{-1}) for every displacement p_list[n] along mu
+ * (Eqs. (1), (3), (5), spin-colour dilution of Sec. 4.2):
+ *   est[s][n] = sum_{c < n_colours} sum_{a} v_{s,c,a}^H P_{p_n} A^{-1} v_{s,c,a}
+ * for noise sets s = set0 .. set0 + n_sets - 1, a over all dof components when
+ * dilute != 0, else a = 0 only.  col_dev: int32 [N] colours in [0, n_colours)
+ * (all zero gives the unprobed Hutchinson estimator).  Every probe of every set
+ * is queued into one batched, graph-driven solve; converged RHS retire on the
+ * device and their slot is refilled from the queue.  Accumulation in FP64.
+ * est_out: host complex128 [n_sets][n_p]; mean_out: host complex128 [n_p] or
+ * NULL; var_out: host float64 [n_p] or NULL, the sample variance over sets
+ * (denominator n_sets - 1; zero when n_sets == 1).  Synchronises. */
+PT_API int pt_trace_PAinv(pt_ctx *ctx, const pt_op *op, const int32_t *col_dev, int n_colours, int mu,
+                   const int *p_list, int n_p, int noise, uint64_t seed, int set0, int n_sets,
+                   int dilute, int prec, double tol, int maxit, double *est_out,
+                   double *mean_out, double *var_out, pt_stats *stats);
+
+/* Adjoint gradient of the probed estimate T = sum_s est[s] for one
+ * displacement p (not in the paper): with x = A^{-1} v, y = A^{-+} P^T v,
+ *   dT/dtheta = - sum_v y^H (dA/dtheta) x.
+ * Laplacian: *dparam_out = dT/dm2 (complex128, host).  Wilson: dT/dkappa, and,
+ * if G_dev / Gbar_dev are not NULL, the link derivatives (user link layout,
+ * device, overwritten)
+ *   G_mu(x)_ab    = dT/dU_mu(x)_ab,   Gbar_mu(x)_ab = dT/d conj(U_mu(x)_ab)
+ * (entries of U treated as free complex numbers).  Forward and adjoint solves
+ * are recomputed (no Krylov history is stored); the adjoint solve uses
+ * A^{-+} = g5 A^{-1} g5.  est_out: host complex128 [n_sets] or NULL.
+ * Synchronises. */
+PT_API int pt_grad(pt_ctx *ctx, const pt_op *op, const int32_t *col_dev, int n_colours, int mu, int p,
+            int noise, uint64_t seed, int set0, int n_sets, int dilute, int prec, double tol,
+            int maxit, double *est_out, double *dparam_out, double *G_dev, double *Gbar_dev,
+            pt_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTRACE_H */

@@ -71,12 +71,13 @@ class Wilson:
 def probed_estimates(op, col, m, seed, n_sets, kind, mu, p_list, tol, dilute=True, set0=0):
     """est[s, n] = sum_{c, a} v_{s,c,a}^H P_{p_n} A^{-1} v_{s,c,a}  (Eqs. (1), (5)).
 
-    `dilute`: True -> all `op.dof` components (Kronecker product with the
-    identity, Sec. 4.2); the scalar Laplacian has dof = 1 either way.
+    `dilute`: True -> one probe per component a (Kronecker product with the
+    identity, Sec. 4.2); False -> one probe per colour with independent noise
+    in every component.  The scalar Laplacian has dof = 1 either way.
     Returns a complex128 array [n_sets, n_p].
     """
     dims = op.dims
-    comps = range(op.dof) if dilute else [0]
+    comps = range(op.dof) if dilute else [None]
     est = np.zeros((n_sets, len(p_list)), dtype=np.complex128)
     for s in range(n_sets):
         for c in range(m):

@@ -26,7 +26,7 @@ from .probes import probe
 
 def _probe_pairs(op, col, m, seed, n_sets, kind, mu, p, tol, dilute=True):
     """Yield (v, x, y) for every probe: x = A^{-1} v, y = A^{-dagger} P^T v."""
-    comps = range(op.dof) if dilute else [0]
+    comps = range(op.dof) if dilute else [None]
     for s in range(n_sets):
         for c in range(m):
             for a in comps:

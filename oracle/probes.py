@@ -16,13 +16,22 @@ from .rng import noise
 
 
 def probe(col, colour, seed, s, kind, dof=1, component=0):
-    """v_{s,c,a}(x, b) = z0_s(x) [col(x) = c] delta_{a b}."""
+    """Diluted (component = a): v_{s,c,a}(x, b) = z0_s(x) [col(x) = c] delta_{a b}.
+
+    Undiluted (component = None): every component of a site of colour c gets
+    its own noise value, the one of counter dof * x + b, so that the estimate
+    has no bias from the off-diagonal spin-colour entries of a site.
+    """
     col = np.asarray(col)
     N = col.shape[0]
-    z0 = noise(seed, s, N, kind)
     v = np.zeros((N, dof), dtype=np.complex128 if kind == 1 else np.float64)
     mask = col == colour
-    v[mask, component] = z0[mask]
+    if component is None:
+        z = noise(seed, s, N * dof, kind).reshape(N, dof)
+        v[mask, :] = z[mask, :]
+    else:
+        z0 = noise(seed, s, N, kind)
+        v[mask, component] = z0[mask]
     return v
 
 

@@ -1,0 +1,338 @@
+"""Thin ctypes binding of libptrace (include/ptrace.h).
+
+Argument marshalling only: every step of the estimator runs in the CUDA
+library.  PyTorch provides device memory and the stream.  There is no CPU
+fallback: if the library is missing or no GPU is present the calls raise.
+Field layouts are those of the C ABI (see include/ptrace.h):
+  scalar fields  torch.float64    [nrhs, N]
+  spinor fields  torch.complex128 [nrhs, N, 4, 3]
+  links          torch.complex128 [N, 4, 3, 3]
+"""
+import atexit
+import ctypes
+import os
+import sys
+import weakref
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libptrace.so")
+
+PT_OK, PT_ERR_ARG, PT_ERR_CUDA, PT_ERR_NOCONV, PT_ERR_TIMEOUT, PT_ERR_NUMERIC, PT_ERR_OOM = 0, -1, -2, -3, -4, -5, -6
+PREC = {"fp64": 0, "mixed_fp32": 1, "mixed_bf16": 2}
+NOISE = {"z2": 0, "z4": 1}
+ORDER = {"natural": 0, "redblack": 1}
+_ERRNAMES = {-1: "PT_ERR_ARG", -2: "PT_ERR_CUDA", -3: "PT_ERR_NOCONV", -4: "PT_ERR_TIMEOUT",
+             -5: "PT_ERR_NUMERIC", -6: "PT_ERR_OOM"}
+
+
+class PtraceError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (_ERRNAMES.get(code, str(code)), msg))
+        self.code = code
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_rhs", ctypes.c_int64), ("inner_iters", ctypes.c_int64), ("outer_iters", ctypes.c_int64),
+                ("site_rhs_applies", ctypes.c_int64), ("engine_iters", ctypes.c_int64),
+                ("graph_launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("max_relres", ctypes.c_double), ("n_slots", ctypes.c_int32), ("n_noconv", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SIGS = {
+    "pt_version": ([], _I),
+    "pt_last_error": ([ctypes.c_char_p, ctypes.c_size_t], _I),
+    "pt_create": ([ctypes.POINTER(_P), _I, _P], _I),
+    "pt_destroy": ([_P], _I),
+    "pt_synchronize": ([_P], _I),
+    "pt_set_memory_budget": ([_P, ctypes.c_size_t], _I),
+    "pt_profile_enable": ([_P, _I], _I),
+    "pt_profile_read": ([_P, _I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_D), _I], _I),
+    "pt_op_laplacian": ([_P, ctypes.POINTER(_I), _D, ctypes.POINTER(_P)], _I),
+    "pt_op_wilson": ([_P, ctypes.POINTER(_I), _P, _D, _I, ctypes.POINTER(_P)], _I),
+    "pt_op_dof": ([_P], _I),
+    "pt_op_destroy": ([_P], _I),
+    "pt_apply": ([_P, _P, _P, _P, _I, _I], _I),
+    "pt_stencil": ([_I, ctypes.POINTER(_I), _I, _I, ctypes.POINTER(_I), _I, ctypes.POINTER(_I)], _I),
+    "pt_colour": ([_P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _I, _I, _I, _P, ctypes.POINTER(_I)], _I),
+    "pt_colour_conflicts": ([_P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _I, _I, _P,
+                             ctypes.POINTER(ctypes.c_int64)], _I),
+    "pt_make_probes": ([_P, _P, ctypes.c_int64, _I, _I, ctypes.c_uint64, _I, _I, _I, _P], _I),
+    "pt_solve": ([_P, _P, _P, _P, _I, _I, _D, _I, _P, _P, ctypes.POINTER(Stats)], _I),
+    "pt_trace_PAinv": ([_P, _P, _P, _I, _I, ctypes.POINTER(_I), _I, _I, ctypes.c_uint64, _I, _I, _I, _I, _D, _I,
+                        _P, _P, _P, ctypes.POINTER(Stats)], _I),
+    "pt_grad": ([_P, _P, _P, _I, _I, _I, _I, ctypes.c_uint64, _I, _I, _I, _I, _D, _I, _P, _P, _P, _P,
+                 ctypes.POINTER(Stats)], _I),
+}
+
+
+def lib():
+    """Load libptrace.so (built by __graft_entry__.build()); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libptrace.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(code, ok=(PT_OK,)):
+    if code not in ok:
+        buf = ctypes.create_string_buffer(512)
+        lib().pt_last_error(buf, 512)
+        raise PtraceError(code, buf.value.decode(errors="replace"))
+    return code
+
+
+def _ints(vals):
+    vals = [int(v) for v in vals]
+    return (_I * len(vals))(*vals)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _np_ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+# Live handles, destroyed operators-first at interpreter exit while the CUDA
+# runtime is still up (a destructor running after it has shut down may crash).
+_LIVE = weakref.WeakValueDictionary()
+_LIVE_ID = [0]
+
+
+def _register(obj):
+    _LIVE_ID[0] += 1
+    _LIVE[_LIVE_ID[0]] = obj
+
+
+@atexit.register
+def _close_all():
+    objs = list(_LIVE.values())
+    for o in objs:
+        if isinstance(o, Operator):
+            o.close()
+    for o in objs:
+        if isinstance(o, Context):
+            o.close()
+
+
+def exported_symbols():
+    """Names the binding expects the library to export."""
+    return sorted(_SIGS)
+
+
+class Context:
+    """A library context bound to one CUDA device and stream.
+
+    stream: a torch.cuda.Stream, an integer cudaStream_t, or None for torch's
+    current stream (so torch CUDA events bracket the library's kernels)."""
+
+    def __init__(self, device=0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the ptrace library has no CPU path")
+        self.device = int(device)
+        torch.cuda.set_device(self.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        if handle == 0:
+            handle = 1          # torch's default stream is the legacy stream: cudaStreamLegacy
+        self.stream = stream
+        self._h = ctypes.c_void_p()
+        _check(lib().pt_create(ctypes.byref(self._h), self.device, ctypes.c_void_p(handle)))
+        _register(self)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().pt_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def synchronize(self):
+        _check(lib().pt_synchronize(self._h))
+
+    def set_memory_budget(self, nbytes):
+        _check(lib().pt_set_memory_budget(self._h, int(nbytes)))
+
+    def profile(self, on=True):
+        _check(lib().pt_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self, which=0, reset=True):
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        _check(lib().pt_profile_read(self._h, which, ctypes.byref(n), ctypes.byref(ms), 1 if reset else 0))
+        return n.value, ms.value
+
+
+class Operator:
+    def __init__(self, ctx, handle, dims, dof, keep=None):
+        self.ctx, self._h, self.dims, self.dof, self._keep = ctx, handle, list(dims), dof, keep
+        self.N = int(np.prod(dims))
+        _register(self)
+
+    def close(self):
+        if self._h:
+            lib().pt_op_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def field_shape(self, nrhs):
+        return (nrhs, self.N) if self.dof == 1 else (nrhs, self.N, 4, 3)
+
+    def field_dtype(self):
+        import torch
+        return torch.float64 if self.dof == 1 else torch.complex128
+
+
+def laplacian(ctx, dims, m2):
+    h = ctypes.c_void_p()
+    _check(lib().pt_op_laplacian(ctx.handle, _ints(dims), float(m2), ctypes.byref(h)))
+    op = Operator(ctx, h, dims, 1)
+    op.m2 = float(m2)
+    return op
+
+
+def wilson(ctx, dims, U, kappa, antiperiodic_t=True):
+    """U: torch.complex128 tensor [N, 4, 3, 3] on the context's device."""
+    import torch
+    assert U.dtype == torch.complex128 and U.is_cuda and U.is_contiguous()
+    h = ctypes.c_void_p()
+    _check(lib().pt_op_wilson(ctx.handle, _ints(dims), _ptr(U), float(kappa), 1 if antiperiodic_t else 0,
+                              ctypes.byref(h)))
+    op = Operator(ctx, h, dims, 12)
+    op.kappa = float(kappa)
+    ctx.synchronize()
+    return op
+
+
+def apply(op, x, prec="fp64"):
+    import torch
+    x = x.contiguous()
+    y = torch.empty_like(x)
+    nrhs = x.shape[0]
+    _check(lib().pt_apply(op.ctx.handle, op._h, _ptr(x), _ptr(y), nrhs, PREC[prec]))
+    return y
+
+
+def stencil(mu, p_list, k):
+    p = _ints(p_list)
+    n = _I()
+    lib().pt_stencil(mu, p, len(p_list), k, None, 0, ctypes.byref(n))
+    out = (_I * (4 * max(n.value, 1)))()
+    _check(lib().pt_stencil(mu, p, len(p_list), k, out, n.value, ctypes.byref(n)))
+    return np.array(out[:4 * n.value], dtype=np.int64).reshape(-1, 4)
+
+
+def colour(ctx, dims, mu, p_list, k, order="natural", out=None):
+    import torch
+    N = int(np.prod(dims))
+    col = out if out is not None else torch.empty(N, dtype=torch.int32, device="cuda:%d" % ctx.device)
+    m = _I()
+    _check(lib().pt_colour(ctx.handle, _ints(dims), mu, _ints(p_list), len(p_list), k,
+                           ORDER[order] if isinstance(order, str) else int(order), _ptr(col), ctypes.byref(m)))
+    return col, m.value
+
+
+def conflicts(ctx, dims, mu, p_list, k, col):
+    n = ctypes.c_int64()
+    _check(lib().pt_colour_conflicts(ctx.handle, _ints(dims), mu, _ints(p_list), len(p_list), k, _ptr(col),
+                                     ctypes.byref(n)))
+    return n.value
+
+
+def make_probe(ctx, col, colour_index, noise, seed, set_index, dof, component):
+    """One probe in the user layout; component -1 = undiluted (independent noise per component)."""
+    import torch
+    N = col.numel()
+    if dof == 1:
+        v = torch.empty(N, dtype=torch.float64, device=col.device)
+    else:
+        v = torch.empty((N, 4, 3), dtype=torch.complex128, device=col.device)
+    _check(lib().pt_make_probes(ctx.handle, _ptr(col), N, int(colour_index), NOISE[noise] if isinstance(noise, str)
+                                else int(noise), int(seed), int(set_index), int(dof), int(component), _ptr(v)))
+    return v
+
+
+def solve(op, B, prec="mixed_fp32", tol=1e-10, maxit=10000, allow_noconv=False):
+    import torch
+    B = B.contiguous()
+    X = torch.empty_like(B)
+    nrhs = B.shape[0]
+    iters = np.zeros(nrhs, dtype=np.int32)
+    relres = np.zeros(nrhs, dtype=np.float64)
+    st = Stats()
+    rc = lib().pt_solve(op.ctx.handle, op._h, _ptr(B), _ptr(X), nrhs, PREC[prec], float(tol), int(maxit),
+                        _np_ptr(iters), _np_ptr(relres), ctypes.byref(st))
+    _check(rc, (PT_OK, PT_ERR_NOCONV) if allow_noconv else (PT_OK,))
+    return X, iters, relres, st.as_dict()
+
+
+def trace(op, col, n_colours, mu, p_list, noise="z2", seed=0, set0=0, n_sets=1, dilute=True,
+          prec="mixed_fp32", tol=1e-10, maxit=20000):
+    """Probed estimates est[s, n] of Tr(P_{p_n} A^{-1}); returns (est, mean, var, stats)."""
+    n_p = len(p_list)
+    est = np.zeros((n_sets, n_p), dtype=np.complex128)
+    mean = np.zeros(n_p, dtype=np.complex128)
+    var = np.zeros(n_p, dtype=np.float64)
+    st = Stats()
+    rc = lib().pt_trace_PAinv(op.ctx.handle, op._h, _ptr(col), int(n_colours), int(mu), _ints(p_list), n_p,
+                              NOISE[noise] if isinstance(noise, str) else int(noise), int(seed), int(set0),
+                              int(n_sets), 1 if dilute else 0, PREC[prec], float(tol), int(maxit),
+                              _np_ptr(est), _np_ptr(mean), _np_ptr(var), ctypes.byref(st))
+    _check(rc)
+    return est, mean, var, st.as_dict()
+
+
+def grad(op, col, n_colours, mu, p, noise="z2", seed=0, set0=0, n_sets=1, dilute=True, prec="mixed_fp32",
+         tol=1e-10, maxit=20000, links=False):
+    """Adjoint gradient: returns (est[n_sets], dparam, G, Gbar, stats); G/Gbar are
+    torch complex128 [N, 4, 3, 3] when links=True (Wilson only), else None."""
+    import torch
+    est = np.zeros(n_sets, dtype=np.complex128)
+    dp = np.zeros(1, dtype=np.complex128)
+    G = Gb = None
+    if links:
+        G = torch.empty((op.N, 4, 3, 3), dtype=torch.complex128, device=col.device)
+        Gb = torch.empty_like(G)
+    st = Stats()
+    rc = lib().pt_grad(op.ctx.handle, op._h, _ptr(col), int(n_colours), int(mu), int(p),
+                       NOISE[noise] if isinstance(noise, str) else int(noise), int(seed), int(set0), int(n_sets),
+                       1 if dilute else 0, PREC[prec], float(tol), int(maxit), _np_ptr(est), _np_ptr(dp),
+                       _ptr(G), _ptr(Gb), ctypes.byref(st))
+    _check(rc)
+    return est, complex(dp[0]), G, Gb, st.as_dict()

@@ -1,0 +1,57 @@
+"""C-ABI library: it builds, loads without a GPU, exports every symbol that
+include/ptrace.h declares, and its host-side stencil (Eq. (9)) matches the
+oracle.  No compute call is made (there may be no GPU)."""
+import os
+import re
+import shutil
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def ptlib():
+    from paper_2106_01275_gb300 import build
+    if build.needs_build():
+        if not shutil.which(build.NVCC) and not os.path.exists(build.NVCC):
+            pytest.skip("nvcc not available to build libptrace.so")
+        build.build()
+    from paper_2106_01275_gb300 import ptrace
+    return ptrace
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "ptrace.h")).read()
+    return sorted(set(re.findall(r"PT_API\s+int\s+(pt_\w+)\s*\(", txt)))
+
+
+def test_header_and_binding_agree(ptlib):
+    assert header_symbols() == ptlib.exported_symbols()
+
+
+def test_library_exports_every_declared_symbol(ptlib):
+    L = ptlib.lib()
+    for name in header_symbols():
+        assert hasattr(L, name), name
+    assert L.pt_version() >= 100
+
+
+@pytest.mark.parametrize("mu,p_list,k", [(0, [0], 1), (2, [3], 2), (3, [1, 2], 3), (1, [5], 2), (2, [0], 4)])
+def test_stencil_matches_oracle(ptlib, mu, p_list, k):
+    from oracle.stencil import displaced_stencil
+    got = ptlib.stencil(mu, p_list, k)
+    want = displaced_stencil(4, mu, p_list, k)
+    assert np.array_equal(got, want)
+
+
+def test_bad_arguments_are_rejected_without_a_gpu(ptlib):
+    import ctypes
+    L = ptlib.lib()
+    n = ctypes.c_int()
+    p = (ctypes.c_int * 1)(1)
+    assert L.pt_stencil(7, p, 1, 2, None, 0, ctypes.byref(n)) == ptlib.PT_ERR_ARG
+    buf = ctypes.create_string_buffer(256)
+    L.pt_last_error(buf, 256)
+    assert b"pt_stencil" in buf.value
