@@ -108,6 +108,10 @@ PT_API int pt_synchronize(pt_ctx *ctx);
  * right-hand sides (default 16 GiB).  Larger budgets keep more RHS in flight. */
 PT_API int pt_set_memory_budget(pt_ctx *ctx, size_t bytes);
 
+/* Cap on the right-hand sides the solver engine keeps in flight (0 = no cap
+ * beyond the memory budget).  n = 1 gives the plain one-RHS-at-a-time solve. */
+PT_API int pt_set_max_slots(pt_ctx *ctx, int n);
+
 /* Enable (1) or disable (0) per-kernel CUDA-event timing inside the engine.
  * pt_profile_read returns, for the kernel class `which` (0 = the operator
  * apply of the inner Krylov iteration), the launches and the summed
@@ -210,6 +214,20 @@ PT_API int pt_trace_PAinv(pt_ctx *ctx, const pt_op *op, const int32_t *col_dev, 
                    const int *p_list, int n_p, int noise, uint64_t seed, int set0, int n_sets,
                    int dilute, int prec, double tol, int maxit, double *est_out,
                    double *mean_out, double *var_out, pt_stats *stats);
+
+/* Several colourings in one batched solve (Sec. 3.3 and Sec. 4.3 compare
+ * colourings and reuse one colouring for many displacements): colouring i is
+ * cols_dev[i * N .. (i+1) * N) with n_colours[i] colours (host array); every
+ * probe of every colouring and set is queued into the same engine run, and
+ * every solve is contracted with every displacement in p_list.
+ *   est_out[i][s][n] (host complex128 [n_col][n_sets][n_p])
+ *     = sum_{c < n_colours[i]} sum_a v_{s,c,a}^H P_{p_n} A^{-1} v_{s,c,a}
+ * with v built from colouring i.  The noise of set s is the same for every
+ * colouring.  Other arguments as pt_trace_PAinv.  Synchronises. */
+PT_API int pt_trace_PAinv_multi(pt_ctx *ctx, const pt_op *op, int n_col, const int32_t *cols_dev,
+                                const int *n_colours, int mu, const int *p_list, int n_p, int noise,
+                                uint64_t seed, int set0, int n_sets, int dilute, int prec, double tol,
+                                int maxit, double *est_out, pt_stats *stats);
 
 /* Adjoint gradient of the probed estimate T = sum_s est[s] for one
  * displacement p (not in the paper): with x = A^{-1} v, y = A^{-+} P^T v,

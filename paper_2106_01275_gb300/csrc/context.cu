@@ -87,6 +87,12 @@ extern "C" int pt_set_memory_budget(pt_ctx *c, size_t bytes) {
     return PT_OK;
 }
 
+extern "C" int pt_set_max_slots(pt_ctx *c, int n) {
+    PT_CHECK_ARG(c && n >= 0, "pt_set_max_slots: need n >= 0");
+    c->max_slots = n;
+    return PT_OK;
+}
+
 extern "C" int pt_profile_enable(pt_ctx *c, int on) {
     PT_CHECK_ARG(c, "pt_profile_enable: ctx is NULL");
     c->prof = on != 0;

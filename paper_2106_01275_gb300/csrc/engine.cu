@@ -27,6 +27,8 @@
 
 #include "pt_common.cuh"
 
+#define PT_BLOCK 256        // threads per engine work item
+
 enum { PH_EMPTY = 0, PH_START = 1, PH_OUTER = 2, PH_INNER = 3, PH_CONTRACT = 4, PH_DONE = 5 };
 enum { MODE_TRACE = 0, MODE_SOLVE = 1, MODE_GRAD = 2 };
 enum { LIST_CONTRACT = 0, LIST_OUTER = 1, LIST_INNER = 2 };
@@ -42,6 +44,7 @@ struct Slot {
 
 struct Task {
     int set, colour, comp, flags;
+    int cidx, pad0, pad1, pad2;   // cidx: which colouring (multi-colouring runs)
 };
 
 struct TaskStat {
@@ -51,7 +54,7 @@ struct TaskStat {
 
 struct EP {
     Geom g;
-    int kind, nsb, R;
+    int kind, nsb, R, gs, vec4;
     int64_t L;                 // reals per slot field
     double diag, kappa;
     int antip;
@@ -67,7 +70,7 @@ struct EP {
     const double *B_user;      // solve mode: user layout sources
     double *X_user;            // solve mode: user layout solutions
     double *x64;
-    void *e, *r, *pv, *q, *s, *t, *r0;
+    void *e, *r, *pv, *q, *s, *t, *r0, *p1;   // p1: second CG direction buffer
     Slot *slots;
     double *partials;
     int *counters, *lists, *counts, *head, *flags;
@@ -140,7 +143,7 @@ __device__ __forceinline__ Cx<double> source_val(const EP &P, const Task &tk, ui
         src = shift_site(P.g, idx, x, P.mu, -P.pshift);      // (P^T v)(x) = v(x - p)
         if (KIND && a >= 6) sg = -1.0;                       // g5 = diag(1, 1, -1, -1)
     }
-    if (P.col[src] != tk.colour) return Cx<double>{0.0, 0.0};
+    if (P.col[(size_t)tk.cidx * P.g.N + src] != tk.colour) return Cx<double>{0.0, 0.0};
     Cx<double> z;
     if (P.dilute) {
         if (a != tk.comp) return Cx<double>{0.0, 0.0};
@@ -151,57 +154,95 @@ __device__ __forceinline__ Cx<double> source_val(const EP &P, const Task &tk, ui
     return Cx<double>{sg * z.re, sg * z.im};
 }
 
-// ------------------------------------------------------------------ reduction tail
-// Item partials -> (last item of the slot) deterministic total in `tot` (valid in
-// all threads).  Returns true in every thread of the CTA that finishes the slot.
+// ------------------------------------------------------------------ work items and reductions
+// An item is one slot's block of Tile<KIND>::SITES consecutive sites, processed
+// by one CTA of PT_BLOCK threads (SPT sites per thread).  A reduction stores one
+// partial sum per item (plain stores: the kernel boundary orders them); a
+// finalize kernel with one warp per slot adds the slot's nsb partials in a
+// fixed order (deterministic) and advances the slot's state machine.
+template <int KIND>
+struct Tile {
+    static constexpr int SPT = KIND ? 1 : 8;
+    static constexpr int SITES = PT_BLOCK * SPT;
+};
+
+// Item order: slots are taken in groups of P.gs; inside a group the items run
+// site-block-major, so that consecutive CTAs share a site block (the links of
+// the Wilson operator are reused across the group from L2) while a slot's halo
+// blocks are visited close in time (gs = 1: slot-major, for the Laplacian).
+#define ITEM_LOOP(LIST)                                                         \
+    const int cnt = P.counts[LIST];                                             \
+    const int *lst = P.lists + (size_t)(LIST) * P.R;                            \
+    const int64_t n_items = (int64_t)cnt * P.nsb;                               \
+    const int64_t gitems_ = (int64_t)P.gs * P.nsb;                              \
+    for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {              \
+        const int64_t g_ = it / gitems_;                                        \
+        const int base_ = (int)(g_ * P.gs);                                     \
+        const int gsz_ = min(P.gs, cnt - base_);                                \
+        const int rem_ = (int)(it - g_ * gitems_);                              \
+        const int b = rem_ / gsz_;                                              \
+        const int j = lst[base_ + rem_ % gsz_];
+#define ITEM_LOOP_END }
+
+#define SITE_LOOP(KIND)                                                         \
+    for (int k_ = 0; k_ < Tile<KIND>::SPT; ++k_) {                              \
+        const int idx = b * Tile<KIND>::SITES + k_ * PT_BLOCK + (int)threadIdx.x; \
+        if (idx >= N) continue;
+#define SITE_LOOP_END }
+
 template <int K>
-__device__ __forceinline__ bool slot_reduce(const EP &P, int j, int b, double v[K], double *sh, double tot[K]) {
-    __shared__ int s_last;
+__device__ __forceinline__ void item_store(const EP &P, int j, int b, double v[K], double *sh) {
     block_sum<K>(v, sh);
     if (threadIdx.x == 0) {
         double *dst = P.partials + ((size_t)j * P.nsb + b) * K;
 #pragma unroll
         for (int k = 0; k < K; ++k) dst[k] = v[k];
-        __threadfence();
-        int prev = atomicAdd(&P.counters[j], 1);
-        s_last = (prev == P.nsb - 1);
     }
-    __syncthreads();
-    bool last = s_last;
-    if (last) {
-        __threadfence();
-        double acc[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] = 0.0;
-        const double *src = P.partials + (size_t)j * P.nsb * K;
-        for (int i = threadIdx.x; i < P.nsb; i += blockDim.x)
-#pragma unroll
-            for (int k = 0; k < K; ++k) acc[k] += __ldcg(src + (size_t)i * K + k);
-        block_sum<K>(acc, sh);
-        if (threadIdx.x == 0) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) sh[k] = acc[k];
-            P.counters[j] = 0;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < K; ++k) tot[k] = sh[k];
-    }
-    __syncthreads();
-    return last;
 }
 
-// work-item loop helper: item -> (slot, site block); site-block-major order so
-// that consecutive CTAs share a site block (link and halo reuse in L2)
-#define ITEM_LOOP(LIST)                                                         \
+// per-thread partials accumulated in the arithmetic type R (FP32 for the
+// FP32 / BF16 inner solves: the FP64 pipe of GB300 is too narrow for a
+// per-site FP64 sum), widened to FP64 for the block and slot reductions
+template <int K, typename R>
+__device__ __forceinline__ void item_store_r(const EP &P, int j, int b, const R vr[K], double *sh) {
+    double v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = (double)vr[k];
+    item_store<K>(P, j, b, v, sh);
+}
+
+#define WARP_LOOP(LIST)                                                         \
     const int cnt = P.counts[LIST];                                             \
     const int *lst = P.lists + (size_t)(LIST) * P.R;                            \
-    const int64_t n_items = (int64_t)cnt * P.nsb;                               \
-    for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {              \
-        const int b = (int)(it / cnt);                                          \
-        const int j = lst[it % cnt];
+    const int lane = threadIdx.x & 31;                                          \
+    const int wstride = (int)((gridDim.x * blockDim.x) >> 5);                   \
+    for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < cnt; w += wstride) { \
+        const int j = lst[w];                                                   \
+        Slot &st = P.slots[j];
+#define WARP_LOOP_END }
 
-#define ITEM_LOOP_END }
+// all lanes receive the slot's total (fixed summation order)
+template <int K>
+__device__ __forceinline__ void warp_total(const EP &P, int j, double tot[K]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < K; ++k) tot[k] = 0.0;
+    const double *src = P.partials + (size_t)j * P.nsb * K;
+    for (int i = lane; i < P.nsb; i += 32)
+#pragma unroll
+        for (int k = 0; k < K; ++k) tot[k] += src[(size_t)i * K + k];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tot[k] += __shfl_xor_sync(0xffffffffu, tot[k], o);
+}
+
+// value rounded to the storage type S (and back to the arithmetic type)
+template <typename S, typename R>
+__device__ __forceinline__ R rnd(R v) {
+    if constexpr (std::is_same<S, __nv_bfloat16>::value) return __bfloat162float(__float2bfloat16_rn(v));
+    else return v;
+}
 
 // ------------------------------------------------------------------ schedule
 __device__ int block_exclusive_scan(int v, int *sh, int &total) {
@@ -281,40 +322,41 @@ __global__ void __launch_bounds__(1024) k_schedule(EP P) {
 }
 
 // ------------------------------------------------------------------ contract / copy-out
+// trace mode: q_n = sum_x conj(v(x)) x(x + p_n e_mu) for every displacement
+// (the shifted dot of Eq. (1) with P_{p_n}); solve mode: copy x to the user.
 template <int KIND>
-__global__ void __launch_bounds__(PT_BS) k_contract(EP P) {
+__global__ void __launch_bounds__(PT_BLOCK) k_contract(EP P) {
     __shared__ double sh[32 * 2 * PT_MAX_P];
     const int N = P.g.N;
     ITEM_LOOP(LIST_CONTRACT)
-        Slot &st = P.slots[j];
+        const Slot &st = P.slots[j];
         if (st.phase != PH_CONTRACT) continue;
         const Task tk = P.tasks[st.task];
-        const int idx = b * PT_BS + threadIdx.x;
         const double *x = P.x64 + (size_t)j * P.L;
         if (P.mode == MODE_SOLVE) {
-            if (idx < N) {
+            SITE_LOOP(KIND)
                 if constexpr (KIND == 0) {
                     P.X_user[(size_t)tk.set * N + idx] = x[idx];
                 } else {
                     double *dst = P.X_user + ((size_t)tk.set * N + idx) * 24;
                     for (int c = 0; c < 12; ++c) {
                         Cx<double> v = ld_cx<double, double>(x, N, c, idx);
-                        dst[2 * c] = v.re; dst[2 * c + 1] = v.im;
+                        dst[2 * c] = v.re;
+                        dst[2 * c + 1] = v.im;
                     }
                 }
-            }
-            double v[1] = {0.0}, tot[1];
-            if (slot_reduce<1>(P, j, b, v, sh, tot) && threadIdx.x == 0) st.phase = PH_DONE;
+            SITE_LOOP_END
             continue;
         }
-        // trace mode: q_n = sum_x conj(v(x)) x(x + p_n e_mu), v = the task's probe
         double acc[2 * PT_MAX_P];
 #pragma unroll
         for (int n = 0; n < 2 * PT_MAX_P; ++n) acc[n] = 0.0;
-        if (idx < N && P.col[idx] == tk.colour) {
+        const uint64_t key = pt_set_key(P.seed, tk.set);
+        const int32_t *col = P.col + (size_t)tk.cidx * N;
+        SITE_LOOP(KIND)
+            if (col[idx] != tk.colour) continue;
             int xc[4];
             site_coords(P.g, idx, xc);
-            const uint64_t key = pt_set_key(P.seed, tk.set);
             const int dof = KIND ? 12 : 1;
             for (int a = 0; a < dof; ++a) {
                 if (P.dilute && a != tk.comp) continue;
@@ -324,64 +366,80 @@ __global__ void __launch_bounds__(PT_BS) k_contract(EP P) {
                 for (int n = 0; n < PT_MAX_P; ++n) {
                     if (n >= P.n_p) break;
                     int y = shift_site(P.g, idx, xc, P.mu, P.p[n]);
-                    Cx<double> xv = Fld<KIND, double>::ld(x, N, a, y);
-                    Cx<double> q = cconjmul(z, xv);
+                    Cx<double> q = cconjmul(z, Fld<KIND, double>::ld(x, N, a, y));
                     acc[2 * n] += q.re;
                     acc[2 * n + 1] += q.im;
                 }
             }
-        }
-        double tot[2 * PT_MAX_P];
-        if (slot_reduce<2 * PT_MAX_P>(P, j, b, acc, sh, tot) && threadIdx.x == 0) {
-            for (int n = 0; n < P.n_p; ++n) {
-                P.task_out[((size_t)st.task * P.n_p + n) * 2] = tot[2 * n];
-                P.task_out[((size_t)st.task * P.n_p + n) * 2 + 1] = tot[2 * n + 1];
-            }
-            st.phase = PH_DONE;
-        }
+        SITE_LOOP_END
+        item_store<2 * PT_MAX_P>(P, j, b, acc, sh);
     ITEM_LOOP_END
 }
 
+__global__ void k_fin_contract(EP P) {
+    WARP_LOOP(LIST_CONTRACT)
+        if (st.phase != PH_CONTRACT) continue;
+        if (P.mode == MODE_TRACE) {
+            double tot[2 * PT_MAX_P];
+            warp_total<2 * PT_MAX_P>(P, j, tot);
+            if (lane == 0)
+                for (int n = 0; n < P.n_p; ++n) {
+                    P.task_out[((size_t)st.task * P.n_p + n) * 2] = tot[2 * n];
+                    P.task_out[((size_t)st.task * P.n_p + n) * 2 + 1] = tot[2 * n + 1];
+                }
+        }
+        __syncwarp();
+        if (lane == 0) st.phase = PH_DONE;
+    WARP_LOOP_END
+}
+
 // ------------------------------------------------------------------ outer (FP64) steps
+// x64 += e (FP64 defect-correction update); x64 = 0 for a newly started task
 template <int KIND, typename S>
-__global__ void __launch_bounds__(PT_BS) k_outer_update(EP P) {
+__global__ void __launch_bounds__(PT_BLOCK) k_outer_update(EP P) {
     typedef Fld<KIND, S> F;
     const int N = P.g.N;
     ITEM_LOOP(LIST_OUTER)
         const int ph = P.slots[j].phase;
-        const int idx = b * PT_BS + threadIdx.x;
-        if (idx >= N) continue;
+        if (ph != PH_START && ph != PH_OUTER) continue;
         double *x = P.x64 + (size_t)j * P.L;
         const S *e = slot_cptr<S>(P.e, j, P.L);
-        for (int c = 0; c < F::NC; ++c) {
-            Cx<double> v = {0.0, 0.0};
-            if (ph == PH_OUTER) {
-                Cx<double> xv = Fld<KIND, double>::ld(x, N, c, idx);
-                auto ev = F::ld(e, N, c, idx);
-                v = Cx<double>{xv.re + (double)ev.re, xv.im + (double)ev.im};
+        SITE_LOOP(KIND)
+            for (int c = 0; c < F::NC; ++c) {
+                Cx<double> v = {0.0, 0.0};
+                if (ph == PH_OUTER) {
+                    Cx<double> xv = Fld<KIND, double>::ld(x, N, c, idx);
+                    auto ev = F::ld(e, N, c, idx);
+                    v = Cx<double>{xv.re + (double)ev.re, xv.im + (double)ev.im};
+                }
+                Fld<KIND, double>::st(x, N, c, idx, v);
             }
-            Fld<KIND, double>::st(x, N, c, idx, v);
-        }
+        SITE_LOOP_END
     ITEM_LOOP_END
 }
 
+// r64 = b - A x64 in FP64; r = (S) r64 starts the inner solve (e = 0);
+// partials: |r64|^2, |b|^2, |r|^2 (of the rounded r)
 template <int KIND, typename S>
-__global__ void __launch_bounds__(PT_BS) k_outer_residual(EP P) {
+__global__ void __launch_bounds__(PT_BLOCK) k_outer_residual(EP P) {
     typedef Fld<KIND, S> F;
     typedef typename F::R R;
     __shared__ double sh[32 * 3];
     const int N = P.g.N;
     ITEM_LOOP(LIST_OUTER)
-        Slot &st = P.slots[j];
+        const Slot &st = P.slots[j];
         const int ph = st.phase;
         if (ph != PH_START && ph != PH_OUTER) continue;
         const Task tk = P.tasks[st.task];
-        const int idx = b * PT_BS + threadIdx.x;
+        const uint64_t key = (P.mode == MODE_SOLVE) ? 0 : pt_set_key(P.seed, tk.set);
+        S *r = slot_ptr<S>(P.r, j, P.L);
+        S *pv = slot_ptr<S>(P.pv, j, P.L);
+        S *e = slot_ptr<S>(P.e, j, P.L);
+        S *r0 = KIND ? slot_ptr<S>(P.r0, j, P.L) : nullptr;
         double v[3] = {0.0, 0.0, 0.0};
-        if (idx < N) {
+        SITE_LOOP(KIND)
             int xc[4];
             site_coords(P.g, idx, xc);
-            const uint64_t key = (P.mode == MODE_SOLVE) ? 0 : pt_set_key(P.seed, tk.set);
             Cx<double> ax[F::NC];
             if (ph == PH_OUTER) {
                 apply_site<KIND, double, double, double>(P, P.x64 + (size_t)j * P.L, P.U64, idx, xc, ax);
@@ -389,34 +447,40 @@ __global__ void __launch_bounds__(PT_BS) k_outer_residual(EP P) {
 #pragma unroll
                 for (int c = 0; c < F::NC; ++c) ax[c] = Cx<double>{0.0, 0.0};
             }
-            S *r = slot_ptr<S>(P.r, j, P.L);
-            S *pv = slot_ptr<S>(P.pv, j, P.L);
-            S *e = slot_ptr<S>(P.e, j, P.L);
-            S *r0 = KIND ? slot_ptr<S>(P.r0, j, P.L) : nullptr;
             for (int c = 0; c < F::NC; ++c) {
                 Cx<double> bv = source_val<KIND>(P, tk, key, idx, xc, c);
                 Cx<double> rv = csub(bv, ax[c]);
                 v[0] += rv.re * rv.re + rv.im * rv.im;
                 v[1] += bv.re * bv.re + bv.im * bv.im;
-                Cx<R> rs = Cx<R>{(R)rv.re, (R)rv.im};
+                Cx<R> rs = Cx<R>{rnd<S, R>((R)rv.re), rnd<S, R>((R)rv.im)};
                 F::st(r, N, c, idx, rs);
-                F::st(pv, N, c, idx, rs);
-                if constexpr (KIND == 1) F::st(r0, N, c, idx, rs);
+                if constexpr (KIND == 1) {
+                    F::st(pv, N, c, idx, rs);
+                    F::st(r0, N, c, idx, rs);
+                }
                 F::st(e, N, c, idx, Cx<R>{R(0), R(0)});
-                Cx<R> back = F::ld(r, N, c, idx);          // the inner solve sees the rounded r
-                v[2] += (double)back.re * (double)back.re + (double)back.im * (double)back.im;
+                v[2] += (double)rs.re * (double)rs.re + (double)rs.im * (double)rs.im;
             }
-        }
+        SITE_LOOP_END
+        item_store<3>(P, j, b, v, sh);
+    ITEM_LOOP_END
+}
+
+__global__ void k_fin_outer(EP P) {
+    WARP_LOOP(LIST_OUTER)
+        const int ph = st.phase;
+        if (ph != PH_START && ph != PH_OUTER) continue;
         double tot[3];
-        if (slot_reduce<3>(P, j, b, v, sh, tot) && threadIdx.x == 0) {
+        warp_total<3>(P, j, tot);
+        if (lane == 0) {
             if (ph == PH_START) st.bnorm2 = tot[1];
             const double b2 = st.bnorm2;
             const double rel = b2 > 0.0 ? sqrt(tot[0] / b2) : 0.0;
             st.relres = rel;
             st.outer_it += 1;
-            bool finite = isfinite(tot[0]);
+            const bool finite = isfinite(tot[0]);
             if (!finite) atomicOr(&P.flags[FLAG_NUMERIC], 1);
-            bool conv = (b2 == 0.0) || rel <= P.tol;
+            const bool conv = (b2 == 0.0) || rel <= P.tol;
             if (conv || !finite || st.total_it >= P.maxit) {
                 if (!conv && finite) atomicAdd(&P.flags[FLAG_NOCONV], 1);
                 P.tstat[st.task] = TaskStat{st.total_it, st.outer_it, rel};
@@ -427,71 +491,107 @@ __global__ void __launch_bounds__(PT_BS) k_outer_residual(EP P) {
                 st.rr = tot[2];
                 st.rr0 = tot[2];
                 st.rho = Cx<double>{tot[2], 0.0};
-                const double floor2 = 0.25 * P.tol * P.tol * b2;
-                st.target2 = fmax(P.delta * P.delta * tot[2], floor2);
+                st.beta = Cx<double>{0.0, 0.0};
+                st.target2 = fmax(P.delta * P.delta * tot[2], 0.25 * P.tol * P.tol * b2);
             }
         }
-    ITEM_LOOP_END
+    WARP_LOOP_END
 }
 
 // ------------------------------------------------------------------ CG (Laplacian)
-template <typename S, typename LS>
-__global__ void __launch_bounds__(PT_BS) k_cg_apply(EP P) {
-    typedef Fld<0, S> F;
-    typedef typename F::R R;
+// Fused direction update and stencil: with i = inner iteration,
+//   p_i = r + beta p_{i-1}  (p_0 = r)   -- recomputed at the neighbours, stored at x
+//   q   = A p_i,  partial p_i . q
+// p alternates between two buffers (pv, p1) so that no CTA reads a value
+// another CTA is overwriting.
+template <typename S>
+__global__ void __launch_bounds__(PT_BLOCK) k_cg_apply(EP P) {
+    typedef typename ArithT<S>::T R;
     __shared__ double sh[32];
     const int N = P.g.N;
+    const R diag = (R)P.diag;
     ITEM_LOOP(LIST_INNER)
-        Slot &st = P.slots[j];
+        const Slot &st = P.slots[j];
         if (st.phase != PH_INNER) continue;
-        const int idx = b * PT_BS + threadIdx.x;
-        double v[1] = {0.0};
-        if (idx < N) {
+        const int i = st.inner_it;
+        const R be = (R)st.beta.re;
+        const bool first = (i == 0);
+        const S *r = slot_cptr<S>(P.r, j, P.L);
+        const S *pold = slot_cptr<S>((i & 1) ? P.p1 : P.pv, j, P.L);
+        S *pnew = slot_ptr<S>((i & 1) ? P.pv : P.p1, j, P.L);
+        S *q = slot_ptr<S>(P.q, j, P.L);
+        R vr[1] = {R(0)};
+        SITE_LOOP(0)
             int xc[4];
             site_coords(P.g, idx, xc);
-            const S *pv = slot_cptr<S>(P.pv, j, P.L);
-            R q = lap_site<R, S>(P.g, pv, (R)P.diag, idx, xc);
-            st_real(slot_ptr<S>(P.q, j, P.L), (size_t)idx, q);
-            v[0] = (double)ld_real(pv, (size_t)idx) * (double)q;
-        }
+            auto pn = [&](int y) -> R {
+                R rv = ld_real(r, (size_t)y);
+                return first ? rv : rnd<S, R>(rv + be * (R)ld_real(pold, (size_t)y));
+            };
+            const R pc = pn(idx);
+            R nb = R(0);
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu) {
+                nb += pn(nb_fwd(P.g, idx, xc, mu));
+                nb += pn(nb_bwd(P.g, idx, xc, mu));
+            }
+            const R qv = rnd<S, R>(diag * pc - nb);
+            st_real(pnew, (size_t)idx, pc);
+            st_real(q, (size_t)idx, qv);
+            vr[0] += pc * qv;
+        SITE_LOOP_END
+        item_store_r<1>(P, j, b, vr, sh);
+    ITEM_LOOP_END
+}
+
+__global__ void k_fin_cg_alpha(EP P) {
+    WARP_LOOP(LIST_INNER)
+        if (st.phase != PH_INNER) continue;
         double tot[1];
-        if (slot_reduce<1>(P, j, b, v, sh, tot) && threadIdx.x == 0) {
+        warp_total<1>(P, j, tot);
+        if (lane == 0) {
             if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
                 atomicOr(&P.flags[FLAG_NUMERIC], 2);
-                st.phase = PH_OUTER;                     // fall back to a true-residual restart
-                st.alpha = Cx<double>{0.0, 0.0};
+                st.phase = PH_OUTER;                     // restart from the true residual
             } else {
                 st.alpha = Cx<double>{st.rr / tot[0], 0.0};
             }
         }
-    ITEM_LOOP_END
+    WARP_LOOP_END
 }
 
+// e += alpha p_i;  r -= alpha q;  partial |r|^2
 template <typename S>
-__global__ void __launch_bounds__(PT_BS) k_cg_update(EP P) {
+__global__ void __launch_bounds__(PT_BLOCK) k_cg_update(EP P) {
+    typedef typename ArithT<S>::T R;
     __shared__ double sh[32];
     const int N = P.g.N;
     ITEM_LOOP(LIST_INNER)
-        Slot &st = P.slots[j];
+        const Slot &st = P.slots[j];
         if (st.phase != PH_INNER) continue;
-        const int idx = b * PT_BS + threadIdx.x;
-        double v[1] = {0.0};
-        if (idx < N) {
-            typedef typename ArithT<S>::T R;
-            const R al = (R)st.alpha.re;
-            S *e = slot_ptr<S>(P.e, j, P.L);
-            S *r = slot_ptr<S>(P.r, j, P.L);
-            const S *pv = slot_cptr<S>(P.pv, j, P.L);
-            const S *q = slot_cptr<S>(P.q, j, P.L);
-            R ev = ld_real(e, (size_t)idx) + al * ld_real(pv, (size_t)idx);
-            R rv = ld_real(r, (size_t)idx) - al * ld_real(q, (size_t)idx);
+        const R al = (R)st.alpha.re;
+        S *e = slot_ptr<S>(P.e, j, P.L);
+        S *r = slot_ptr<S>(P.r, j, P.L);
+        const S *pc = slot_cptr<S>((st.inner_it & 1) ? P.pv : P.p1, j, P.L);
+        const S *q = slot_cptr<S>(P.q, j, P.L);
+        R vr[1] = {R(0)};
+        SITE_LOOP(0)
+            const R ev = rnd<S, R>((R)ld_real(e, (size_t)idx) + al * (R)ld_real(pc, (size_t)idx));
+            const R rv = rnd<S, R>((R)ld_real(r, (size_t)idx) - al * (R)ld_real(q, (size_t)idx));
             st_real(e, (size_t)idx, ev);
             st_real(r, (size_t)idx, rv);
-            double rs = (double)ld_real(r, (size_t)idx);
-            v[0] = rs * rs;
-        }
+            vr[0] += rv * rv;
+        SITE_LOOP_END
+        item_store_r<1>(P, j, b, vr, sh);
+    ITEM_LOOP_END
+}
+
+__global__ void k_fin_cg_beta(EP P) {
+    WARP_LOOP(LIST_INNER)
+        if (st.phase != PH_INNER) continue;
         double tot[1];
-        if (slot_reduce<1>(P, j, b, v, sh, tot) && threadIdx.x == 0) {
+        warp_total<1>(P, j, tot);
+        if (lane == 0) {
             st.inner_it += 1;
             st.total_it += 1;
             if (tot[0] <= st.target2 || st.inner_it >= P.max_inner || st.total_it >= P.maxit || !isfinite(tot[0])) {
@@ -501,161 +601,308 @@ __global__ void __launch_bounds__(PT_BS) k_cg_update(EP P) {
                 st.rr = tot[0];
             }
         }
+    WARP_LOOP_END
+}
+
+// ------------------------------------------------------------------ CG, four sites per thread
+// Fast path when D_0 is a multiple of 4: a thread owns the quad of sites
+// 4m .. 4m+3 of one x row.  The quad and its y, z, t neighbour quads are
+// vector loads (16 B for FP32, 8 B for BF16, 2 x 16 B for FP64); the two x
+// neighbours outside the quad are scalar loads.  Same arithmetic as the
+// one-site kernels above, so the two paths give identical results.
+template <typename S> struct Quad;
+template <> struct Quad<float> {
+    __device__ __forceinline__ static void ld(const float *p, int i, float v[4]) {
+        const float4 a = *reinterpret_cast<const float4 *>(p + i);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+    __device__ __forceinline__ static void st(float *p, int i, const float v[4]) {
+        *reinterpret_cast<float4 *>(p + i) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <> struct Quad<double> {
+    __device__ __forceinline__ static void ld(const double *p, int i, double v[4]) {
+        const double2 a = *reinterpret_cast<const double2 *>(p + i);
+        const double2 c = *reinterpret_cast<const double2 *>(p + i + 2);
+        v[0] = a.x; v[1] = a.y; v[2] = c.x; v[3] = c.y;
+    }
+    __device__ __forceinline__ static void st(double *p, int i, const double v[4]) {
+        *reinterpret_cast<double2 *>(p + i) = make_double2(v[0], v[1]);
+        *reinterpret_cast<double2 *>(p + i + 2) = make_double2(v[2], v[3]);
+    }
+};
+template <> struct Quad<__nv_bfloat16> {
+    __device__ __forceinline__ static void ld(const __nv_bfloat16 *p, int i, float v[4]) {
+        const uint2 a = *reinterpret_cast<const uint2 *>(p + i);
+        const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&a.x));
+        const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&a.y));
+        v[0] = lo.x; v[1] = lo.y; v[2] = hi.x; v[3] = hi.y;
+    }
+    __device__ __forceinline__ static void st(__nv_bfloat16 *p, int i, const float v[4]) {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]);
+        __nv_bfloat162 hi = __floats2bfloat162_rn(v[2], v[3]);
+        uint2 a;
+        a.x = *reinterpret_cast<uint32_t *>(&lo);
+        a.y = *reinterpret_cast<uint32_t *>(&hi);
+        *reinterpret_cast<uint2 *>(p + i) = a;
+    }
+};
+
+#define QUAD_LOOP                                                               \
+    for (int k_ = 0; k_ < Tile<0>::SPT / 4; ++k_) {                             \
+        const int idx = 4 * (b * (Tile<0>::SITES / 4) + k_ * PT_BLOCK + (int)threadIdx.x); \
+        if (idx >= N) continue;
+#define QUAD_LOOP_END }
+
+template <typename S>
+__global__ void __launch_bounds__(PT_BLOCK) k_cg_apply_v4(EP P) {
+    typedef typename ArithT<S>::T R;
+    __shared__ double sh[32];
+    const int N = P.g.N;
+    const int D0 = P.g.D[0];
+    const R diag = (R)P.diag;
+    ITEM_LOOP(LIST_INNER)
+        const Slot &st = P.slots[j];
+        if (st.phase != PH_INNER) continue;
+        const int i = st.inner_it;
+        const R be = (R)st.beta.re;
+        const bool first = (i == 0);
+        const S *r = slot_cptr<S>(P.r, j, P.L);
+        const S *pold = slot_cptr<S>((i & 1) ? P.p1 : P.pv, j, P.L);
+        S *pnew = slot_ptr<S>((i & 1) ? P.pv : P.p1, j, P.L);
+        S *q = slot_ptr<S>(P.q, j, P.L);
+        R vr[1] = {R(0)};
+        QUAD_LOOP
+            int xc[4];
+            site_coords(P.g, idx, xc);
+            auto pquad = [&](int y, R out[4]) {
+                Quad<S>::ld(r, y, out);
+                if (!first) {
+                    R pp[4];
+                    Quad<S>::ld(pold, y, pp);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) out[c] = rnd<S, R>(out[c] + be * pp[c]);
+                }
+            };
+            auto pone = [&](int y) -> R {
+                R rv = ld_real(r, (size_t)y);
+                return first ? rv : rnd<S, R>(rv + be * (R)ld_real(pold, (size_t)y));
+            };
+            R pc[4], t[4];
+            pquad(idx, pc);
+            const R left = pone(xc[0] == 0 ? idx + D0 - 1 : idx - 1);
+            const R right = pone(xc[0] + 4 == D0 ? idx + 4 - D0 : idx + 4);
+            // neighbours summed in the order of the one-site kernel: x+, x-, y+, y-, z+, z-, t+, t-
+            R acc[4] = {pc[1] + left, pc[2] + pc[0], pc[3] + pc[1], right + pc[2]};
+#pragma unroll
+            for (int mu = 1; mu < 4; ++mu) {
+                pquad(nb_fwd(P.g, idx, xc, mu), t);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[c] += t[c];
+                pquad(nb_bwd(P.g, idx, xc, mu), t);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[c] += t[c];
+            }
+            R qv[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                qv[c] = rnd<S, R>(diag * pc[c] - acc[c]);
+                vr[0] += pc[c] * qv[c];
+            }
+            Quad<S>::st(pnew, idx, pc);
+            Quad<S>::st(q, idx, qv);
+        QUAD_LOOP_END
+        item_store_r<1>(P, j, b, vr, sh);
     ITEM_LOOP_END
 }
 
 template <typename S>
-__global__ void __launch_bounds__(PT_BS) k_cg_dir(EP P) {
+__global__ void __launch_bounds__(PT_BLOCK) k_cg_update_v4(EP P) {
+    typedef typename ArithT<S>::T R;
+    __shared__ double sh[32];
     const int N = P.g.N;
     ITEM_LOOP(LIST_INNER)
         const Slot &st = P.slots[j];
         if (st.phase != PH_INNER) continue;
-        const int idx = b * PT_BS + threadIdx.x;
-        if (idx >= N) continue;
-        typedef typename ArithT<S>::T R;
-        const R be = (R)st.beta.re;
-        S *pv = slot_ptr<S>(P.pv, j, P.L);
-        const S *r = slot_cptr<S>(P.r, j, P.L);
-        st_real(pv, (size_t)idx, ld_real(r, (size_t)idx) + be * ld_real(pv, (size_t)idx));
+        const R al = (R)st.alpha.re;
+        S *e = slot_ptr<S>(P.e, j, P.L);
+        S *r = slot_ptr<S>(P.r, j, P.L);
+        const S *pc = slot_cptr<S>((st.inner_it & 1) ? P.pv : P.p1, j, P.L);
+        const S *q = slot_cptr<S>(P.q, j, P.L);
+        R vr[1] = {R(0)};
+        QUAD_LOOP
+            R ev[4], pv[4], qv[4], rv[4];
+            Quad<S>::ld(e, idx, ev);
+            Quad<S>::ld(pc, idx, pv);
+            Quad<S>::ld(q, idx, qv);
+            Quad<S>::ld(r, idx, rv);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                ev[c] = rnd<S, R>(ev[c] + al * pv[c]);
+                rv[c] = rnd<S, R>(rv[c] - al * qv[c]);
+                vr[0] += rv[c] * rv[c];
+            }
+            Quad<S>::st(e, idx, ev);
+            Quad<S>::st(r, idx, rv);
+        QUAD_LOOP_END
+        item_store_r<1>(P, j, b, vr, sh);
     ITEM_LOOP_END
 }
 
 // ------------------------------------------------------------------ BiCGStab (Wilson)
-// v = A p;  alpha = rho / (r0, v)
+// v = A p;  partial (r0, v)
 template <typename S, typename LS>
-__global__ void __launch_bounds__(PT_BS) k_bicg_apply1(EP P) {
+__global__ void __launch_bounds__(PT_BLOCK) k_bicg_apply1(EP P) {
     typedef Fld<1, S> F;
     typedef typename F::R R;
     __shared__ double sh[32 * 2];
     const int N = P.g.N;
     ITEM_LOOP(LIST_INNER)
-        Slot &st = P.slots[j];
+        const Slot &st = P.slots[j];
         if (st.phase != PH_INNER) continue;
-        const int idx = b * PT_BS + threadIdx.x;
-        double v[2] = {0.0, 0.0};
-        if (idx < N) {
+        const S *pv = slot_cptr<S>(P.pv, j, P.L);
+        S *q = slot_ptr<S>(P.q, j, P.L);
+        const S *r0 = slot_cptr<S>(P.r0, j, P.L);
+        R vr[2] = {R(0), R(0)};
+        SITE_LOOP(1)
             int xc[4];
             site_coords(P.g, idx, xc);
             Cx<R> av[12];
-            apply_site<1, R, S, LS>(P, slot_cptr<S>(P.pv, j, P.L), (const LS *)P.U, idx, xc, av);
-            S *q = slot_ptr<S>(P.q, j, P.L);
-            const S *r0 = slot_cptr<S>(P.r0, j, P.L);
+            apply_site<1, R, S, LS>(P, pv, (const LS *)P.U, idx, xc, av);
             for (int c = 0; c < 12; ++c) {
-                F::st(q, N, c, idx, av[c]);
-                Cx<R> w = F::ld(q, N, c, idx);
-                Cx<R> z = F::ld(r0, N, c, idx);
-                v[0] += (double)z.re * w.re + (double)z.im * w.im;
-                v[1] += (double)z.re * w.im - (double)z.im * w.re;
+                const Cx<R> w = Cx<R>{rnd<S, R>(av[c].re), rnd<S, R>(av[c].im)};
+                F::st(q, N, c, idx, w);
+                const Cx<R> z = F::ld(r0, N, c, idx);
+                vr[0] += z.re * w.re + z.im * w.im;
+                vr[1] += z.re * w.im - z.im * w.re;
             }
-        }
+        SITE_LOOP_END
+        item_store_r<2>(P, j, b, vr, sh);
+    ITEM_LOOP_END
+}
+
+__global__ void k_fin_bicg_alpha(EP P) {
+    WARP_LOOP(LIST_INNER)
+        if (st.phase != PH_INNER) continue;
         double tot[2];
-        if (slot_reduce<2>(P, j, b, v, sh, tot) && threadIdx.x == 0) {
-            double d2 = tot[0] * tot[0] + tot[1] * tot[1];
+        warp_total<2>(P, j, tot);
+        if (lane == 0) {
+            const double d2 = tot[0] * tot[0] + tot[1] * tot[1];
             if (!(d2 > 0.0) || !isfinite(d2)) {
                 atomicOr(&P.flags[FLAG_NUMERIC], 4);
                 st.phase = PH_OUTER;
-                st.alpha = Cx<double>{0.0, 0.0};
-            } else {
-                // alpha = rho / (r0, v)
+            } else {  // alpha = rho / (r0, v)
                 st.alpha = Cx<double>{(st.rho.re * tot[0] + st.rho.im * tot[1]) / d2,
                                       (st.rho.im * tot[0] - st.rho.re * tot[1]) / d2};
             }
         }
-    ITEM_LOOP_END
+    WARP_LOOP_END
 }
 
 // s = r - alpha v
 template <typename S>
-__global__ void __launch_bounds__(PT_BS) k_bicg_s(EP P) {
+__global__ void __launch_bounds__(PT_BLOCK) k_bicg_s(EP P) {
     typedef Fld<1, S> F;
     typedef typename F::R R;
     const int N = P.g.N;
     ITEM_LOOP(LIST_INNER)
         const Slot &st = P.slots[j];
         if (st.phase != PH_INNER) continue;
-        const int idx = b * PT_BS + threadIdx.x;
-        if (idx >= N) continue;
         const Cx<R> al = Cx<R>{(R)st.alpha.re, (R)st.alpha.im};
         const S *r = slot_cptr<S>(P.r, j, P.L);
         const S *q = slot_cptr<S>(P.q, j, P.L);
         S *s = slot_ptr<S>(P.s, j, P.L);
-        for (int c = 0; c < 12; ++c) F::st(s, N, c, idx, csub(F::ld(r, N, c, idx), cmul(al, F::ld(q, N, c, idx))));
+        SITE_LOOP(1)
+            for (int c = 0; c < 12; ++c) F::st(s, N, c, idx, csub(F::ld(r, N, c, idx), cmul(al, F::ld(q, N, c, idx))));
+        SITE_LOOP_END
     ITEM_LOOP_END
 }
 
-// t = A s;  omega = (t, s) / (t, t)
+// t = A s;  partials (t, s), |t|^2
 template <typename S, typename LS>
-__global__ void __launch_bounds__(PT_BS) k_bicg_apply2(EP P) {
+__global__ void __launch_bounds__(PT_BLOCK) k_bicg_apply2(EP P) {
     typedef Fld<1, S> F;
     typedef typename F::R R;
     __shared__ double sh[32 * 3];
     const int N = P.g.N;
     ITEM_LOOP(LIST_INNER)
-        Slot &st = P.slots[j];
+        const Slot &st = P.slots[j];
         if (st.phase != PH_INNER) continue;
-        const int idx = b * PT_BS + threadIdx.x;
-        double v[3] = {0.0, 0.0, 0.0};
-        if (idx < N) {
+        const S *s = slot_cptr<S>(P.s, j, P.L);
+        S *t = slot_ptr<S>(P.t, j, P.L);
+        R vr[3] = {R(0), R(0), R(0)};
+        SITE_LOOP(1)
             int xc[4];
             site_coords(P.g, idx, xc);
             Cx<R> av[12];
-            const S *s = slot_cptr<S>(P.s, j, P.L);
             apply_site<1, R, S, LS>(P, s, (const LS *)P.U, idx, xc, av);
-            S *t = slot_ptr<S>(P.t, j, P.L);
             for (int c = 0; c < 12; ++c) {
-                F::st(t, N, c, idx, av[c]);
-                Cx<R> tv = F::ld(t, N, c, idx);
-                Cx<R> sv = F::ld(s, N, c, idx);
-                v[0] += (double)tv.re * sv.re + (double)tv.im * sv.im;     // (t, s) = conj(t) s
-                v[1] += (double)tv.re * sv.im - (double)tv.im * sv.re;
-                v[2] += (double)tv.re * tv.re + (double)tv.im * tv.im;
+                const Cx<R> tv = Cx<R>{rnd<S, R>(av[c].re), rnd<S, R>(av[c].im)};
+                F::st(t, N, c, idx, tv);
+                const Cx<R> sv = F::ld(s, N, c, idx);
+                vr[0] += tv.re * sv.re + tv.im * sv.im;     // (t, s) = conj(t) s
+                vr[1] += tv.re * sv.im - tv.im * sv.re;
+                vr[2] += tv.re * tv.re + tv.im * tv.im;
             }
-        }
-        double tot[3];
-        if (slot_reduce<3>(P, j, b, v, sh, tot) && threadIdx.x == 0) {
-            if (!(tot[2] > 0.0) || !isfinite(tot[2])) {
-                st.omega = Cx<double>{0.0, 0.0};
-            } else {
-                st.omega = Cx<double>{tot[0] / tot[2], tot[1] / tot[2]};
-            }
-        }
+        SITE_LOOP_END
+        item_store_r<3>(P, j, b, vr, sh);
     ITEM_LOOP_END
 }
 
-// e += alpha p + omega s;  r = s - omega t;  rho' = (r0, r), |r|^2
+__global__ void k_fin_bicg_omega(EP P) {
+    WARP_LOOP(LIST_INNER)
+        if (st.phase != PH_INNER) continue;
+        double tot[3];
+        warp_total<3>(P, j, tot);
+        if (lane == 0) {
+            if (!(tot[2] > 0.0) || !isfinite(tot[2])) st.omega = Cx<double>{0.0, 0.0};
+            else st.omega = Cx<double>{tot[0] / tot[2], tot[1] / tot[2]};
+        }
+    WARP_LOOP_END
+}
+
+// e += alpha p + omega s;  r = s - omega t;  partials (r0, r), |r|^2
 template <typename S>
-__global__ void __launch_bounds__(PT_BS) k_bicg_update(EP P) {
+__global__ void __launch_bounds__(PT_BLOCK) k_bicg_update(EP P) {
     typedef Fld<1, S> F;
     typedef typename F::R R;
     __shared__ double sh[32 * 3];
     const int N = P.g.N;
     ITEM_LOOP(LIST_INNER)
-        Slot &st = P.slots[j];
+        const Slot &st = P.slots[j];
         if (st.phase != PH_INNER) continue;
-        const int idx = b * PT_BS + threadIdx.x;
-        double v[3] = {0.0, 0.0, 0.0};
-        if (idx < N) {
-            const Cx<R> al = Cx<R>{(R)st.alpha.re, (R)st.alpha.im};
-            const Cx<R> om = Cx<R>{(R)st.omega.re, (R)st.omega.im};
-            S *e = slot_ptr<S>(P.e, j, P.L);
-            S *r = slot_ptr<S>(P.r, j, P.L);
-            const S *pv = slot_cptr<S>(P.pv, j, P.L);
-            const S *s = slot_cptr<S>(P.s, j, P.L);
-            const S *t = slot_cptr<S>(P.t, j, P.L);
-            const S *r0 = slot_cptr<S>(P.r0, j, P.L);
+        const Cx<R> al = Cx<R>{(R)st.alpha.re, (R)st.alpha.im};
+        const Cx<R> om = Cx<R>{(R)st.omega.re, (R)st.omega.im};
+        S *e = slot_ptr<S>(P.e, j, P.L);
+        S *r = slot_ptr<S>(P.r, j, P.L);
+        const S *pv = slot_cptr<S>(P.pv, j, P.L);
+        const S *s = slot_cptr<S>(P.s, j, P.L);
+        const S *t = slot_cptr<S>(P.t, j, P.L);
+        const S *r0 = slot_cptr<S>(P.r0, j, P.L);
+        R vr[3] = {R(0), R(0), R(0)};
+        SITE_LOOP(1)
             for (int c = 0; c < 12; ++c) {
-                Cx<R> sv = F::ld(s, N, c, idx);
+                const Cx<R> sv = F::ld(s, N, c, idx);
                 F::st(e, N, c, idx, cadd(F::ld(e, N, c, idx), cadd(cmul(al, F::ld(pv, N, c, idx)), cmul(om, sv))));
-                F::st(r, N, c, idx, csub(sv, cmul(om, F::ld(t, N, c, idx))));
-                Cx<R> rv = F::ld(r, N, c, idx);
-                Cx<R> z = F::ld(r0, N, c, idx);
-                v[0] += (double)z.re * rv.re + (double)z.im * rv.im;
-                v[1] += (double)z.re * rv.im - (double)z.im * rv.re;
-                v[2] += (double)rv.re * rv.re + (double)rv.im * rv.im;
+                const Cx<R> rv0 = csub(sv, cmul(om, F::ld(t, N, c, idx)));
+                const Cx<R> rv = Cx<R>{rnd<S, R>(rv0.re), rnd<S, R>(rv0.im)};
+                F::st(r, N, c, idx, rv);
+                const Cx<R> z = F::ld(r0, N, c, idx);
+                vr[0] += z.re * rv.re + z.im * rv.im;
+                vr[1] += z.re * rv.im - z.im * rv.re;
+                vr[2] += rv.re * rv.re + rv.im * rv.im;
             }
-        }
+        SITE_LOOP_END
+        item_store_r<3>(P, j, b, vr, sh);
+    ITEM_LOOP_END
+}
+
+__global__ void k_fin_bicg_beta(EP P) {
+    WARP_LOOP(LIST_INNER)
+        if (st.phase != PH_INNER) continue;
         double tot[3];
-        if (slot_reduce<3>(P, j, b, v, sh, tot) && threadIdx.x == 0) {
+        warp_total<3>(P, j, tot);
+        if (lane == 0) {
             st.inner_it += 1;
             st.total_it += 1;
             const double om2 = st.omega.re * st.omega.re + st.omega.im * st.omega.im;
@@ -663,71 +910,104 @@ __global__ void __launch_bounds__(PT_BS) k_bicg_update(EP P) {
             if (tot[2] <= st.target2 || st.inner_it >= P.max_inner || st.total_it >= P.maxit ||
                 !isfinite(tot[2]) || !(om2 > 0.0) || !(rho2 > 0.0)) {
                 st.phase = PH_OUTER;
-            } else {
-                // beta = (rho' / rho) (alpha / omega)
-                Cx<double> rn = Cx<double>{tot[0], tot[1]};
-                Cx<double> q1 = Cx<double>{(rn.re * st.rho.re + rn.im * st.rho.im) / rho2,
-                                           (rn.im * st.rho.re - rn.re * st.rho.im) / rho2};
-                Cx<double> q2 = Cx<double>{(st.alpha.re * st.omega.re + st.alpha.im * st.omega.im) / om2,
-                                           (st.alpha.im * st.omega.re - st.alpha.re * st.omega.im) / om2};
+            } else {  // beta = (rho' / rho) (alpha / omega)
+                const Cx<double> rn = Cx<double>{tot[0], tot[1]};
+                const Cx<double> q1 = Cx<double>{(rn.re * st.rho.re + rn.im * st.rho.im) / rho2,
+                                                 (rn.im * st.rho.re - rn.re * st.rho.im) / rho2};
+                const Cx<double> q2 = Cx<double>{(st.alpha.re * st.omega.re + st.alpha.im * st.omega.im) / om2,
+                                                 (st.alpha.im * st.omega.re - st.alpha.re * st.omega.im) / om2};
                 st.beta = cmul(q1, q2);
                 st.rho = rn;
                 st.rr = tot[2];
             }
         }
-    ITEM_LOOP_END
+    WARP_LOOP_END
 }
 
 // p = r + beta (p - omega v)
 template <typename S>
-__global__ void __launch_bounds__(PT_BS) k_bicg_dir(EP P) {
+__global__ void __launch_bounds__(PT_BLOCK) k_bicg_dir(EP P) {
     typedef Fld<1, S> F;
     typedef typename F::R R;
     const int N = P.g.N;
     ITEM_LOOP(LIST_INNER)
         const Slot &st = P.slots[j];
         if (st.phase != PH_INNER) continue;
-        const int idx = b * PT_BS + threadIdx.x;
-        if (idx >= N) continue;
         const Cx<R> be = Cx<R>{(R)st.beta.re, (R)st.beta.im};
         const Cx<R> om = Cx<R>{(R)st.omega.re, (R)st.omega.im};
         S *pv = slot_ptr<S>(P.pv, j, P.L);
         const S *r = slot_cptr<S>(P.r, j, P.L);
         const S *q = slot_cptr<S>(P.q, j, P.L);
-        for (int c = 0; c < 12; ++c) {
-            Cx<R> pp = csub(F::ld(pv, N, c, idx), cmul(om, F::ld(q, N, c, idx)));
-            F::st(pv, N, c, idx, cadd(F::ld(r, N, c, idx), cmul(be, pp)));
-        }
+        SITE_LOOP(1)
+            for (int c = 0; c < 12; ++c) {
+                const Cx<R> pp = csub(F::ld(pv, N, c, idx), cmul(om, F::ld(q, N, c, idx)));
+                F::st(pv, N, c, idx, cadd(F::ld(r, N, c, idx), cmul(be, pp)));
+            }
+        SITE_LOOP_END
     ITEM_LOOP_END
 }
 
 // ------------------------------------------------------------------ host driver
 struct EngineRun {
     EP P;
-    int grid_items;
+    int grid_items;        // persistent CTAs of the item kernels
+    int grid_warps;        // CTAs of the finalize kernels (8 warps each)
     int kernels_per_iter;
 };
 
-template <int KIND, typename S, typename LS>
-static void enqueue_iteration(const EngineRun &E, cudaStream_t st) {
-    const EP &P = E.P;
-    const int G = E.grid_items;
-    k_schedule<<<1, 1024, 0, st>>>(P);
-    k_contract<KIND><<<G, PT_BS, 0, st>>>(P);
-    k_outer_update<KIND, S><<<G, PT_BS, 0, st>>>(P);
-    k_outer_residual<KIND, S><<<G, PT_BS, 0, st>>>(P);
-    if constexpr (KIND == 0) {
-        k_cg_apply<S, LS><<<G, PT_BS, 0, st>>>(P);
-        k_cg_update<S><<<G, PT_BS, 0, st>>>(P);
-        k_cg_dir<S><<<G, PT_BS, 0, st>>>(P);
-    } else {
-        k_bicg_apply1<S, LS><<<G, PT_BS, 0, st>>>(P);
-        k_bicg_s<S><<<G, PT_BS, 0, st>>>(P);
-        k_bicg_apply2<S, LS><<<G, PT_BS, 0, st>>>(P);
-        k_bicg_update<S><<<G, PT_BS, 0, st>>>(P);
-        k_bicg_dir<S><<<G, PT_BS, 0, st>>>(P);
-    }
+// Events recorded around kernel groups when profiling is on (9 per iteration):
+// e0..e4 inner kernels, e5/e6 outer steps, e7/e8 whole iteration.
+#define PT_EV_PER_ITER 9
+static inline void ev_rec(const cudaEvent_t *ev, int i, cudaStream_t st) {
+    if (ev) cudaEventRecordWithFlags(ev[i], st, cudaEventRecordExternal);
 }
+
+template <int KIND, typename S, typename LS>
+static void enqueue_iteration(const EngineRun &E, cudaStream_t st, const cudaEvent_t *ev) {
+    const EP &P = E.P;
+    const int G = E.grid_items, W = E.grid_warps;
+    ev_rec(ev, 7, st);
+    k_schedule<<<1, 1024, 0, st>>>(P);
+    k_contract<KIND><<<G, PT_BLOCK, 0, st>>>(P);
+    k_fin_contract<<<W, 256, 0, st>>>(P);
+    ev_rec(ev, 5, st);
+    k_outer_update<KIND, S><<<G, PT_BLOCK, 0, st>>>(P);
+    k_outer_residual<KIND, S><<<G, PT_BLOCK, 0, st>>>(P);
+    k_fin_outer<<<W, 256, 0, st>>>(P);
+    ev_rec(ev, 6, st);
+    if constexpr (KIND == 0) {
+        ev_rec(ev, 0, st);
+        if (P.vec4) k_cg_apply_v4<S><<<G, PT_BLOCK, 0, st>>>(P);
+        else k_cg_apply<S><<<G, PT_BLOCK, 0, st>>>(P);
+        ev_rec(ev, 1, st);
+        k_fin_cg_alpha<<<W, 256, 0, st>>>(P);
+        if (P.vec4) k_cg_update_v4<S><<<G, PT_BLOCK, 0, st>>>(P);
+        else k_cg_update<S><<<G, PT_BLOCK, 0, st>>>(P);
+        k_fin_cg_beta<<<W, 256, 0, st>>>(P);
+        ev_rec(ev, 2, st);
+    } else {
+        ev_rec(ev, 0, st);
+        k_bicg_apply1<S, LS><<<G, PT_BLOCK, 0, st>>>(P);
+        ev_rec(ev, 1, st);
+        k_fin_bicg_alpha<<<W, 256, 0, st>>>(P);
+        k_bicg_s<S><<<G, PT_BLOCK, 0, st>>>(P);
+        ev_rec(ev, 2, st);
+        k_bicg_apply2<S, LS><<<G, PT_BLOCK, 0, st>>>(P);
+        ev_rec(ev, 3, st);
+        k_fin_bicg_omega<<<W, 256, 0, st>>>(P);
+        k_bicg_update<S><<<G, PT_BLOCK, 0, st>>>(P);
+        k_fin_bicg_beta<<<W, 256, 0, st>>>(P);
+        k_bicg_dir<S><<<G, PT_BLOCK, 0, st>>>(P);
+        ev_rec(ev, 4, st);
+    }
+    ev_rec(ev, 8, st);
+}
+
+// (class, start event, end event) of the timed kernel groups; class 0 = the
+// operator apply of the inner Krylov iteration, 1 = inner vector updates,
+// 2 = FP64 outer steps, 3 = whole engine iteration.
+static const int PROF_PAIRS_LAP[4][3] = {{0, 0, 1}, {1, 1, 2}, {2, 5, 6}, {3, 7, 8}};
+static const int PROF_PAIRS_WIL[6][3] = {{0, 0, 1}, {1, 1, 2}, {0, 2, 3}, {1, 3, 4}, {2, 5, 6}, {3, 7, 8}};
 
 struct EngineRequest {
     int mode;
@@ -757,12 +1037,13 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     pt_ctx *c = op->ctx;
     const Geom g = op->g;
     const int64_t L = pt_field_reals(op);
-    const int nvec = KIND ? 7 : 4;
+    const int nvec = KIND ? 7 : 5;
     const size_t per_slot = (size_t)L * (sizeof(double) + nvec * sizeof(S));
     int R = rq.R_force > 0 ? rq.R_force : (int)std::min<size_t>((size_t)rq.n_tasks, c->mem_budget / per_slot);
+    if (rq.R_force <= 0 && c->max_slots > 0) R = std::min(R, c->max_slots);
     if (R < 1) R = 1;
     if (rq.R_force <= 0) R = std::min(R, 4096);
-    const int nsb = (g.N + PT_BS - 1) / PT_BS;
+    const int nsb = (g.N + Tile<KIND>::SITES - 1) / Tile<KIND>::SITES;
     const int K_MAX = 2 * PT_MAX_P;
     // layout of the work space
     size_t off = 0;
@@ -791,6 +1072,8 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     P.kind = KIND;
     P.nsb = nsb;
     P.R = R;
+    P.gs = KIND ? 8 : 1;
+    P.vec4 = (KIND == 0 && g.D[0] % 4 == 0) ? 1 : 0;
     P.L = L;
     P.diag = 8.0 + op->m2;
     P.kappa = op->kappa;
@@ -815,6 +1098,7 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     P.X_user = rq.X_user;
     P.x64 = (double *)(base + o_x64);
     void **vp[7] = {&P.e, &P.r, &P.pv, &P.q, &P.s, &P.t, &P.r0};
+    if constexpr (KIND == 0) vp[4] = &P.p1;     // CG: e, r, p (two buffers), q
     for (int v = 0; v < nvec; ++v) *vp[v] = base + o_vec[v];
     P.slots = (Slot *)(base + o_slots);
     P.partials = (double *)(base + o_part);
@@ -844,20 +1128,27 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
 
     int occ = 0;
     if constexpr (KIND == 0) {
-        PT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_apply<S, LS>, PT_BS, 0));
+        PT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_apply<S>, PT_BLOCK, 0));
     } else {
-        PT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bicg_apply1<S, LS>, PT_BS, 0));
+        PT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bicg_apply1<S, LS>, PT_BLOCK, 0));
     }
     occ = std::max(occ, 1);
     E.grid_items = c->num_sms * occ;
-    E.kernels_per_iter = KIND ? 9 : 7;
+    E.grid_warps = std::max(1, std::min((R + 7) / 8, c->num_sms * 4));
+    E.kernels_per_iter = KIND ? 14 : 10;
 
     // capture ITERS engine iterations into one graph
     const int ITERS = 8;
+    std::vector<cudaEvent_t> evs;
+    if (c->prof) {
+        evs.resize(ITERS * PT_EV_PER_ITER);
+        for (auto &e : evs) PT_CUDA(cudaEventCreate(&e));
+    }
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     PT_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < ITERS; ++i) enqueue_iteration<KIND, S, LS>(E, c->cap_stream);
+    for (int i = 0; i < ITERS; ++i)
+        enqueue_iteration<KIND, S, LS>(E, c->cap_stream, c->prof ? &evs[(size_t)i * PT_EV_PER_ITER] : nullptr);
     cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &graph);
     if (ce != cudaSuccess) return pt_cuda_fail(ce, "cudaStreamEndCapture", __FILE__, __LINE__);
     ce = cudaGraphInstantiate(&exec, graph, 0);
@@ -870,13 +1161,26 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     int64_t launches = 0;
     int rc_loop = PT_OK;
     int *hf = c->h_flags;
+    const int (*pairs)[3] = KIND ? PROF_PAIRS_WIL : PROF_PAIRS_LAP;
+    const int n_pairs = KIND ? 6 : 4;
     while (true) {
-        ce = cudaGraphLaunch(exec, st);
+        ce = cudaGraphLaunch(exec, c->stream);
         if (ce != cudaSuccess) { rc_loop = pt_cuda_fail(ce, "cudaGraphLaunch", __FILE__, __LINE__); break; }
         ++launches;
-        ce = cudaMemcpyAsync(hf, P.flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, st);
-        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        ce = cudaMemcpyAsync(hf, P.flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
         if (ce != cudaSuccess) { rc_loop = pt_cuda_fail(ce, "engine flag read", __FILE__, __LINE__); break; }
+        if (c->prof) {
+            for (int i = 0; i < ITERS; ++i)
+                for (int q = 0; q < n_pairs; ++q) {
+                    float ms = 0.f;
+                    const cudaEvent_t *ev = &evs[(size_t)i * PT_EV_PER_ITER];
+                    if (cudaEventElapsedTime(&ms, ev[pairs[q][1]], ev[pairs[q][2]]) == cudaSuccess) {
+                        c->prof_ms[pairs[q][0]] += ms;
+                        c->prof_launches[pairs[q][0]] += 1;
+                    }
+                }
+        }
         if (hf[FLAG_DONE]) break;
         if (launches >= max_launches) {
             pt_set_error("solver engine did not finish within %lld graph launches", (long long)max_launches);
@@ -884,6 +1188,7 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
             break;
         }
     }
+    for (auto &e : evs) cudaEventDestroy(e);
     cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);
     pt_kernel_launch_count += launches * ITERS * E.kernels_per_iter;
@@ -966,7 +1271,7 @@ extern "C" int pt_solve(pt_ctx *c, const pt_op *op, const double *B_dev, double 
     PT_CHECK_ARG(B_dev && X_dev, "pt_solve: NULL field");
     PT_CUDA(cudaSetDevice(c->device));
     std::vector<Task> tasks(nrhs);
-    for (int i = 0; i < nrhs; ++i) tasks[i] = Task{i, 0, 0, 0};
+    for (int i = 0; i < nrhs; ++i) tasks[i] = Task{i, 0, 0, 0, 0, 0, 0, 0};
     EngineRequest rq;
     rq.mode = MODE_SOLVE;
     rq.n_tasks = nrhs;
@@ -992,39 +1297,44 @@ extern "C" int pt_solve(pt_ctx *c, const pt_op *op, const double *B_dev, double 
 }
 
 // ------------------------------------------------------------------ pt_trace_PAinv
-static void build_probe_tasks(int n_colours, int set0, int n_sets, int dof, int dilute, int adj_pairs,
+static void build_probe_tasks(int cidx, int n_colours, int set0, int n_sets, int dof, int dilute, int adj_pairs,
                               std::vector<Task> &tasks) {
-    tasks.clear();
     const int ncomp = dilute ? dof : 1;
     for (int s = 0; s < n_sets; ++s)
         for (int col = 0; col < n_colours; ++col)
             for (int a = 0; a < ncomp; ++a) {
-                tasks.push_back(Task{set0 + s, col, dilute ? a : -1, 0});
-                if (adj_pairs) tasks.push_back(Task{set0 + s, col, dilute ? a : -1, TASK_ADJ});
+                tasks.push_back(Task{set0 + s, col, dilute ? a : -1, 0, cidx, 0, 0, 0});
+                if (adj_pairs) tasks.push_back(Task{set0 + s, col, dilute ? a : -1, TASK_ADJ, cidx, 0, 0, 0});
             }
 }
 
-extern "C" int pt_trace_PAinv(pt_ctx *c, const pt_op *op, const int32_t *col_dev, int n_colours, int mu,
-                              const int *p_list, int n_p, int noise, uint64_t seed, int set0, int n_sets, int dilute,
-                              int prec, double tol, int maxit, double *est_out, double *mean_out, double *var_out,
-                              pt_stats *stats) {
+extern "C" int pt_trace_PAinv_multi(pt_ctx *c, const pt_op *op, int n_col, const int32_t *cols_dev,
+                                    const int *n_colours, int mu, const int *p_list, int n_p, int noise, uint64_t seed,
+                                    int set0, int n_sets, int dilute, int prec, double tol, int maxit, double *est_out,
+                                    pt_stats *stats) {
     PT_CHECK_ARG(c && op && op->ctx == c, "pt_trace_PAinv: bad context/operator");
-    PT_CHECK_ARG(col_dev && est_out, "pt_trace_PAinv: NULL colour or output array");
-    PT_CHECK_ARG(n_colours >= 1 && n_sets >= 1 && set0 >= 0, "pt_trace_PAinv: need n_colours, n_sets >= 1");
+    PT_CHECK_ARG(cols_dev && est_out && n_colours && n_col >= 1, "pt_trace_PAinv: NULL colour or output array");
+    PT_CHECK_ARG(n_sets >= 1 && set0 >= 0, "pt_trace_PAinv: need n_sets >= 1, set0 >= 0");
+    for (int i = 0; i < n_col; ++i)
+        PT_CHECK_ARG(n_colours[i] >= 1 && n_colours[i] <= op->g.N, "pt_trace_PAinv: n_colours out of range");
     PT_CHECK_ARG(mu >= 0 && mu < 4, "pt_trace_PAinv: mu must be in 0..3");
     PT_CHECK_ARG(n_p >= 1 && n_p <= PT_MAX_P && p_list, "pt_trace_PAinv: 1 <= n_p <= %d", PT_MAX_P);
     PT_CHECK_ARG(noise == PT_NOISE_Z2 || (noise == PT_NOISE_Z4 && op->dof == 12),
                  "pt_trace_PAinv: Z4 noise needs the complex (Wilson) operator");
     int rc = check_solver_args(prec, tol, maxit);
     if (rc) return rc;
+    int64_t n_tasks = 0;
+    for (int i = 0; i < n_col; ++i) n_tasks += (int64_t)n_colours[i] * n_sets * (dilute ? op->dof : 1);
+    PT_CHECK_ARG(n_tasks < (1LL << 30), "pt_trace_PAinv: too many right-hand sides");
     PT_CUDA(cudaSetDevice(c->device));
     std::vector<Task> tasks;
-    build_probe_tasks(n_colours, set0, n_sets, op->dof, dilute, 0, tasks);
+    tasks.reserve((size_t)n_tasks);
+    for (int i = 0; i < n_col; ++i) build_probe_tasks(i, n_colours[i], set0, n_sets, op->dof, dilute, 0, tasks);
     EngineRequest rq;
     rq.mode = MODE_TRACE;
     rq.n_tasks = (int)tasks.size();
     rq.h_tasks = tasks.data();
-    rq.col = col_dev;
+    rq.col = cols_dev;
     rq.seed = seed;
     rq.noise = noise; rq.mu = mu; rq.n_p = n_p; rq.dilute = dilute ? 1 : 0; rq.pshift = 0;
     rq.p_list = p_list;
@@ -1036,16 +1346,25 @@ extern "C" int pt_trace_PAinv(pt_ctx *c, const pt_op *op, const int32_t *col_dev
     rq.R_force = 0;
     rc = run_engine(op, rq, stats);
     if (rc != PT_OK && rc != PT_ERR_NOCONV) return rc;
-    // per-set sums in a fixed task order (deterministic)
-    for (int s = 0; s < n_sets; ++s)
-        for (int n = 0; n < n_p; ++n) { est_out[(s * n_p + n) * 2] = 0.0; est_out[(s * n_p + n) * 2 + 1] = 0.0; }
+    // per (colouring, set) sums in the fixed task order (deterministic)
+    for (size_t i = 0; i < (size_t)n_col * n_sets * n_p * 2; ++i) est_out[i] = 0.0;
     for (size_t t = 0; t < tasks.size(); ++t) {
-        int s = tasks[t].set - set0;
+        const size_t row = ((size_t)tasks[t].cidx * n_sets + (tasks[t].set - set0)) * n_p;
         for (int n = 0; n < n_p; ++n) {
-            est_out[(s * n_p + n) * 2] += rq.task_out[(t * n_p + n) * 2];
-            est_out[(s * n_p + n) * 2 + 1] += rq.task_out[(t * n_p + n) * 2 + 1];
+            est_out[(row + n) * 2] += rq.task_out[(t * n_p + n) * 2];
+            est_out[(row + n) * 2 + 1] += rq.task_out[(t * n_p + n) * 2 + 1];
         }
     }
+    return rc;
+}
+
+extern "C" int pt_trace_PAinv(pt_ctx *c, const pt_op *op, const int32_t *col_dev, int n_colours, int mu,
+                              const int *p_list, int n_p, int noise, uint64_t seed, int set0, int n_sets, int dilute,
+                              int prec, double tol, int maxit, double *est_out, double *mean_out, double *var_out,
+                              pt_stats *stats) {
+    int rc = pt_trace_PAinv_multi(c, op, 1, col_dev, &n_colours, mu, p_list, n_p, noise, seed, set0, n_sets, dilute,
+                                  prec, tol, maxit, est_out, stats);
+    if (rc != PT_OK && rc != PT_ERR_NOCONV) return rc;
     for (int n = 0; n < n_p; ++n) {
         double mr = 0.0, mi = 0.0;
         for (int s = 0; s < n_sets; ++s) { mr += est_out[(s * n_p + n) * 2]; mi += est_out[(s * n_p + n) * 2 + 1]; }
@@ -1172,7 +1491,7 @@ extern "C" int pt_grad(pt_ctx *c, const pt_op *op, const int32_t *col_dev, int n
         PT_CUDA(cudaMemsetAsync(Gbar_dev, 0, (size_t)N * 72 * sizeof(double), c->stream));
     }
     std::vector<Task> all;
-    build_probe_tasks(n_colours, set0, n_sets, op->dof, dilute, 1, all);
+    build_probe_tasks(0, n_colours, set0, n_sets, op->dof, dilute, 1, all);
     const int n_pairs_total = (int)all.size() / 2;
     // chunk of pairs resident at once
     const int64_t L = pt_field_reals(op);

@@ -35,10 +35,33 @@ int pt_cuda_fail(cudaError_t e, const char *what, const char *file, int line);
     } while (0)
 
 // ------------------------------------------------------------------ geometry
+// Division by a lattice extent without a hardware divide (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", PLDI
+// 1994): with l = ceil(log2 d), p = 31 + l and m = ceil(2^p / d) < 2^32,
+// floor(n / d) = floor(n m / 2^p) for every 0 <= n < 2^31.
+struct FastDiv {
+    uint32_t d, m, p;
+};
+
+static inline FastDiv make_fastdiv(uint32_t d) {
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;
+    FastDiv f;
+    f.d = d;
+    f.p = 31 + l;
+    f.m = (uint32_t)(((1ull << f.p) + d - 1) / d);
+    return f;
+}
+
+__device__ __forceinline__ int fdiv(const FastDiv &f, int n) {
+    return (int)(((uint64_t)(uint32_t)n * f.m) >> f.p);
+}
+
 struct Geom {
     int D[4];
     int stride[4];
     int N;
+    FastDiv fd[3];
 };
 
 static inline Geom make_geom(const int dims[4]) {
@@ -46,15 +69,18 @@ static inline Geom make_geom(const int dims[4]) {
     int s = 1;
     for (int mu = 0; mu < 4; ++mu) { g.D[mu] = dims[mu]; g.stride[mu] = s; s *= dims[mu]; }
     g.N = s;
+    for (int mu = 0; mu < 3; ++mu) g.fd[mu] = make_fastdiv((uint32_t)dims[mu]);
     return g;
 }
 
 __device__ __forceinline__ void site_coords(const Geom &g, int idx, int x[4]) {
-    int r = idx;
-    x[0] = r % g.D[0]; r /= g.D[0];
-    x[1] = r % g.D[1]; r /= g.D[1];
-    x[2] = r % g.D[2];
-    x[3] = r / g.D[2];
+    int q0 = fdiv(g.fd[0], idx);
+    x[0] = idx - q0 * g.D[0];
+    int q1 = fdiv(g.fd[1], q0);
+    x[1] = q0 - q1 * g.D[1];
+    int q2 = fdiv(g.fd[2], q1);
+    x[2] = q1 - q2 * g.D[2];
+    x[3] = q2;
 }
 
 __device__ __forceinline__ int nb_fwd(const Geom &g, int idx, const int x[4], int mu) {
@@ -327,6 +353,7 @@ struct pt_ctx {
     bool own_stream;
     int num_sms;
     size_t mem_budget;
+    int max_slots;           // 0: no cap on the right-hand sides in flight
     // grow-only work space
     void *ws;
     size_t ws_bytes;

@@ -54,6 +54,7 @@ _SIGS = {
     "pt_destroy": ([_P], _I),
     "pt_synchronize": ([_P], _I),
     "pt_set_memory_budget": ([_P, ctypes.c_size_t], _I),
+    "pt_set_max_slots": ([_P, _I], _I),
     "pt_profile_enable": ([_P, _I], _I),
     "pt_profile_read": ([_P, _I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_D), _I], _I),
     "pt_op_laplacian": ([_P, ctypes.POINTER(_I), _D, ctypes.POINTER(_P)], _I),
@@ -69,6 +70,8 @@ _SIGS = {
     "pt_solve": ([_P, _P, _P, _P, _I, _I, _D, _I, _P, _P, ctypes.POINTER(Stats)], _I),
     "pt_trace_PAinv": ([_P, _P, _P, _I, _I, ctypes.POINTER(_I), _I, _I, ctypes.c_uint64, _I, _I, _I, _I, _D, _I,
                         _P, _P, _P, ctypes.POINTER(Stats)], _I),
+    "pt_trace_PAinv_multi": ([_P, _P, _I, _P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _I, _I, ctypes.c_uint64,
+                              _I, _I, _I, _I, _D, _I, _P, ctypes.POINTER(Stats)], _I),
     "pt_grad": ([_P, _P, _P, _I, _I, _I, _I, ctypes.c_uint64, _I, _I, _I, _I, _D, _I, _P, _P, _P, _P,
                  ctypes.POINTER(Stats)], _I),
 }
@@ -181,6 +184,9 @@ class Context:
 
     def set_memory_budget(self, nbytes):
         _check(lib().pt_set_memory_budget(self._h, int(nbytes)))
+
+    def set_max_slots(self, n):
+        _check(lib().pt_set_max_slots(self._h, int(n)))
 
     def profile(self, on=True):
         _check(lib().pt_profile_enable(self._h, 1 if on else 0))
@@ -316,6 +322,23 @@ def trace(op, col, n_colours, mu, p_list, noise="z2", seed=0, set0=0, n_sets=1, 
                               _np_ptr(est), _np_ptr(mean), _np_ptr(var), ctypes.byref(st))
     _check(rc)
     return est, mean, var, st.as_dict()
+
+
+def trace_multi(op, cols, n_colours, mu, p_list, noise="z2", seed=0, set0=0, n_sets=1, dilute=True,
+                prec="mixed_fp32", tol=1e-10, maxit=20000):
+    """Several colourings in one batched solve.  cols: torch.int32 [n_col, N] on the
+    device; n_colours: list of ints.  Returns (est[n_col, n_sets, n_p], stats)."""
+    n_col = len(n_colours)
+    assert cols.shape[0] == n_col and cols.is_contiguous()
+    n_p = len(p_list)
+    est = np.zeros((n_col, n_sets, n_p), dtype=np.complex128)
+    st = Stats()
+    rc = lib().pt_trace_PAinv_multi(op.ctx.handle, op._h, n_col, _ptr(cols), _ints(n_colours), int(mu),
+                                    _ints(p_list), n_p, NOISE[noise] if isinstance(noise, str) else int(noise),
+                                    int(seed), int(set0), int(n_sets), 1 if dilute else 0, PREC[prec], float(tol),
+                                    int(maxit), _np_ptr(est), ctypes.byref(st))
+    _check(rc)
+    return est, st.as_dict()
 
 
 def grad(op, col, n_colours, mu, p, noise="z2", seed=0, set0=0, n_sets=1, dilute=True, prec="mixed_fp32",

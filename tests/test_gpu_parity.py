@@ -191,6 +191,19 @@ def test_trace_4to4_laplacian(pt, ctx, k, prec):
     assert np.allclose(var, OE.sample_variance(want), rtol=1e-6, atol=1e-9)
 
 
+@pytest.mark.parametrize("dims", [[5, 4, 3, 6], [6, 2, 4, 3]])
+def test_trace_ragged_laplacian(pt, ctx, dims):
+    """Extents that are not multiples of 4 take the one-site kernels (the 16^4
+    lattice takes the four-site kernels); both must match the oracle."""
+    m2, p = 0.2, 2
+    colv, m = greedy_colour(dims, 2, [p], 1, 1)
+    op = pt.laplacian(ctx, dims, m2)
+    for prec in ("fp64", "mixed_fp32", "mixed_bf16"):
+        est, _, _, st = pt.trace(op, _t(colv), m, 2, [0, p], "z2", 9, 0, 3, True, prec, 1e-11, 5000)
+        want = OE.probed_estimates(OE.Laplacian(dims, m2), colv, m, 9, 3, 0, 2, [0, p], 1e-13)
+        assert np.allclose(est, want, rtol=1e-8, atol=1e-9), prec
+
+
 def test_hutchinson_64_vectors_4to4(pt, ctx):
     dims, m2 = [4, 4, 4, 4], 0.1
     op = pt.laplacian(ctx, dims, m2)
