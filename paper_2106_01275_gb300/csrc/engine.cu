@@ -204,11 +204,60 @@ __device__ __forceinline__ void item_store(const EP &P, int j, int b, double v[K
 // FP32 / BF16 inner solves: the FP64 pipe of GB300 is too narrow for a
 // per-site FP64 sum), widened to FP64 for the block and slot reductions
 template <int K, typename R>
-__device__ __forceinline__ void item_store_r(const EP &P, int j, int b, const R vr[K], double *sh) {
-    double v[K];
+__device__ __forceinline__ void item_store_r(const EP &P, int j, int b, R vr[K], double *sh) {
+    if constexpr (std::is_same<R, double>::value) {
+        item_store<K>(P, j, b, vr, sh);
+    } else {
+        // warp tree in R, then the (at most 32) warp sums added in FP64 in a fixed order
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = (double)vr[k];
-    item_store<K>(P, j, b, v, sh);
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) vr[k] += __shfl_down_sync(0xffffffffu, vr[k], o);
+        __syncthreads();
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < K; ++k) sh[warp * K + k] = (double)vr[k];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double *dst = P.partials + ((size_t)j * P.nsb + b) * K;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                double s = 0.0;
+                for (int w = 0; w < nw; ++w) s += sh[w * K + k];
+                dst[k] = s;
+            }
+        }
+    }
+}
+
+// contraction partials: only the first K = 2 n_p of the 2 PT_MAX_P entries are
+// reduced (FP64 throughout: these are the trace accumulations); the rest are zero
+__device__ __forceinline__ void item_store_contract(const EP &P, int j, int b, double acc[2 * PT_MAX_P], int K,
+                                                    double *sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < 2 * PT_MAX_P; ++k) {
+        if (k < K) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+        }
+    }
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 2 * PT_MAX_P; ++k)
+            if (k < K) sh[warp * 2 * PT_MAX_P + k] = acc[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double *dst = P.partials + ((size_t)j * P.nsb + b) * 2 * PT_MAX_P;
+        for (int k = 0; k < 2 * PT_MAX_P; ++k) {
+            double s = 0.0;
+            if (k < K)
+                for (int w = 0; w < nw; ++w) s += sh[w * 2 * PT_MAX_P + k];
+            dst[k] = s;
+        }
+    }
 }
 
 #define WARP_LOOP(LIST)                                                         \
@@ -372,7 +421,7 @@ __global__ void __launch_bounds__(PT_BLOCK) k_contract(EP P) {
                 }
             }
         SITE_LOOP_END
-        item_store<2 * PT_MAX_P>(P, j, b, acc, sh);
+        item_store_contract(P, j, b, acc, 2 * P.n_p, sh);
     ITEM_LOOP_END
 }
 
