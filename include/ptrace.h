@@ -173,6 +173,27 @@ PT_API int pt_colour(pt_ctx *ctx, const int dims[4], int mu, const int *p_list, 
 PT_API int pt_colour_conflicts(pt_ctx *ctx, const int dims[4], int mu, const int *p_list, int n_p,
                         int k, const int32_t *col_dev, int64_t *n_conflicts);
 
+/* Allocation-free form of pt_colour_conflicts (the paper has no counterpart:
+ * this is a service for callers that cannot allocate device memory, such as
+ * a host program whose own pool allocator owns the device memory, a caller
+ * that cannot afford the device-wide synchronisation of cudaMalloc/cudaFree,
+ * or one running under a fixed device-memory cap).  Same result as
+ * pt_colour_conflicts, without a context: it runs on the calling thread's
+ * current device and on `stream` (a cudaStream_t; NULL = the default stream).
+ * Scratch is a file-scope device array of the library: at most 16384 stencil
+ * offsets (larger stencils return PT_ERR_ARG) and one counter, 256 KiB in
+ * total, held by every device that loads the library until the process
+ * exits.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Calls neither allocate nor free device memory.  Every call shares the
+ * array, which keeps the last call's contents; the call clears its counter
+ * itself.  Calls are serialised inside the process and each one finishes on
+ * the GPU before it returns; work that another caller enqueues to use this
+ * array concurrently would race with it.  *n_conflicts is host.
+ * Synchronises `stream`. */
+PT_API int pt_colour_conflicts_noalloc(void *stream, const int dims[4], int mu, const int *p_list, int n_p,
+                                       int k, const int32_t *col_dev, int64_t *n_conflicts);
+
 /* ------------------------------------------------------------------- probes */
 
 /* Materialise one probing vector (Eq. (3) with the noise of Eq. (5) and the

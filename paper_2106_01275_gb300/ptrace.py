@@ -66,6 +66,8 @@ _SIGS = {
     "pt_colour": ([_P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _I, _I, _I, _P, ctypes.POINTER(_I)], _I),
     "pt_colour_conflicts": ([_P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _I, _I, _P,
                              ctypes.POINTER(ctypes.c_int64)], _I),
+    "pt_colour_conflicts_noalloc": ([_P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _I, _I, _P,
+                                     ctypes.POINTER(ctypes.c_int64)], _I),
     "pt_make_probes": ([_P, _P, ctypes.c_int64, _I, _I, ctypes.c_uint64, _I, _I, _I, _P], _I),
     "pt_solve": ([_P, _P, _P, _P, _I, _I, _D, _I, _P, _P, ctypes.POINTER(Stats)], _I),
     "pt_trace_PAinv": ([_P, _P, _P, _I, _I, ctypes.POINTER(_I), _I, _I, ctypes.c_uint64, _I, _I, _I, _I, _D, _I,
@@ -278,6 +280,20 @@ def conflicts(ctx, dims, mu, p_list, k, col):
     n = ctypes.c_int64()
     _check(lib().pt_colour_conflicts(ctx.handle, _ints(dims), mu, _ints(p_list), len(p_list), k, _ptr(col),
                                      ctypes.byref(n)))
+    return n.value
+
+
+def conflicts_noalloc(dims, mu, p_list, k, col, stream=None):
+    """Allocation-free conflict count (pt_colour_conflicts_noalloc): no context,
+    no device allocation; runs on the current device and `stream` (default:
+    torch's current stream)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    n = ctypes.c_int64()
+    _check(lib().pt_colour_conflicts_noalloc(ctypes.c_void_p(handle), _ints(dims), int(mu), _ints(p_list),
+                                             len(p_list), int(k), _ptr(col), ctypes.byref(n)))
     return n.value
 
 
