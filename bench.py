@@ -47,6 +47,11 @@ METRIC = "time to Tr(PA^-1) at fixed sigma; stencil site*RHS/s & HBM %; mixed vs
 # FP32 stencil apply of the inner CG, fused with the direction update
 # p_i = r + beta p_{i-1}: read r and p_{i-1}, write p_i and q = A p_i (4 B each)
 APPLY_BYTES_PER_SITE_RHS = 16
+# DRAM bytes (read + write) per site*RHS of k_cg_apply_v4<float> from one ncu
+# capture of the small case (238 RHS, all active: 125.5 MB + 85.8 MB per
+# launch; profiles/k_cg_apply_v4_lap16_small.md).  Set to None whenever the
+# kernel changes until it is captured again.
+APPLY_NCU_TRAFFIC_PER_SITE_RHS = (125.515008e6 + 85.80608e6) / (238 * 65536)
 
 
 def peaks():
@@ -201,7 +206,11 @@ def run_ours(args):
     roofline = {"bound": "hbm", "kernel": "k_cg_apply<float> (FP32 p update + stencil apply + p.q dot)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
-                "traffic": None, "algorithmic_bytes_per_site_rhs": APPLY_BYTES_PER_SITE_RHS,
+                "traffic": (APPLY_NCU_TRAFFIC_PER_SITE_RHS * inner_iters * N / apply_launches
+                            if APPLY_NCU_TRAFFIC_PER_SITE_RHS and apply_launches else None),
+                "traffic_source": "ncu dram read+write of the apply kernel on the 238-RHS case, "
+                                  "scaled per site*RHS to the average launch",
+                "algorithmic_bytes_per_site_rhs": APPLY_BYTES_PER_SITE_RHS,
                 "launches": apply_launches, "apply_ms_total": apply_ms,
                 "apply_share_of_step": apply_ms / t_ms if t_ms else None}
 
