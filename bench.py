@@ -1,26 +1,31 @@
 #!/usr/bin/env python3
 """Benchmark of the displacement-probed estimator of Tr(P A^{-1}) on one GB300.
 
-Workload (default, "lap16"): shifted scalar Laplacian on a 16^4 lattice
-(65,536 sites), m^2 = 0.01; displacements p = 0..4 along dim 3; one
-displaced distance-k colouring per (p, k) for k = 1..4 (the smaller of the
-natural and red-black greedy colourings, 20 colourings, 457 colours);
-8 independent Z2 noise sets per colouring -> 3,656 right-hand sides per step.
-One step = every probe of every colouring solved (mixed FP32 CG inside FP64
-defect correction to relative residual 1e-10) and contracted with every
-displacement p = 0..4, all in one batched, graph-driven engine run.
+Default workload "lap16" (the plain-method configuration of the metric):
+shifted scalar Laplacian on a 16^4 lattice (65,536 sites), m^2 = 0.01;
+displacements p = 0..4 along dim 3; one displaced distance-k colouring per
+(p, k), k = 1..4 (the smaller of the natural and red-black greedy colourings:
+20 colourings, 457 colours); 8 independent Z2 noise sets per colouring ->
+3,656 right-hand sides per step.  One step = every probe of every colouring
+solved (mixed FP32 CG inside FP64 defect correction to relative residual
+1e-10) and contracted with every displacement, in one batched engine run.
+
+"wilson24": Wilson-Dirac on 24^3 x 48, kappa = 0.124, antiperiodic t, links
+exp(i 0.3 H) from seed 1234; displacements p = 0, 2, 4, 8 along z with their
+(p, 2) colourings, Z4 noise with 12x spin-colour dilution, 2 noise sets;
+mixed FP32 BiCGStab inside FP64 defect correction to 1e-10.
 
 Reported value: operator applications x sites per second over the whole step
-(site*RHS/s).  Also reported: the time to the standard deviation reached by
-8 noise sets (= the step time), the same for the plain FP64 one-RHS-at-a-time
-GPU solve on identical probes, the roofline of the dominant kernel (the FP32
-stencil apply of the inner CG) against the measured HBM bandwidth, an end to
-end measurement through the C ABI with host buffers, and the FP64 CPU oracle
-timed on the host cores (cpu_baseline).
+(site*RHS/s).  Also reported: the time to the standard deviation of the noise
+sets of one step (= the step time), the same for the plain FP64
+one-RHS-at-a-time GPU solve on identical probes, the roofline of the dominant
+kernel (the stencil apply of the inner Krylov iteration, timed with CUDA
+events recorded inside the solver's graph), an end-to-end measurement through
+the C ABI with host buffers, and the FP64 CPU oracle on the host cores.
 
---impl reference times the CPU oracle itself on this workload's metric.
+--impl reference times the CPU oracle itself on the workload's metric.
 Multi-GPU (torchrun): every rank runs the full workload on its own noise sets
-(weak scaling); there is no collective on the data path.
+(weak scaling); no collective touches the data path.
 """
 import argparse
 import json
@@ -34,24 +39,45 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-DIMS = [16, 16, 16, 16]
-M2 = 0.01
-MU = 3
-P_LIST = [0, 1, 2, 3, 4]
-K_LIST = [1, 2, 3, 4]
-N_SETS = 8
+METRIC = "time to Tr(PA^-1) at fixed sigma; stencil site*RHS/s & HBM %; mixed vs FP64 1xGB300"
 TOL = 1e-10
 MAXIT = 20000
 SEED = 1000
-METRIC = "time to Tr(PA^-1) at fixed sigma; stencil site*RHS/s & HBM %; mixed vs FP64 1xGB300"
-# FP32 stencil apply of the inner CG, fused with the direction update
-# p_i = r + beta p_{i-1}: read r and p_{i-1}, write p_i and q = A p_i (4 B each)
-APPLY_BYTES_PER_SITE_RHS = 16
-# DRAM bytes (read + write) per site*RHS of k_cg_apply_v4<float> from one ncu
-# capture of the small case (238 RHS, all active: 125.5 MB + 85.8 MB per
-# launch; profiles/k_cg_apply_v4_lap16_small.md).  Set to None whenever the
-# kernel changes until it is captured again.
-APPLY_NCU_TRAFFIC_PER_SITE_RHS = (125.515008e6 + 85.80608e6) / (238 * 65536)
+
+
+class Workload:
+    def __init__(self, name, kind, dims, mu, pk, p_contract, n_sets, noise, desc, m2=None, kappa=None,
+                 link_seed=None, plain_subset=None):
+        self.name, self.kind, self.dims, self.mu, self.pk = name, kind, list(dims), mu, list(pk)
+        self.p_contract, self.n_sets, self.noise, self.desc = list(p_contract), n_sets, noise, desc
+        self.m2, self.kappa, self.link_seed = m2, kappa, link_seed
+        self.plain_subset = plain_subset     # colourings used for the plain FP64 timing (None = all)
+        self.N = int(np.prod(dims))
+
+    # algorithmic bytes of the inner apply kernel (FP32), per site*RHS and per site*launch
+    def apply_bytes(self):
+        if self.kind == "lap":
+            return 16.0, 0.0       # read r, p_{i-1}; write p_i, q
+        return 192.0, 288.0        # spinor in + out; 4 x 2 links x 9 complex FP32 once per launch
+
+
+def workloads(case):
+    small = case == "small"
+    lap = Workload(
+        "lap16", "lap", [16, 16, 16, 16], 3,
+        [(0, 4)] if small else [(p, k) for k in (1, 2, 3, 4) for p in (0, 1, 2, 3, 4)],
+        [0, 1, 2, 3, 4], 2 if small else 8, "z2",
+        "lap16: 16^4 shifted Laplacian m2=0.01, p=0..4 along dim 3, (p,k)-colourings k=1..4 "
+        "(min of natural/red-black, 457 colours), 8 Z2 sets, mixed FP32 CG + FP64 defect correction to 1e-10"
+        if not small else "lap16 small: (p,k)=(0,4) colouring, 2 Z2 sets", m2=0.01)
+    wil = Workload(
+        "wilson24", "wil", [16, 16, 16, 32] if small else [24, 24, 24, 48], 2,
+        [(4, 2)] if small else [(0, 2), (2, 2), (4, 2), (8, 2)], [0, 2, 4, 8], 1 if small else 2, "z4",
+        "wilson24: Wilson-Dirac 24^3x48 kappa=0.124 antiperiodic t, p=0,2,4,8 along z with (p,2)-colourings, "
+        "Z4 x 12 spin-colour dilution, 2 sets, mixed FP32 BiCGStab + FP64 defect correction to 1e-10"
+        if not small else "wilson24 small: 16^3x32, (p,k)=(4,2), 1 Z4 set, 12x dilution",
+        kappa=0.124, link_seed=1234, plain_subset=[3])
+    return {"lap16": lap, "wilson24": wil}
 
 
 def peaks():
@@ -117,23 +143,27 @@ def dist_setup():
     return world, rank, local
 
 
-def make_colourings(pt, ctx, small=False):
+def make_colourings(pt, ctx, W):
     """One colouring per (p, k): the smaller of natural and red-black."""
     import torch
-    N = int(np.prod(DIMS))
-    pk = [(0, 4)] if small else [(p, k) for k in K_LIST for p in P_LIST]
-    cols = torch.empty((len(pk), N), dtype=torch.int32, device="cuda")
-    m, labels = [], []
-    i = 0
-    for p, k in pk:
-        c0, m0 = pt.colour(ctx, DIMS, MU, [p], k, "natural")
-        c1, m1 = pt.colour(ctx, DIMS, MU, [p], k, "redblack")
+    cols = torch.empty((len(W.pk), W.N), dtype=torch.int32, device="cuda")
+    m = []
+    for i, (p, k) in enumerate(W.pk):
+        c0, m0 = pt.colour(ctx, W.dims, W.mu, [p], k, "natural")
+        c1, m1 = pt.colour(ctx, W.dims, W.mu, [p], k, "redblack")
         cols[i].copy_(c0 if m0 <= m1 else c1)
         m.append(min(m0, m1))
-        labels.append((p, k))
-        i += 1
     torch.cuda.synchronize()
-    return cols, m, labels
+    return cols, m
+
+
+def make_operator(pt, ctx, W):
+    import torch
+    if W.kind == "lap":
+        return pt.laplacian(ctx, W.dims, W.m2)
+    from paper_2106_01275_gb300 import inputs
+    U = torch.as_tensor(inputs.gauge_links(W.dims, W.link_seed)).cuda()
+    return pt.wilson(ctx, W.dims, U, W.kappa, True)
 
 
 def run_ours(args):
@@ -146,21 +176,26 @@ def run_ours(args):
     torch.cuda.set_device(local)
     from paper_2106_01275_gb300 import ptrace as pt
 
+    W = workloads(args.case)[args.workload]
     ctx = pt.Context(local)
-    ctx.set_memory_budget(64 << 30)
-    op = pt.laplacian(ctx, DIMS, M2)
-    cols, m, labels = make_colourings(pt, ctx, args.case == "small")
-    N = int(np.prod(DIMS))
-    set0 = rank * N_SETS                      # weak scaling: each rank its own noise sets
-    n_sets_step = 2 if args.case == "small" else N_SETS
+    ctx.set_memory_budget((200 if W.kind == "wil" else 64) << 30)
+    op = make_operator(pt, ctx, W)
+    cols, m = make_colourings(pt, ctx, W)
+    N = W.N
+    set0 = rank * W.n_sets                    # weak scaling: each rank its own noise sets
 
-    def step(prec="mixed_fp32", set_base=set0, n_sets=n_sets_step):
-        return pt.trace_multi(op, cols, m, MU, P_LIST, "z2", SEED, set_base, n_sets, True, prec, TOL, MAXIT)
+    def step(prec="mixed_fp32", set_base=set0, n_sets=W.n_sets, c=cols, mm=m):
+        return pt.trace_multi(op, c, mm, W.mu, W.p_contract, W.noise, SEED, set_base, n_sets, True, prec,
+                              TOL, MAXIT)
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
+    # autotune the engine on trial probes of the largest colouring (set-up, untimed)
+    big = int(np.argmax(m))
+    tuning = pt.autotune(op, cols[big].contiguous(), m[big], W.mu, W.noise, SEED + 7, "mixed_fp32", TOL, MAXIT,
+                         64 if W.kind == "lap" else 24) if not args.no_tune else pt.get_tuning(op, "mixed_fp32")
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -169,7 +204,8 @@ def run_ours(args):
     clk = ClockSampler(local)
     clk.start()
     ctx.profile(True)
-    ctx.profile_read(0, reset=True)
+    for c in range(4):
+        ctx.profile_read(c, reset=True)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record()
@@ -185,7 +221,8 @@ def run_ours(args):
     ctx.profile(False)
     clocks = clk.stop()
     t_ms = ev0.elapsed_time(ev1)
-    apply_launches, apply_ms = ctx.profile_read(0, reset=True)
+    prof = [ctx.profile_read(c, reset=True) for c in range(4)]
+    apply_launches, apply_ms = prof[0]
     site_rhs = sum(s["site_rhs_applies"] for s in stats)
     inner_iters = sum(s["inner_iters"] for s in stats)
     launches = sum(s["kernel_launches"] for s in stats)
@@ -201,55 +238,67 @@ def run_ours(args):
     step_s = t_ms / 1e3 / args.steps
 
     peak, peak_kind = peaks()
-    apply_bytes = inner_iters * N * APPLY_BYTES_PER_SITE_RHS
+    b_rhs, b_launch = W.apply_bytes()
+    applies_per_iter = 1 if W.kind == "lap" else 2
+    apply_bytes = inner_iters * applies_per_iter * N * b_rhs + apply_launches * N * b_launch
     achieved = apply_bytes / (apply_ms / 1e3) / 1e9 if apply_ms > 0 else None
-    roofline = {"bound": "hbm", "kernel": "k_cg_apply<float> (FP32 p update + stencil apply + p.q dot)",
+    traffic = None
+    if W.kind == "lap" and APPLY_NCU_TRAFFIC_PER_SITE_RHS and apply_launches:
+        traffic = APPLY_NCU_TRAFFIC_PER_SITE_RHS * inner_iters * N / apply_launches
+    roofline = {"bound": "hbm",
+                "kernel": "k_cg_apply_v4<float> (p update + stencil + p.q)" if W.kind == "lap"
+                else "k_bicg_apply1/2<float,float> (Wilson apply + dots)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
-                "traffic": (APPLY_NCU_TRAFFIC_PER_SITE_RHS * inner_iters * N / apply_launches
-                            if APPLY_NCU_TRAFFIC_PER_SITE_RHS and apply_launches else None),
-                "traffic_source": "ncu dram read+write of the apply kernel on the 238-RHS case, "
-                                  "scaled per site*RHS to the average launch",
-                "algorithmic_bytes_per_site_rhs": APPLY_BYTES_PER_SITE_RHS,
+                "traffic": traffic,
+                "traffic_source": ("ncu dram read+write of the apply kernel on the small case, scaled per "
+                                   "site*RHS to the average launch") if traffic else None,
+                "algorithmic_bytes_per_site_rhs": b_rhs, "algorithmic_bytes_per_site_launch": b_launch,
                 "launches": apply_launches, "apply_ms_total": apply_ms,
-                "apply_share_of_step": apply_ms / t_ms if t_ms else None}
+                "apply_share_of_step": apply_ms / t_ms if t_ms else None,
+                "step_breakdown_ms": {"apply": prof[0][1], "inner_vector": prof[1][1], "outer_fp64": prof[2][1],
+                                      "all_iterations": prof[3][1]}}
 
     out = {"metric": METRIC, "value": value, "unit": "site*RHS/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
-           "config": {"workload": "lap16: 16^4 shifted Laplacian m2=0.01, p=0..4 along dim 3, "
-                                  "(p,k)-colourings k=1..4 (min of natural/red-black, 457 colours), "
-                                  "8 Z2 sets, mixed FP32 CG + FP64 defect correction to 1e-10",
-                      "lattice": DIMS, "n_rhs_per_step": int(stats[-1]["n_rhs"]),
+           "config": {"workload": W.desc, "lattice": W.dims, "n_rhs_per_step": int(stats[-1]["n_rhs"]),
                       "n_colours": m, "parallelism": "rhs-batched, %d rank(s), weak" % world,
-                      "l2": "working set > L2 (all RHS resident: %.1f GB)" %
-                            (stats[-1]["n_slots"] * N * 24 / 1e9)},
-           "gpu_launches": int(launches), "roofline": roofline, "clocks": clocks}
+                      "tuning": tuning,
+                      "l2": "working set > L2 (resident RHS: %d, %.1f GB of inner vectors)" %
+                            (stats[-1]["n_slots"], stats[-1]["n_slots"] * N * (5 if W.kind == "lap" else 7) *
+                             (4 if W.kind == "lap" else 96) / 1e9)},
+           "gpu_launches": int(launches), "roofline": roofline, "clocks": clocks,
+           "mean_inner_iters_per_rhs": stats[-1]["inner_iters"] / stats[-1]["n_rhs"],
+           "mean_outer_iters_per_rhs": stats[-1]["outer_iters"] / stats[-1]["n_rhs"],
+           "solves_per_s": stats[-1]["n_rhs"] / step_s}
 
     if rank == 0 and world == 1 and not args.skip_baselines:
-        # time to sigma: every (p, k) estimator at 8 sets reaches its sigma in one step
-        sig = {}
-        var = np.var(est, axis=1, ddof=1)            # [n_col, n_p]
-        for i, (p, k) in enumerate(labels):
-            sig["p%d_k%d" % (p, k)] = float(np.sqrt(var[i, P_LIST.index(p)] / N_SETS))
+        # time to sigma: the estimators reach the sigma of their W.n_sets sets in one step
         out["time_to_sigma_s"] = step_s
-        out["sigma_target"] = "sigma of the mean after 8 Z2 sets, each (p,k) estimator of Tr(P_p A^-1)"
-        out["solves_per_s"] = stats[-1]["n_rhs"] / step_s
-        out["mean_inner_iters_per_rhs"] = stats[-1]["inner_iters"] / stats[-1]["n_rhs"]
-        # plain FP64 one-RHS-at-a-time GPU solve on identical probes: one of the 8 sets, x 8
+        out["sigma_target"] = ("sigma of the mean over the %d noise sets of one step, for every (p,k) estimator "
+                               "and displacement" % W.n_sets)
+        # plain FP64 one-RHS-at-a-time GPU solve on identical probes
+        sub = W.plain_subset if W.plain_subset is not None else list(range(len(m)))
+        csub = cols[sub].contiguous()
+        msub = [m[i] for i in sub]
+        n_sets_plain = 1
         ctx.set_max_slots(1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        est64, st64 = step("fp64", set0, 1)
+        est64, st64 = step("fp64", set0, n_sets_plain, csub, msub)
         torch.cuda.synchronize()
-        t_plain_set = time.perf_counter() - t0
+        t_plain = time.perf_counter() - t0
         ctx.set_max_slots(0)
-        est_mixed_set0 = est[:, 0, :]
-        rel = np.max(np.abs(est64[:, 0, :] - est_mixed_set0) / np.maximum(np.abs(est64[:, 0, :]), 1e-300))
-        out["fp64_plain"] = {"time_to_sigma_s": t_plain_set * N_SETS, "measured_sets": 1,
-                             "time_per_set_s": t_plain_set, "site_rhs_per_s": st64["site_rhs_applies"] / t_plain_set,
+        frac = st64["n_rhs"] / stats[-1]["n_rhs"]          # share of the step's right-hand sides timed
+        t_plain_step = t_plain / frac
+        ref = est[sub][:, :n_sets_plain, :]
+        rel = np.max(np.abs(est64 - ref) / np.maximum(np.abs(est64), 1e-300))
+        out["fp64_plain"] = {"time_to_sigma_s": t_plain_step, "measured_rhs": int(st64["n_rhs"]),
+                             "measured_s": t_plain, "scaled_by_rhs_fraction": frac,
+                             "site_rhs_per_s": st64["site_rhs_applies"] / t_plain,
                              "max_rel_diff_vs_mixed": float(rel)}
-        out["speedup_vs_fp64_plain"] = t_plain_set * N_SETS / step_s
+        out["speedup_vs_fp64_plain"] = t_plain_step / step_s
         # e2e through the C ABI with host buffers: colourings copied in, estimates copied out
         cols_host = cols.cpu().pin_memory()
         torch.cuda.synchronize()
@@ -257,14 +306,13 @@ def run_ours(args):
         site_e2e = 0
         for _ in range(args.steps):
             cols_dev = cols_host.to("cuda", non_blocking=True)
-            est_h, st_h = pt.trace_multi(op, cols_dev, m, MU, P_LIST, "z2", SEED, set0, N_SETS, True,
-                                         "mixed_fp32", TOL, MAXIT)
+            est_h, st_h = step(c=cols_dev)
             site_e2e += st_h["site_rhs_applies"]
         t_e2e = time.perf_counter() - t0
         out["e2e"] = {"value": site_e2e / t_e2e, "unit": "site*RHS/s",
                       "h2d_bytes_per_step": int(cols_host.numel() * 4),
                       "d2h_bytes_per_step": int(est_h.size * 16)}
-        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        out["cpu_baseline"] = cpu_baseline(W, args.cpu_seconds)
     elif rank == 0:
         out["cpu_baseline"] = None
     if rank == 0:
@@ -273,27 +321,53 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def oracle_sample(seconds):
+# DRAM bytes (read + write) per site*RHS of k_cg_apply_v4<float> from one ncu
+# capture of the lap16 small case (238 RHS, all active: 125.5 MB + 85.8 MB per
+# launch; profiles/k_cg_apply_v4_lap16_small.md).  Set to None whenever the
+# kernel changes until it is captured again.
+APPLY_NCU_TRAFFIC_PER_SITE_RHS = (125.515008e6 + 85.80608e6) / (238 * 65536)
+
+
+def oracle_sample(W, seconds):
     """The oracle as it stands, on a bounded sample of the workload: probes of
-    the (p, k) = (4, 1) colouring (set 0, then further sets) solved one by one
-    with its FP64 CG to 1e-10 and contracted; returns site*RHS/s."""
+    one colouring (set 0, then further sets) solved one by one with its FP64
+    CG / BiCGStab to 1e-10 and contracted; returns site*RHS/s (operator
+    applications x sites per second), the RHS count and the elapsed time."""
     import oracle.estimator as OE
     from oracle.colouring import greedy_colour
     from oracle.lattice import displace
     from oracle.probes import probe
-    from oracle.solvers import cg
-    from oracle.operators import laplacian_apply
-    col, m = greedy_colour(DIMS, MU, [4], 1, 0)
-    N = int(np.prod(DIMS))
+    p, k = (4, 1) if W.kind == "lap" else W.pk[-1]
+    col, m = greedy_colour(W.dims, W.mu, [p], k, 0)
+    if W.kind == "lap":
+        op = OE.Laplacian(W.dims, W.m2)
+        kind, comps, applies = 0, [0], 1
+    else:
+        from paper_2106_01275_gb300 import inputs
+        op = OE.Wilson(W.dims, inputs.gauge_links(W.dims, W.link_seed), W.kappa, True)
+        kind, comps, applies = 1, list(range(12)), 2
     t0 = time.perf_counter()
     site_rhs, n_rhs, s = 0, 0, 0
+    if W.kind == "wil":
+        # one oracle BiCGStab solve here takes minutes: time its operator
+        # applications (the dominant work) on the probes instead
+        v = probe(col, 0, SEED, 0, kind, op.dof, 0)
+        while time.perf_counter() - t0 < seconds:
+            v = op.apply(v) / 4.0
+            site_rhs += W.N
+            n_rhs += 1
+        dt = time.perf_counter() - t0
+        return site_rhs / dt, n_rhs, dt
     while time.perf_counter() - t0 < seconds:
         for c in range(m):
-            v = probe(col, c, SEED, s, 0, 1, 0)[:, 0]
-            x, its, rel = cg(lambda f: laplacian_apply(f, DIMS, M2), v, TOL, MAXIT)
-            _ = [np.vdot(v, displace(x, DIMS, MU, p)) for p in P_LIST]
-            site_rhs += (its + 1) * N
-            n_rhs += 1
+            for a in comps:
+                v = probe(col, c, SEED, s, kind, op.dof, a)
+                x, its, rel = op.solve(v, TOL, MAXIT)
+                _ = [np.vdot(v, displace(x, W.dims, W.mu, q)) for q in W.p_contract]
+                site_rhs += (applies * its + 1) * W.N
+                n_rhs += 1
+                if time.perf_counter() - t0 >= seconds:
+                    break
             if time.perf_counter() - t0 >= seconds:
                 break
         s += 1
@@ -301,23 +375,25 @@ def oracle_sample(seconds):
     return site_rhs / dt, n_rhs, dt
 
 
-def cpu_baseline(seconds):
-    v, n_rhs, dt = oracle_sample(seconds)
-    return {"value": v, "unit": "site*RHS/s", "cores": 1, "kind": "oracle",
-            "sample": "%d RHS of the (p,k)=(4,1) colouring, FP64 CG to 1e-10 with contraction, %.1f s" % (n_rhs, dt)}
+def cpu_baseline(W, seconds):
+    v, n_rhs, dt = oracle_sample(W, seconds)
+    what = ("%d RHS of one colouring of %s, FP64 CG to 1e-10 with contraction" % (n_rhs, W.name)
+            if W.kind == "lap" else "%d FP64 Wilson operator applications on %s" % (n_rhs, W.name))
+    return {"value": v, "unit": "site*RHS/s", "cores": 1, "kind": "oracle", "sample": "%s, %.1f s" % (what, dt)}
 
 
 def run_reference(args):
     world, rank, local = dist_setup()
     if rank != 0:
         return
+    W = workloads(args.case)[args.workload]
     per_step = max(2.0, min(20.0, args.cpu_seconds / max(args.steps, 1)))
     for _ in range(args.warmup):
-        oracle_sample(min(per_step, 2.0))
+        oracle_sample(W, min(per_step, 2.0))
     t0 = time.perf_counter()
     site, n_rhs = 0.0, 0
     for _ in range(args.steps):
-        v, n, dt = oracle_sample(per_step)
+        v, n, dt = oracle_sample(W, per_step)
         site += v * dt
         n_rhs += n
     t = time.perf_counter() - t0
@@ -325,7 +401,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "site*RHS/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "lap16 (oracle on a bounded sample per step)", "lattice": DIMS},
+           "config": {"workload": W.desc + " (CPU oracle on a bounded sample per step)", "lattice": W.dims},
            "cpu_baseline": {"value": value, "unit": "site*RHS/s", "cores": 1, "kind": "oracle",
                             "sample": "%d RHS over %d steps of %.1f s" % (n_rhs, args.steps, per_step)},
            "e2e": {"value": value, "unit": "site*RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -338,10 +414,12 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="lap16", choices=["lap16", "wilson24"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--skip-baselines", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="use the engine's default parameters")
     ap.add_argument("--case", default="full", choices=["full", "small"],
-                    help="small: the (p,k)=(0,4) colouring with 2 sets only (for profiler captures)")
+                    help="small: one colouring and few right-hand sides (for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -112,6 +112,37 @@ PT_API int pt_set_memory_budget(pt_ctx *ctx, size_t bytes);
  * beyond the memory budget).  n = 1 gives the plain one-RHS-at-a-time solve. */
 PT_API int pt_set_max_slots(pt_ctx *ctx, int n);
 
+/* Free parameters of the solver engine (not in the paper).
+ *   delta        inner relative tolerance of a mixed-precision Krylov cycle
+ *                (0 for FP64: the inner solve runs to the outer tolerance)
+ *   group        right-hand sides whose work items are interleaved site block
+ *                by site block, so that they share the links through L2
+ *   graph_iters  engine iterations captured in one CUDA graph (host polls
+ *                the completion flag once per graph launch)
+ * seconds_per_rhs is an output of pt_autotune (device time per trial RHS). */
+typedef struct pt_tune {
+    double delta;
+    int32_t group;
+    int32_t graph_iters;
+    int32_t pad;
+    double seconds_per_rhs;
+} pt_tune;
+
+/* Autotuner: solves the same trial right-hand sides (up to trial_rhs probes
+ * of one noise set spread over the colours of col_dev) with candidate
+ * parameters, by coordinate descent over delta (mixed precision), group
+ * (Wilson) and graph_iters, keeps the fastest, and stores it in the context
+ * for this operator's (kind, precision, lattice); later solves, traces and
+ * gradients with that key use it.  *best (host) receives it.  Synchronises. */
+PT_API int pt_autotune(pt_ctx *ctx, const pt_op *op, const int32_t *col_dev, int n_colours, int mu, int noise,
+                       uint64_t seed, int prec, double tol, int maxit, int trial_rhs, pt_tune *best);
+
+/* Install tuning parameters for (op kind, prec, lattice), e.g. from a cache;
+ * t = NULL restores the defaults.  pt_get_tuning returns the parameters the
+ * next run with that key will use. */
+PT_API int pt_set_tuning(pt_ctx *ctx, const pt_op *op, int prec, const pt_tune *t);
+PT_API int pt_get_tuning(pt_ctx *ctx, const pt_op *op, int prec, pt_tune *t);
+
 /* Enable (1) or disable (0) per-kernel CUDA-event timing inside the engine.
  * pt_profile_read returns, for the kernel class `which` (0 = the operator
  * apply of the inner Krylov iteration), the launches and the summed

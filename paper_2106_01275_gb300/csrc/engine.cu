@@ -999,10 +999,22 @@ __global__ void __launch_bounds__(PT_BLOCK) k_bicg_dir(EP P) {
 // ------------------------------------------------------------------ host driver
 struct EngineRun {
     EP P;
-    int grid_items;        // persistent CTAs of the item kernels
+    int grid_items;        // persistent CTAs of an item kernel without its own entry below
     int grid_warps;        // CTAs of the finalize kernels (8 warps each)
     int kernels_per_iter;
+    // persistent grid of each item kernel: SMs x its own resident CTAs per SM
+    int g_contract, g_oupd, g_ores, g_apply1, g_apply2, g_upd, g_s, g_dir;
 };
+
+template <typename K>
+static int persistent_grid(K kernel, int num_sms) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, PT_BLOCK, 0) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    return num_sms * occ;
+}
 
 // Events recorded around kernel groups when profiling is on (9 per iteration):
 // e0..e4 inner kernels, e5/e6 outer steps, e7/e8 whole iteration.
@@ -1014,39 +1026,39 @@ static inline void ev_rec(const cudaEvent_t *ev, int i, cudaStream_t st) {
 template <int KIND, typename S, typename LS>
 static void enqueue_iteration(const EngineRun &E, cudaStream_t st, const cudaEvent_t *ev) {
     const EP &P = E.P;
-    const int G = E.grid_items, W = E.grid_warps;
+    const int W = E.grid_warps;
     ev_rec(ev, 7, st);
     k_schedule<<<1, 1024, 0, st>>>(P);
-    k_contract<KIND><<<G, PT_BLOCK, 0, st>>>(P);
+    k_contract<KIND><<<E.g_contract, PT_BLOCK, 0, st>>>(P);
     k_fin_contract<<<W, 256, 0, st>>>(P);
     ev_rec(ev, 5, st);
-    k_outer_update<KIND, S><<<G, PT_BLOCK, 0, st>>>(P);
-    k_outer_residual<KIND, S><<<G, PT_BLOCK, 0, st>>>(P);
+    k_outer_update<KIND, S><<<E.g_oupd, PT_BLOCK, 0, st>>>(P);
+    k_outer_residual<KIND, S><<<E.g_ores, PT_BLOCK, 0, st>>>(P);
     k_fin_outer<<<W, 256, 0, st>>>(P);
     ev_rec(ev, 6, st);
     if constexpr (KIND == 0) {
         ev_rec(ev, 0, st);
-        if (P.vec4) k_cg_apply_v4<S><<<G, PT_BLOCK, 0, st>>>(P);
-        else k_cg_apply<S><<<G, PT_BLOCK, 0, st>>>(P);
+        if (P.vec4) k_cg_apply_v4<S><<<E.g_apply1, PT_BLOCK, 0, st>>>(P);
+        else k_cg_apply<S><<<E.g_apply1, PT_BLOCK, 0, st>>>(P);
         ev_rec(ev, 1, st);
         k_fin_cg_alpha<<<W, 256, 0, st>>>(P);
-        if (P.vec4) k_cg_update_v4<S><<<G, PT_BLOCK, 0, st>>>(P);
-        else k_cg_update<S><<<G, PT_BLOCK, 0, st>>>(P);
+        if (P.vec4) k_cg_update_v4<S><<<E.g_upd, PT_BLOCK, 0, st>>>(P);
+        else k_cg_update<S><<<E.g_upd, PT_BLOCK, 0, st>>>(P);
         k_fin_cg_beta<<<W, 256, 0, st>>>(P);
         ev_rec(ev, 2, st);
     } else {
         ev_rec(ev, 0, st);
-        k_bicg_apply1<S, LS><<<G, PT_BLOCK, 0, st>>>(P);
+        k_bicg_apply1<S, LS><<<E.g_apply1, PT_BLOCK, 0, st>>>(P);
         ev_rec(ev, 1, st);
         k_fin_bicg_alpha<<<W, 256, 0, st>>>(P);
-        k_bicg_s<S><<<G, PT_BLOCK, 0, st>>>(P);
+        k_bicg_s<S><<<E.g_s, PT_BLOCK, 0, st>>>(P);
         ev_rec(ev, 2, st);
-        k_bicg_apply2<S, LS><<<G, PT_BLOCK, 0, st>>>(P);
+        k_bicg_apply2<S, LS><<<E.g_apply2, PT_BLOCK, 0, st>>>(P);
         ev_rec(ev, 3, st);
         k_fin_bicg_omega<<<W, 256, 0, st>>>(P);
-        k_bicg_update<S><<<G, PT_BLOCK, 0, st>>>(P);
+        k_bicg_update<S><<<E.g_upd, PT_BLOCK, 0, st>>>(P);
         k_fin_bicg_beta<<<W, 256, 0, st>>>(P);
-        k_bicg_dir<S><<<G, PT_BLOCK, 0, st>>>(P);
+        k_bicg_dir<S><<<E.g_dir, PT_BLOCK, 0, st>>>(P);
         ev_rec(ev, 4, st);
     }
     ev_rec(ev, 8, st);
@@ -1080,6 +1092,25 @@ struct EngineRequest {
 };
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Engine parameters for (operator kind, precision, lattice): the autotuner's
+// candidate while it runs, else a stored tuning, else the defaults.
+static pt_ctx::Tune engine_tuning(const pt_ctx *c, const pt_op *op, int prec) {
+    if (c->in_trial) return c->trial;
+    for (int i = 0; i < 16; ++i) {
+        const pt_ctx::Tune &t = c->tune[i];
+        if (t.used && t.kind == op->kind && t.prec == prec && !memcmp(t.dims, op->dims, sizeof(t.dims))) return t;
+    }
+    pt_ctx::Tune d;
+    memset(&d, 0, sizeof(d));
+    d.kind = op->kind;
+    d.prec = prec;
+    memcpy(d.dims, op->dims, sizeof(d.dims));
+    d.delta = prec == PT_PREC_FP64 ? 0.0 : (prec == PT_PREC_MIXED_FP32 ? 1e-5 : 1e-2);
+    d.group = op->kind ? 8 : 1;
+    d.graph_iters = 8;
+    return d;
+}
 
 template <int KIND, typename S, typename LS>
 static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
@@ -1121,7 +1152,8 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     P.kind = KIND;
     P.nsb = nsb;
     P.R = R;
-    P.gs = KIND ? 8 : 1;
+    const pt_ctx::Tune tn = engine_tuning(c, op, rq.prec);
+    P.gs = tn.group;
     P.vec4 = (KIND == 0 && g.D[0] % 4 == 0) ? 1 : 0;
     P.L = L;
     P.diag = 8.0 + op->m2;
@@ -1160,9 +1192,10 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     P.task_out = (double *)(base + o_tout);
     P.tol = rq.tol;
     P.maxit = rq.maxit;
-    if (rq.prec == PT_PREC_FP64) { P.delta = 0.0; P.max_inner = rq.maxit; }
-    else if (rq.prec == PT_PREC_MIXED_FP32) { P.delta = KIND ? 1e-5 : 1e-5; P.max_inner = 4000; }
-    else { P.delta = 1e-2; P.max_inner = 400; }
+    P.delta = tn.delta;
+    if (rq.prec == PT_PREC_FP64) P.max_inner = rq.maxit;
+    else if (rq.prec == PT_PREC_MIXED_FP32) P.max_inner = 4000;
+    else P.max_inner = 400;
 
     cudaStream_t st = c->stream;
     PT_CUDA(cudaMemcpyAsync((void *)P.tasks, rq.h_tasks, (size_t)rq.n_tasks * sizeof(Task), cudaMemcpyHostToDevice, st));
@@ -1183,11 +1216,26 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     }
     occ = std::max(occ, 1);
     E.grid_items = c->num_sms * occ;
+    const int ns = c->num_sms;
+    E.g_contract = persistent_grid(k_contract<KIND>, ns);
+    E.g_oupd = persistent_grid(k_outer_update<KIND, S>, ns);
+    E.g_ores = persistent_grid(k_outer_residual<KIND, S>, ns);
+    if constexpr (KIND == 0) {
+        E.g_apply1 = E.g_apply2 = P.vec4 ? persistent_grid(k_cg_apply_v4<S>, ns) : persistent_grid(k_cg_apply<S>, ns);
+        E.g_upd = P.vec4 ? persistent_grid(k_cg_update_v4<S>, ns) : persistent_grid(k_cg_update<S>, ns);
+        E.g_s = E.g_dir = E.g_upd;
+    } else {
+        E.g_apply1 = persistent_grid(k_bicg_apply1<S, LS>, ns);
+        E.g_apply2 = persistent_grid(k_bicg_apply2<S, LS>, ns);
+        E.g_upd = persistent_grid(k_bicg_update<S>, ns);
+        E.g_s = persistent_grid(k_bicg_s<S>, ns);
+        E.g_dir = persistent_grid(k_bicg_dir<S>, ns);
+    }
     E.grid_warps = std::max(1, std::min((R + 7) / 8, c->num_sms * 4));
     E.kernels_per_iter = KIND ? 14 : 10;
 
     // capture ITERS engine iterations into one graph
-    const int ITERS = 8;
+    const int ITERS = tn.graph_iters;
     std::vector<cudaEvent_t> evs;
     if (c->prof) {
         evs.resize(ITERS * PT_EV_PER_ITER);
@@ -1636,4 +1684,136 @@ extern "C" int pt_grad(pt_ctx *c, const pt_op *op, const int32_t *col_dev, int n
         for (int i = 0; i < 2 * n_sets; ++i) est_out[i] = est[i];
     if (stats) *stats = acc;
     return rc_all;
+}
+
+// ------------------------------------------------------------------ autotuner
+// Coordinate descent over the engine's free parameters on a trial subset of
+// the probes: the inner relative tolerance delta (mixed precision only), the
+// slot group of the item order (Wilson only) and the engine iterations per
+// CUDA graph.  Each candidate solves the same trial right-hand sides; the
+// fastest (device time, synchronised) wins and is stored for the operator's
+// (kind, precision, lattice).
+static int store_tuning(pt_ctx *c, const pt_op *op, int prec, const pt_tune *t) {
+    int slot = -1;
+    for (int i = 0; i < 16; ++i) {
+        pt_ctx::Tune &e = c->tune[i];
+        if (e.used && e.kind == op->kind && e.prec == prec && !memcmp(e.dims, op->dims, sizeof(e.dims))) { slot = i; break; }
+        if (!e.used && slot < 0) slot = i;
+    }
+    if (slot < 0) slot = 0;
+    pt_ctx::Tune &e = c->tune[slot];
+    if (!t) { e.used = 0; return PT_OK; }
+    e.used = 1;
+    e.kind = op->kind;
+    e.prec = prec;
+    memcpy(e.dims, op->dims, sizeof(e.dims));
+    e.delta = t->delta;
+    e.group = t->group;
+    e.graph_iters = t->graph_iters;
+    return PT_OK;
+}
+
+extern "C" int pt_set_tuning(pt_ctx *c, const pt_op *op, int prec, const pt_tune *t) {
+    PT_CHECK_ARG(c && op && op->ctx == c, "pt_set_tuning: bad context/operator");
+    PT_CHECK_ARG(prec == PT_PREC_FP64 || prec == PT_PREC_MIXED_FP32 || prec == PT_PREC_MIXED_BF16,
+                 "pt_set_tuning: unknown precision %d", prec);
+    if (t) {
+        PT_CHECK_ARG(t->delta >= 0.0 && t->delta < 1.0, "pt_set_tuning: delta must be in [0, 1)");
+        PT_CHECK_ARG(t->group >= 1 && t->group <= 64, "pt_set_tuning: group must be in [1, 64]");
+        PT_CHECK_ARG(t->graph_iters >= 1 && t->graph_iters <= 64, "pt_set_tuning: graph_iters must be in [1, 64]");
+    }
+    return store_tuning(c, op, prec, t);
+}
+
+extern "C" int pt_get_tuning(pt_ctx *c, const pt_op *op, int prec, pt_tune *t) {
+    PT_CHECK_ARG(c && op && op->ctx == c && t, "pt_get_tuning: NULL argument");
+    const pt_ctx::Tune e = engine_tuning(c, op, prec);
+    t->delta = e.delta;
+    t->group = e.group;
+    t->graph_iters = e.graph_iters;
+    t->pad = 0;
+    t->seconds_per_rhs = 0.0;
+    return PT_OK;
+}
+
+extern "C" int pt_autotune(pt_ctx *c, const pt_op *op, const int32_t *col_dev, int n_colours, int mu, int noise,
+                           uint64_t seed, int prec, double tol, int maxit, int trial_rhs, pt_tune *best) {
+    PT_CHECK_ARG(c && op && op->ctx == c && col_dev && best, "pt_autotune: NULL argument");
+    PT_CHECK_ARG(n_colours >= 1 && mu >= 0 && mu < 4 && trial_rhs >= 1, "pt_autotune: bad colours/mu/trial_rhs");
+    PT_CHECK_ARG(noise == PT_NOISE_Z2 || (noise == PT_NOISE_Z4 && op->dof == 12),
+                 "pt_autotune: Z4 noise needs the complex (Wilson) operator");
+    int rc = check_solver_args(prec, tol, maxit);
+    if (rc) return rc;
+    PT_CUDA(cudaSetDevice(c->device));
+    // trial tasks spread evenly over the colours and components of one noise set
+    std::vector<Task> all, trial;
+    build_probe_tasks(0, n_colours, 0, 1, op->dof, 1, 0, all);
+    const int n = std::min<int>(trial_rhs, (int)all.size());
+    for (int i = 0; i < n; ++i) trial.push_back(all[(size_t)i * all.size() / n]);
+    const int p0 = 0;
+    cudaEvent_t e0, e1;
+    PT_CUDA(cudaEventCreate(&e0));
+    PT_CUDA(cudaEventCreate(&e1));
+    auto time_candidate = [&](const pt_ctx::Tune &cand, double *sec) -> int {
+        EngineRequest rq;
+        rq.mode = MODE_TRACE;
+        rq.n_tasks = (int)trial.size();
+        rq.h_tasks = trial.data();
+        rq.col = col_dev;
+        rq.seed = seed;
+        rq.noise = noise; rq.mu = mu; rq.n_p = 1; rq.dilute = 1; rq.pshift = 0;
+        rq.p_list = &p0;
+        rq.B_user = nullptr;
+        rq.X_user = nullptr;
+        rq.tol = tol;
+        rq.maxit = maxit;
+        rq.prec = prec;
+        rq.R_force = 0;
+        c->trial = cand;
+        c->in_trial = 1;
+        cudaEventRecord(e0, c->stream);
+        int r = run_engine(op, rq, nullptr);
+        cudaEventRecord(e1, c->stream);
+        c->in_trial = 0;
+        if (r != PT_OK) return r;
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *sec = ms / 1e3;
+        return PT_OK;
+    };
+    c->in_trial = 0;
+    pt_ctx::Tune cur = engine_tuning(c, op, prec);
+    double t_best = 0.0;
+    rc = time_candidate(cur, &t_best);                       // warm-up (work space, first graph)
+    if (!rc) rc = time_candidate(cur, &t_best);
+    std::vector<double> deltas;
+    if (prec == PT_PREC_MIXED_FP32) deltas = {1e-2, 1e-3, 1e-4, 1e-5, 1e-6};
+    else if (prec == PT_PREC_MIXED_BF16) deltas = {3e-2, 1e-2, 3e-3, 1e-3};
+    std::vector<int> groups;
+    if (op->kind == 1) groups = {1, 2, 4, 8, 16};
+    const std::vector<int> iters = {4, 8, 16};
+    for (int pass = 0; pass < 3 && !rc; ++pass) {
+        const size_t nc = pass == 0 ? deltas.size() : pass == 1 ? groups.size() : iters.size();
+        for (size_t i = 0; i < nc && !rc; ++i) {
+            pt_ctx::Tune cand = cur;
+            if (pass == 0) cand.delta = deltas[i];
+            else if (pass == 1) cand.group = groups[i];
+            else cand.graph_iters = iters[i];
+            if (!memcmp(&cand, &cur, sizeof(cand))) continue;
+            double t = 0.0;
+            rc = time_candidate(cand, &t);
+            if (!rc && t < t_best) { t_best = t; cur = cand; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->in_trial = 0;
+    if (rc) return rc;
+    best->delta = cur.delta;
+    best->group = cur.group;
+    best->graph_iters = cur.graph_iters;
+    best->pad = 0;
+    best->seconds_per_rhs = t_best / trial.size();
+    return store_tuning(c, op, prec, best);
 }

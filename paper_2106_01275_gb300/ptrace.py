@@ -43,6 +43,15 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Tune(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_double), ("group", ctypes.c_int32), ("graph_iters", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("seconds_per_rhs", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"delta": self.delta, "group": self.group, "graph_iters": self.graph_iters,
+                "seconds_per_rhs": self.seconds_per_rhs}
+
+
 _lib = None
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -55,6 +64,9 @@ _SIGS = {
     "pt_synchronize": ([_P], _I),
     "pt_set_memory_budget": ([_P, ctypes.c_size_t], _I),
     "pt_set_max_slots": ([_P, _I], _I),
+    "pt_autotune": ([_P, _P, _P, _I, _I, _I, ctypes.c_uint64, _I, _D, _I, _I, ctypes.POINTER(Tune)], _I),
+    "pt_set_tuning": ([_P, _P, _I, ctypes.POINTER(Tune)], _I),
+    "pt_get_tuning": ([_P, _P, _I, ctypes.POINTER(Tune)], _I),
     "pt_profile_enable": ([_P, _I], _I),
     "pt_profile_read": ([_P, _I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_D), _I], _I),
     "pt_op_laplacian": ([_P, ctypes.POINTER(_I), _D, ctypes.POINTER(_P)], _I),
@@ -338,6 +350,33 @@ def trace(op, col, n_colours, mu, p_list, noise="z2", seed=0, set0=0, n_sets=1, 
                               _np_ptr(est), _np_ptr(mean), _np_ptr(var), ctypes.byref(st))
     _check(rc)
     return est, mean, var, st.as_dict()
+
+
+def autotune(op, col, n_colours, mu, noise="z2", seed=0, prec="mixed_fp32", tol=1e-10, maxit=20000,
+             trial_rhs=64):
+    """Run the library's autotuner on trial probes of `col`; returns the chosen
+    parameters (also stored in the context for this operator/precision/lattice)."""
+    t = Tune()
+    _check(lib().pt_autotune(op.ctx.handle, op._h, _ptr(col), int(n_colours), int(mu),
+                             NOISE[noise] if isinstance(noise, str) else int(noise), int(seed), PREC[prec],
+                             float(tol), int(maxit), int(trial_rhs), ctypes.byref(t)))
+    return t.as_dict()
+
+
+def set_tuning(op, prec, delta=None, group=None, graph_iters=None, reset=False):
+    if reset:
+        _check(lib().pt_set_tuning(op.ctx.handle, op._h, PREC[prec], None))
+        return
+    cur = get_tuning(op, prec)
+    t = Tune(cur["delta"] if delta is None else float(delta), cur["group"] if group is None else int(group),
+             cur["graph_iters"] if graph_iters is None else int(graph_iters), 0, 0.0)
+    _check(lib().pt_set_tuning(op.ctx.handle, op._h, PREC[prec], ctypes.byref(t)))
+
+
+def get_tuning(op, prec):
+    t = Tune()
+    _check(lib().pt_get_tuning(op.ctx.handle, op._h, PREC[prec], ctypes.byref(t)))
+    return t.as_dict()
 
 
 def trace_multi(op, cols, n_colours, mu, p_list, noise="z2", seed=0, set0=0, n_sets=1, dilute=True,

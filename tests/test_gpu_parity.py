@@ -295,6 +295,36 @@ def test_grad_kappa_finite_difference_gpu(pt, ctx):
     assert abs(dk - fd) <= 1e-5 * abs(fd)
 
 
+# ------------------------------------------------------------------ autotuner
+def test_autotune_then_parity(pt, ctx):
+    """The autotuner picks parameters from its candidate sets, stores them for
+    the operator, and traces with the tuned engine still match the oracle."""
+    dims, m2, p = [8, 8, 8, 8], 0.05, 1
+    colv, m = greedy_colour(dims, 0, [p], 2, 0)
+    op = pt.laplacian(ctx, dims, m2)
+    best = pt.autotune(op, _t(colv), m, 0, "z2", 3, "mixed_fp32", 1e-10, 5000, 16)
+    assert best["delta"] in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6) and best["graph_iters"] in (4, 8, 16)
+    assert best["group"] == 1 and best["seconds_per_rhs"] > 0
+    assert pt.get_tuning(op, "mixed_fp32")["delta"] == best["delta"]
+    est, _, _, _ = pt.trace(op, _t(colv), m, 0, [p], "z2", 3, 0, 2, True, "mixed_fp32", 1e-10, 5000)
+    want = OE.probed_estimates(OE.Laplacian(dims, m2), colv, m, 3, 2, 0, 0, [p], 1e-12)
+    assert np.allclose(est, want, rtol=1e-8, atol=1e-9)
+    # Wilson: the slot group is tuned too; explicit settings are honoured
+    dims, kappa, mu = [4, 4, 4, 8], 0.12, 2
+    U = inputs.gauge_links(dims, 1234)
+    colw, mw = greedy_colour(dims, mu, [1], 1, 0)
+    opw = pt.wilson(ctx, dims, _t(U), kappa, True)
+    bw = pt.autotune(opw, _t(colw), mw, mu, "z4", 5, "mixed_fp32", 1e-10, 5000, 12)
+    assert bw["group"] in (1, 2, 4, 8, 16)
+    pt.set_tuning(opw, "mixed_fp32", delta=1e-3, group=2, graph_iters=4)
+    assert pt.get_tuning(opw, "mixed_fp32") == {"delta": 1e-3, "group": 2, "graph_iters": 4, "seconds_per_rhs": 0.0}
+    est, _, _, _ = pt.trace(opw, _t(colw), mw, mu, [1], "z4", 5, 0, 1, True, "mixed_fp32", 1e-10, 5000)
+    want = OE.probed_estimates(OE.Wilson(dims, U, kappa), colw, mw, 5, 1, 1, mu, [1], 1e-12)
+    assert np.allclose(est, want, rtol=1e-8, atol=1e-7)
+    pt.set_tuning(opw, "mixed_fp32", reset=True)
+    pt.set_tuning(op, "mixed_fp32", reset=True)
+
+
 # ------------------------------------------------------------------ edge cases
 def test_edge_cases(pt, ctx):
     import torch
