@@ -328,6 +328,111 @@ def run_ours(args):
 APPLY_NCU_TRAFFIC_PER_SITE_RHS = (125.515008e6 + 85.80608e6) / (238 * 65536)
 
 
+def run_grad(args):
+    """Adjoint-gradient workload: Wilson-Dirac 32^3 x 64 (small: 16^3 x 32),
+    kappa = 0.12, p = 4 along z with its (4, 2) colouring, one Z4 set with 12x
+    dilution; per step every probe is solved forward and adjoint (mixed FP32
+    BiCGStab + FP64 defect correction to 1e-10), no Krylov history is kept,
+    and dT/dkappa and the per-link derivatives G, Gbar are formed."""
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2106_01275_gb300 import inputs
+    from paper_2106_01275_gb300 import ptrace as pt
+    dims = [16, 16, 16, 32] if args.case == "small" else [32, 32, 32, 64]
+    kappa, mu, p, k = 0.12, 2, 4, 2
+    N = int(np.prod(dims))
+    ctx = pt.Context(local)
+    ctx.set_memory_budget(200 << 30)
+    U = torch.as_tensor(inputs.gauge_links(dims, 4321)).cuda()
+    op = pt.wilson(ctx, dims, U, kappa, True)
+    c0, m0 = pt.colour(ctx, dims, mu, [p], k, "natural")
+    c1, m1 = pt.colour(ctx, dims, mu, [p], k, "redblack")
+    col, m = (c0, m0) if m0 <= m1 else (c1, m1)
+    set0 = rank
+
+    def step(c=col):
+        return pt.grad(op, c, m, mu, p, "z4", SEED, set0, 1, True, "mixed_fp32", TOL, MAXIT, links=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    ctx.profile(True)
+    for c in range(4):
+        ctx.profile_read(c, reset=True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    stats = []
+    for _ in range(args.steps):
+        est, dk, G, Gb, st = step()
+        stats.append(st)
+    ev1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ctx.profile(False)
+    clocks = clk.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    prof = [ctx.profile_read(c, reset=True) for c in range(4)]
+    site_rhs = sum(s["site_rhs_applies"] for s in stats)
+    inner = sum(s["inner_iters"] for s in stats)
+    if world > 1:
+        t = torch.tensor([t_ms, float(site_rhs)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+        t_ms, site_rhs = float(tmax[0]), float(t[1])
+    peak, peak_kind = peaks()
+    apply_bytes = inner * 2 * N * 192.0 + prof[0][0] * N * 288.0
+    achieved = apply_bytes / (prof[0][1] / 1e3) / 1e9 if prof[0][1] > 0 else None
+    out = {"metric": METRIC, "value": site_rhs / (t_ms / 1e3), "unit": "site*RHS/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
+           "config": {"workload": "grad32: adjoint gradient of the probed Tr(P_4 A^-1), Wilson-Dirac %s kappa=0.12, "
+                                  "(4,2)-colouring (%d colours), 1 Z4 set x 12 dilution, forward + adjoint solves, "
+                                  "dT/dkappa and per-link G, Gbar" % ("x".join(map(str, dims)), m),
+                      "lattice": dims, "n_rhs_per_step": int(stats[-1]["n_rhs"]), "n_colours": m,
+                      "parallelism": "rhs-batched, %d rank(s), weak" % world},
+           "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+           "roofline": {"bound": "hbm", "kernel": "k_bicg_apply1/2<float,float>", "achieved": achieved,
+                        "peak": peak, "unit": "GB/s", "frac": achieved / peak if achieved else None,
+                        "peak_source": peak_kind, "traffic": None,
+                        "algorithmic_bytes_per_site_rhs": 192.0, "algorithmic_bytes_per_site_launch": 288.0,
+                        "step_breakdown_ms": {"apply": prof[0][1], "inner_vector": prof[1][1],
+                                              "outer_fp64": prof[2][1], "all_iterations": prof[3][1]}},
+           "clocks": clocks, "dT_dkappa": [dk.real, dk.imag], "estimate": [float(est.sum().real), float(est.sum().imag)],
+           "mean_inner_iters_per_rhs": stats[-1]["inner_iters"] / stats[-1]["n_rhs"],
+           "solves_per_s": stats[-1]["n_rhs"] / (t_ms / 1e3 / args.steps)}
+    if rank == 0 and world == 1 and not args.skip_baselines:
+        cols_host = col.cpu().pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        site_e2e = 0
+        for _ in range(args.steps):
+            est_h, dk_h, G_h, Gb_h, st_h = step(cols_host.to("cuda", non_blocking=True))
+            G_host, Gb_host = G_h.cpu(), Gb_h.cpu()
+            site_e2e += st_h["site_rhs_applies"]
+        t_e2e = time.perf_counter() - t0
+        out["e2e"] = {"value": site_e2e / t_e2e, "unit": "site*RHS/s", "h2d_bytes_per_step": int(N * 4),
+                      "d2h_bytes_per_step": int(G_host.numel() * 16 * 2 + 16 * 2)}
+        W = Workload("grad32", "wil", dims, mu, [(p, k)], [p], 1, "z4", "", kappa=kappa, link_seed=4321)
+        out["cpu_baseline"] = cpu_baseline(W, args.cpu_seconds)
+        out["fp64_plain"] = None
+    elif rank == 0:
+        out["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def oracle_sample(W, seconds):
     """The oracle as it stands, on a bounded sample of the workload: probes of
     one colouring (set 0, then further sets) solved one by one with its FP64
@@ -386,7 +491,12 @@ def run_reference(args):
     world, rank, local = dist_setup()
     if rank != 0:
         return
-    W = workloads(args.case)[args.workload]
+    if args.workload == "grad32":
+        dims = [16, 16, 16, 32] if args.case == "small" else [32, 32, 32, 64]
+        W = Workload("grad32", "wil", dims, 2, [(4, 2)], [4], 1, "z4", "grad32 (oracle operator applications)",
+                     kappa=0.12, link_seed=4321)
+    else:
+        W = workloads(args.case)[args.workload]
     per_step = max(2.0, min(20.0, args.cpu_seconds / max(args.steps, 1)))
     for _ in range(args.warmup):
         oracle_sample(W, min(per_step, 2.0))
@@ -414,7 +524,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="lap16", choices=["lap16", "wilson24"])
+    ap.add_argument("--workload", default="lap16", choices=["lap16", "wilson24", "grad32"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--skip-baselines", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="use the engine's default parameters")
@@ -423,6 +533,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "grad32":
+        run_grad(args)
     else:
         run_ours(args)
 
