@@ -39,6 +39,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2106_01275_gb300 import sharding  # noqa: E402  (imports nothing heavy)
+
 METRIC = "time to Tr(PA^-1) at fixed sigma; stencil site*RHS/s & HBM %; mixed vs FP64 1xGB300"
 TOL = 1e-10
 MAXIT = 20000
@@ -182,7 +184,7 @@ def run_ours(args):
     op = make_operator(pt, ctx, W)
     cols, m = make_colourings(pt, ctx, W)
     N = W.N
-    set0 = rank * W.n_sets                    # weak scaling: each rank its own noise sets
+    set0, _ = sharding.rank_sets(rank, W.n_sets)      # weak scaling: each rank its own noise sets
 
     def step(prec="mixed_fp32", set_base=set0, n_sets=W.n_sets, c=cols, mm=m):
         return pt.trace_multi(op, c, mm, W.mu, W.p_contract, W.noise, SEED, set_base, n_sets, True, prec,
@@ -226,14 +228,7 @@ def run_ours(args):
     site_rhs = sum(s["site_rhs_applies"] for s in stats)
     inner_iters = sum(s["inner_iters"] for s in stats)
     launches = sum(s["kernel_launches"] for s in stats)
-    if world > 1:
-        t = torch.tensor([t_ms, float(site_rhs)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
-        t_ms, site_rhs_all = float(tmax[0]), float(t[1])
-    else:
-        site_rhs_all = float(site_rhs)
+    t_ms, site_rhs_all = sharding.reduce_timing(t_ms, site_rhs, "cuda")
     value = site_rhs_all / (t_ms / 1e3)
     step_s = t_ms / 1e3 / args.steps
 
@@ -351,7 +346,7 @@ def run_grad(args):
     c0, m0 = pt.colour(ctx, dims, mu, [p], k, "natural")
     c1, m1 = pt.colour(ctx, dims, mu, [p], k, "redblack")
     col, m = (c0, m0) if m0 <= m1 else (c1, m1)
-    set0 = rank
+    set0, _ = sharding.rank_sets(rank, 1)
 
     def step(c=col):
         return pt.grad(op, c, m, mu, p, "z4", SEED, set0, 1, True, "mixed_fp32", TOL, MAXIT, links=True)
@@ -383,12 +378,7 @@ def run_grad(args):
     prof = [ctx.profile_read(c, reset=True) for c in range(4)]
     site_rhs = sum(s["site_rhs_applies"] for s in stats)
     inner = sum(s["inner_iters"] for s in stats)
-    if world > 1:
-        t = torch.tensor([t_ms, float(site_rhs)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
-        t_ms, site_rhs = float(tmax[0]), float(t[1])
+    t_ms, site_rhs = sharding.reduce_timing(t_ms, site_rhs, "cuda")
     peak, peak_kind = peaks()
     apply_bytes = inner * 2 * N * 192.0 + prof[0][0] * N * 288.0
     achieved = apply_bytes / (prof[0][1] / 1e3) / 1e9 if prof[0][1] > 0 else None

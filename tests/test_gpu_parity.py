@@ -146,6 +146,23 @@ def test_wilson_apply_full_size_24c48(pt, ctx):
     assert np.max(np.abs(y32 - want)) <= 2e-5 * np.max(np.abs(want))
 
 
+def test_wilson_solve_full_size_24c48(pt, ctx):
+    """Full-size lattice of the batched Wilson workload (24^3 x 48, kappa 0.124):
+    the true residual of the GPU solutions, evaluated with the oracle's FP64
+    operator, is below the tolerance (a property that holds at any size)."""
+    dims, kappa = [24, 24, 24, 48], 0.124
+    N = int(np.prod(dims))
+    U = inputs.gauge_links(dims, 1234)
+    op = pt.wilson(ctx, dims, _t(U), kappa, True)
+    r = np.random.default_rng(8)
+    B = r.standard_normal((2, N, 4, 3)) + 1j * r.standard_normal((2, N, 4, 3))
+    X, iters, relres, st = pt.solve(op, _t(B), "mixed_fp32", 1e-10, 5000)
+    X = X.cpu().numpy()
+    for j in range(2):
+        res = B[j] - OO.wilson_apply(X[j], U, kappa, dims, True)
+        assert np.linalg.norm(res) <= 1.01e-10 * np.linalg.norm(B[j])
+
+
 # ------------------------------------------------------------------ solves
 @pytest.mark.parametrize("prec", ["fp64", "mixed_fp32", "mixed_bf16"])
 def test_laplacian_solve(pt, ctx, prec):
