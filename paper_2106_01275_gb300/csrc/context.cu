@@ -137,7 +137,8 @@ static int check_dims(const int dims[4]) {
 }
 
 // ------------------------------------------------------------------ link packing
-// user [N][4][3][3] complex128 -> packed complex [4][9][N] in FP64, FP32, BF16
+// user [N][4][3][3] complex128 -> packed complex [4][9][N] in FP64 and BF16,
+// and [4][5][N] 16-byte chunks (entries 2k, 2k+1) in FP32
 __global__ void k_pack_links(int N, const double2 *__restrict__ Uu, double2 *U64, float2 *U32,
                              __nv_bfloat162 *U16) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -146,7 +147,8 @@ __global__ void k_pack_links(int N, const double2 *__restrict__ Uu, double2 *U64
     double2 v = Uu[i];
     int64_t o = (int64_t)r * N + idx;
     U64[o] = v;
-    U32[o] = make_float2((float)v.x, (float)v.y);
+    const int mu = r / 9, el = r % 9;
+    U32[(((int64_t)mu * 5 + el / 2) * N + idx) * 2 + (el & 1)] = make_float2((float)v.x, (float)v.y);
     U16[o] = __floats2bfloat162_rn((float)v.x, (float)v.y);
 }
 
@@ -181,7 +183,8 @@ extern "C" int pt_op_wilson(pt_ctx *c, const int dims[4], const double *U_dev, d
     op->antip = antip ? 1 : 0;
     size_t n = (size_t)op->g.N * 36;
     cudaError_t e = cudaMalloc((void **)&op->U64, n * sizeof(double2));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&op->U32, n * sizeof(float2));
+    // FP32 links: [4][5][N] 16-byte chunks (9 complex entries + 1 zero pad per link)
+    if (e == cudaSuccess) e = cudaMalloc((void **)&op->U32, (size_t)op->g.N * 20 * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc((void **)&op->U16, n * sizeof(__nv_bfloat162));
     if (e != cudaSuccess) {
         cudaFree(op->U64); cudaFree(op->U32); cudaFree(op->U16); free(op);
@@ -191,6 +194,9 @@ extern "C" int pt_op_wilson(pt_ctx *c, const int dims[4], const double *U_dev, d
     }
     int threads = 256;
     int64_t blocks = ((int64_t)n + threads - 1) / threads;
+    e = cudaMemsetAsync(op->U32, 0, (size_t)op->g.N * 20 * sizeof(float4), c->stream);   // pad entries
+    if (e != cudaSuccess) { cudaFree(op->U64); cudaFree(op->U32); cudaFree(op->U16); free(op);
+                            return pt_cuda_fail(e, "cudaMemsetAsync", __FILE__, __LINE__); }
     k_pack_links<<<(unsigned)blocks, threads, 0, c->stream>>>(op->g.N, (const double2 *)U_dev,
                                                                (double2 *)op->U64, (float2 *)op->U32,
                                                                (__nv_bfloat162 *)op->U16);

@@ -117,13 +117,13 @@ __device__ __forceinline__ void apply_site(const EP &P, const S *f, const LS *U,
     } else {
         Cx<R> acc[4][3];
         wilson_hop_site<R, S, LS>(P.g, f, U, P.antip, idx, x, acc);
+        Cx<R> ps[4][3];
+        load_spinor<S, R>(f, P.g.N, idx, ps);
+        const R kap = (R)P.kappa;
 #pragma unroll
         for (int s = 0; s < 4; ++s)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                Cx<R> v = ld_cx<S, R>(f, P.g.N, 3 * s + a, idx);
-                out[3 * s + a] = csub(v, cscale(acc[s][a], (R)P.kappa));
-            }
+            for (int a = 0; a < 3; ++a) out[3 * s + a] = csub(ps[s][a], cscale(acc[s][a], kap));
     }
 }
 
@@ -801,7 +801,7 @@ __global__ void __launch_bounds__(PT_BLOCK) k_cg_update_v4(EP P) {
 // ------------------------------------------------------------------ BiCGStab (Wilson)
 // v = A p;  partial (r0, v)
 template <typename S, typename LS>
-__global__ void __launch_bounds__(PT_BLOCK) k_bicg_apply1(EP P) {
+__global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 : 3) k_bicg_apply1(EP P) {
     typedef Fld<1, S> F;
     typedef typename F::R R;
     __shared__ double sh[32 * 2];
@@ -818,13 +818,16 @@ __global__ void __launch_bounds__(PT_BLOCK) k_bicg_apply1(EP P) {
             site_coords(P.g, idx, xc);
             Cx<R> av[12];
             apply_site<1, R, S, LS>(P, pv, (const LS *)P.U, idx, xc, av);
+            Cx<R> z[4][3];
+            load_spinor<S, R>(r0, N, idx, z);
+#pragma unroll
             for (int c = 0; c < 12; ++c) {
-                const Cx<R> w = Cx<R>{rnd<S, R>(av[c].re), rnd<S, R>(av[c].im)};
-                F::st(q, N, c, idx, w);
-                const Cx<R> z = F::ld(r0, N, c, idx);
-                vr[0] += z.re * w.re + z.im * w.im;
-                vr[1] += z.re * w.im - z.im * w.re;
+                av[c] = Cx<R>{rnd<S, R>(av[c].re), rnd<S, R>(av[c].im)};
+                const Cx<R> w = av[c], zc = z[c / 3][c % 3];
+                vr[0] += zc.re * w.re + zc.im * w.im;
+                vr[1] += zc.re * w.im - zc.im * w.re;
             }
+            store_spinor<S, R>(q, N, idx, av);
         SITE_LOOP_END
         item_store_r<2>(P, j, b, vr, sh);
     ITEM_LOOP_END
@@ -869,7 +872,7 @@ __global__ void __launch_bounds__(PT_BLOCK) k_bicg_s(EP P) {
 
 // t = A s;  partials (t, s), |t|^2
 template <typename S, typename LS>
-__global__ void __launch_bounds__(PT_BLOCK) k_bicg_apply2(EP P) {
+__global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 : 3) k_bicg_apply2(EP P) {
     typedef Fld<1, S> F;
     typedef typename F::R R;
     __shared__ double sh[32 * 3];
@@ -885,10 +888,15 @@ __global__ void __launch_bounds__(PT_BLOCK) k_bicg_apply2(EP P) {
             site_coords(P.g, idx, xc);
             Cx<R> av[12];
             apply_site<1, R, S, LS>(P, s, (const LS *)P.U, idx, xc, av);
+            Cx<R> sp[4][3];
+            load_spinor<S, R>(s, N, idx, sp);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) av[c] = Cx<R>{rnd<S, R>(av[c].re), rnd<S, R>(av[c].im)};
+            store_spinor<S, R>(t, N, idx, av);
+#pragma unroll
             for (int c = 0; c < 12; ++c) {
-                const Cx<R> tv = Cx<R>{rnd<S, R>(av[c].re), rnd<S, R>(av[c].im)};
-                F::st(t, N, c, idx, tv);
-                const Cx<R> sv = F::ld(s, N, c, idx);
+                const Cx<R> tv = av[c];
+                const Cx<R> sv = sp[c / 3][c % 3];
                 vr[0] += tv.re * sv.re + tv.im * sv.im;     // (t, s) = conj(t) s
                 vr[1] += tv.re * sv.im - tv.im * sv.re;
                 vr[2] += tv.re * tv.re + tv.im * tv.im;

@@ -1,11 +1,17 @@
 // Internal definitions shared by the CUDA translation units of libptrace.
 //
-// Internal field layout (all precisions share the same flat real indexing, so
-// FP64 / FP32 / BF16 copies of one field convert element by element):
-//   scalar field (dof 1):  real   [N]
-//   spinor field (dof 12): complex [12 components][N sites]  (SoA by component,
-//                          component a = 3 * spin + colour, interleaved re/im)
-//   links:                 complex [4 mu][9 = 3 row x 3 col][N]
+// Internal field layout (structure of arrays; element (component c, site x)
+// is reached through ld_cx / st_cx, so copies in different precisions convert
+// component by component):
+//   scalar field (dof 1):  real [N]
+//   spinor field (dof 12), component a = 3 * spin + colour, complex (re, im):
+//     FP64, BF16: [12 components][N sites]
+//     FP32:       [6 pairs of components][N sites] of 16-byte chunks, so that a
+//                 site's spinor is six 16-byte loads
+//   links:
+//     FP64, BF16: complex [4 mu][9 = 3 row x 3 col][N]
+//     FP32:       [4 mu][5][N] 16-byte chunks holding entries (2k, 2k+1), the
+//                 tenth entry is padding (zero)
 // One right-hand side ("slot") of the batched solver owns one such field per
 // Krylov vector; slot j starts at j * L reals, L = N (scalar) or 24 N (spinor).
 #pragma once
@@ -158,7 +164,8 @@ template <typename S, typename R>
 __device__ __forceinline__ Cx<R> ld_cx(const S *f, int N, int c, int idx);
 template <>
 __device__ __forceinline__ Cx<float> ld_cx<float, float>(const float *f, int N, int c, int idx) {
-    float2 v = reinterpret_cast<const float2 *>(f)[(size_t)c * N + idx];
+    // FP32: component pairs in 16-byte chunks [c / 2][idx], half c % 2
+    float2 v = reinterpret_cast<const float2 *>(f)[((size_t)(c >> 1) * N + idx) * 2 + (c & 1)];
     return Cx<float>{v.x, v.y};
 }
 template <>
@@ -176,7 +183,7 @@ template <typename S, typename R>
 __device__ __forceinline__ void st_cx(S *f, int N, int c, int idx, Cx<R> v);
 template <>
 __device__ __forceinline__ void st_cx<float, float>(float *f, int N, int c, int idx, Cx<float> v) {
-    reinterpret_cast<float2 *>(f)[(size_t)c * N + idx] = make_float2(v.re, v.im);
+    reinterpret_cast<float2 *>(f)[((size_t)(c >> 1) * N + idx) * 2 + (c & 1)] = make_float2(v.re, v.im);
 }
 template <>
 __device__ __forceinline__ void st_cx<double, double>(double *f, int N, int c, int idx, Cx<double> v) {
@@ -185,6 +192,37 @@ __device__ __forceinline__ void st_cx<double, double>(double *f, int N, int c, i
 template <>
 __device__ __forceinline__ void st_cx<__nv_bfloat16, float>(__nv_bfloat16 *f, int N, int c, int idx, Cx<float> v) {
     reinterpret_cast<__nv_bfloat162 *>(f)[(size_t)c * N + idx] = __floats2bfloat162_rn(v.re, v.im);
+}
+
+// whole spinor of one site, ps[spin][colour]: six 16-byte loads for FP32,
+// twelve complex loads otherwise
+template <typename S, typename R>
+__device__ __forceinline__ void load_spinor(const S *f, int N, int idx, Cx<R> ps[4][3]) {
+    if constexpr (std::is_same<S, float>::value) {
+        const float4 *q = reinterpret_cast<const float4 *>(f);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 v = q[(size_t)k * N + idx];
+            ps[(2 * k) / 3][(2 * k) % 3] = Cx<R>{v.x, v.y};
+            ps[(2 * k + 1) / 3][(2 * k + 1) % 3] = Cx<R>{v.z, v.w};
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 12; ++c) ps[c / 3][c % 3] = ld_cx<S, R>(f, N, c, idx);
+    }
+}
+
+template <typename S, typename R>
+__device__ __forceinline__ void store_spinor(S *f, int N, int idx, const Cx<R> v[12]) {
+    if constexpr (std::is_same<S, float>::value) {
+        float4 *q = reinterpret_cast<float4 *>(f);
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            q[(size_t)k * N + idx] = make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 12; ++c) st_cx<S, R>(f, N, c, idx, v[c]);
+    }
 }
 
 // ------------------------------------------------------------------ Wilson hop
@@ -241,11 +279,21 @@ __device__ __forceinline__ void spin_accumulate(int mu, R sg, R eta, const Cx<R>
     }
 }
 
-// links: complex [4][9][N]
+// links: complex [4][9][N] (FP64, BF16) or [4][5][N] 16-byte chunks (FP32)
 template <typename R, typename LS>
 __device__ __forceinline__ void load_link(const LS *U, int N, int mu, int idx, Cx<R> u[3][3]) {
+    if constexpr (std::is_same<LS, float>::value) {
+        const float4 *q = reinterpret_cast<const float4 *>(U) + (size_t)mu * 5 * N;
 #pragma unroll
-    for (int e = 0; e < 9; ++e) u[e / 3][e % 3] = ld_cx<LS, R>(U, N, mu * 9 + e, idx);
+        for (int k = 0; k < 5; ++k) {
+            const float4 v = q[(size_t)k * N + idx];
+            u[(2 * k) / 3][(2 * k) % 3] = Cx<R>{v.x, v.y};
+            if (k < 4) u[(2 * k + 1) / 3][(2 * k + 1) % 3] = Cx<R>{v.z, v.w};
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < 9; ++e) u[e / 3][e % 3] = ld_cx<LS, R>(U, N, mu * 9 + e, idx);
+    }
 }
 
 // (H psi)(x) for one site; psi is read through ld_cx from field f (N sites).
@@ -265,10 +313,7 @@ __device__ __forceinline__ void wilson_hop_site(const Geom &g, const S *f, const
             int y = nb_fwd(g, idx, x, mu);
             R eta = (antip && mu == 3 && x[3] == g.D[3] - 1) ? R(-1) : R(1);
             Cx<R> ps[4][3], h[2][3], uh[2][3], u[3][3];
-#pragma unroll
-            for (int s = 0; s < 4; ++s)
-#pragma unroll
-                for (int a = 0; a < 3; ++a) ps[s][a] = ld_cx<S, R>(f, N, 3 * s + a, y);
+            load_spinor<S, R>(f, N, y, ps);
             spin_project<R>(mu, R(-1), ps, h);
             load_link<R, LS>(U, N, mu, idx, u);
 #pragma unroll
@@ -287,10 +332,7 @@ __device__ __forceinline__ void wilson_hop_site(const Geom &g, const S *f, const
             int y = nb_bwd(g, idx, x, mu);
             R eta = (antip && mu == 3 && x[3] == 0) ? R(-1) : R(1);
             Cx<R> ps[4][3], h[2][3], uh[2][3], u[3][3];
-#pragma unroll
-            for (int s = 0; s < 4; ++s)
-#pragma unroll
-                for (int a = 0; a < 3; ++a) ps[s][a] = ld_cx<S, R>(f, N, 3 * s + a, y);
+            load_spinor<S, R>(f, N, y, ps);
             spin_project<R>(mu, R(1), ps, h);
             load_link<R, LS>(U, N, mu, y, u);
 #pragma unroll
