@@ -865,7 +865,15 @@ __global__ void __launch_bounds__(PT_BLOCK) k_bicg_s(EP P) {
         const S *q = slot_cptr<S>(P.q, j, P.L);
         S *s = slot_ptr<S>(P.s, j, P.L);
         SITE_LOOP(1)
-            for (int c = 0; c < 12; ++c) F::st(s, N, c, idx, csub(F::ld(r, N, c, idx), cmul(al, F::ld(q, N, c, idx))));
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                Cx<R> rv[2], qv[2], sv[2];
+                ld_pair<S, R>(r, N, k, idx, rv);
+                ld_pair<S, R>(q, N, k, idx, qv);
+                sv[0] = csub(rv[0], cmul(al, qv[0]));
+                sv[1] = csub(rv[1], cmul(al, qv[1]));
+                st_pair<S, R>(s, N, k, idx, sv);
+            }
         SITE_LOOP_END
     ITEM_LOOP_END
 }
@@ -938,16 +946,25 @@ __global__ void __launch_bounds__(PT_BLOCK) k_bicg_update(EP P) {
         const S *r0 = slot_cptr<S>(P.r0, j, P.L);
         R vr[3] = {R(0), R(0), R(0)};
         SITE_LOOP(1)
-            for (int c = 0; c < 12; ++c) {
-                const Cx<R> sv = F::ld(s, N, c, idx);
-                F::st(e, N, c, idx, cadd(F::ld(e, N, c, idx), cadd(cmul(al, F::ld(pv, N, c, idx)), cmul(om, sv))));
-                const Cx<R> rv0 = csub(sv, cmul(om, F::ld(t, N, c, idx)));
-                const Cx<R> rv = Cx<R>{rnd<S, R>(rv0.re), rnd<S, R>(rv0.im)};
-                F::st(r, N, c, idx, rv);
-                const Cx<R> z = F::ld(r0, N, c, idx);
-                vr[0] += z.re * rv.re + z.im * rv.im;
-                vr[1] += z.re * rv.im - z.im * rv.re;
-                vr[2] += rv.re * rv.re + rv.im * rv.im;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                Cx<R> sv[2], ev[2], pp[2], tv[2], zv[2], rv[2];
+                ld_pair<S, R>(s, N, k, idx, sv);
+                ld_pair<S, R>(e, N, k, idx, ev);
+                ld_pair<S, R>(pv, N, k, idx, pp);
+                ld_pair<S, R>(t, N, k, idx, tv);
+                ld_pair<S, R>(r0, N, k, idx, zv);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    ev[h] = cadd(ev[h], cadd(cmul(al, pp[h]), cmul(om, sv[h])));
+                    const Cx<R> rv0 = csub(sv[h], cmul(om, tv[h]));
+                    rv[h] = Cx<R>{rnd<S, R>(rv0.re), rnd<S, R>(rv0.im)};
+                    vr[0] += zv[h].re * rv[h].re + zv[h].im * rv[h].im;
+                    vr[1] += zv[h].re * rv[h].im - zv[h].im * rv[h].re;
+                    vr[2] += rv[h].re * rv[h].re + rv[h].im * rv[h].im;
+                }
+                st_pair<S, R>(e, N, k, idx, ev);
+                st_pair<S, R>(r, N, k, idx, rv);
             }
         SITE_LOOP_END
         item_store_r<3>(P, j, b, vr, sh);
@@ -996,9 +1013,15 @@ __global__ void __launch_bounds__(PT_BLOCK) k_bicg_dir(EP P) {
         const S *r = slot_cptr<S>(P.r, j, P.L);
         const S *q = slot_cptr<S>(P.q, j, P.L);
         SITE_LOOP(1)
-            for (int c = 0; c < 12; ++c) {
-                const Cx<R> pp = csub(F::ld(pv, N, c, idx), cmul(om, F::ld(q, N, c, idx)));
-                F::st(pv, N, c, idx, cadd(F::ld(r, N, c, idx), cmul(be, pp)));
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                Cx<R> pp[2], qv[2], rv[2];
+                ld_pair<S, R>(pv, N, k, idx, pp);
+                ld_pair<S, R>(q, N, k, idx, qv);
+                ld_pair<S, R>(r, N, k, idx, rv);
+                pp[0] = cadd(rv[0], cmul(be, csub(pp[0], cmul(om, qv[0]))));
+                pp[1] = cadd(rv[1], cmul(be, csub(pp[1], cmul(om, qv[1]))));
+                st_pair<S, R>(pv, N, k, idx, pp);
             }
         SITE_LOOP_END
     ITEM_LOOP_END

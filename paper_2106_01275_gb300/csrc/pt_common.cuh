@@ -194,6 +194,28 @@ __device__ __forceinline__ void st_cx<__nv_bfloat16, float>(__nv_bfloat16 *f, in
     reinterpret_cast<__nv_bfloat162 *>(f)[(size_t)c * N + idx] = __floats2bfloat162_rn(v.re, v.im);
 }
 
+// components (2k, 2k+1) of a spinor at one site: one 16-byte access for FP32
+template <typename S, typename R>
+__device__ __forceinline__ void ld_pair(const S *f, int N, int k, int idx, Cx<R> v[2]) {
+    if constexpr (std::is_same<S, float>::value) {
+        const float4 a = reinterpret_cast<const float4 *>(f)[(size_t)k * N + idx];
+        v[0] = Cx<R>{a.x, a.y};
+        v[1] = Cx<R>{a.z, a.w};
+    } else {
+        v[0] = ld_cx<S, R>(f, N, 2 * k, idx);
+        v[1] = ld_cx<S, R>(f, N, 2 * k + 1, idx);
+    }
+}
+template <typename S, typename R>
+__device__ __forceinline__ void st_pair(S *f, int N, int k, int idx, const Cx<R> v[2]) {
+    if constexpr (std::is_same<S, float>::value) {
+        reinterpret_cast<float4 *>(f)[(size_t)k * N + idx] = make_float4(v[0].re, v[0].im, v[1].re, v[1].im);
+    } else {
+        st_cx<S, R>(f, N, 2 * k, idx, v[0]);
+        st_cx<S, R>(f, N, 2 * k + 1, idx, v[1]);
+    }
+}
+
 // whole spinor of one site, ps[spin][colour]: six 16-byte loads for FP32,
 // twelve complex loads otherwise
 template <typename S, typename R>
