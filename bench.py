@@ -320,10 +320,10 @@ def run_ours(args):
 
 
 # DRAM bytes (read + write) per site*RHS of k_cg_apply_v4<float> from one ncu
-# capture of the lap16 small case (238 RHS, all active: 125.5 MB + 85.8 MB per
+# capture of the lap16 small case (238 RHS, all active: 124.8 MB + 83.0 MB per
 # launch; profiles/k_cg_apply_v4_lap16_small.md).  Set to None whenever the
 # kernel changes until it is captured again.
-APPLY_NCU_TRAFFIC_PER_SITE_RHS = (125.515008e6 + 85.80608e6) / (238 * 65536)
+APPLY_NCU_TRAFFIC_PER_SITE_RHS = (124.8e6 + 83.0e6) / (238 * 65536)
 
 
 def run_grad(args):
