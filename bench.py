@@ -12,7 +12,7 @@ solved (mixed FP32 CG inside FP64 defect correction to relative residual
 
 "wilson24": Wilson-Dirac on 24^3 x 48, kappa = 0.124, antiperiodic t, links
 exp(i 0.3 H) from seed 1234; displacements p = 0, 2, 4, 8 along z with their
-(p, 2) colourings, Z4 noise with 12x spin-colour dilution, 2 noise sets;
+(p, 2) colourings, Z4 noise with 12x spin-colour dilution, 4 noise sets;
 mixed FP32 BiCGStab inside FP64 defect correction to 1e-10.
 
 Reported value: operator applications x sites per second over the whole step
@@ -77,9 +77,9 @@ def workloads(case):
         if not small else "lap16 small: (p,k)=(0,4) colouring, 2 Z2 sets", m2=0.01)
     wil = Workload(
         "wilson24", "wil", [16, 16, 16, 32] if small else [24, 24, 24, 48], 2,
-        [(4, 2)] if small else [(0, 2), (2, 2), (4, 2), (8, 2)], [0, 2, 4, 8], 1 if small else 2, "z4",
+        [(4, 2)] if small else [(0, 2), (2, 2), (4, 2), (8, 2)], [0, 2, 4, 8], 1 if small else 4, "z4",
         "wilson24: Wilson-Dirac 24^3x48 kappa=0.124 antiperiodic t, p=0,2,4,8 along z with (p,2)-colourings, "
-        "Z4 x 12 spin-colour dilution, 2 sets, mixed FP32 BiCGStab + FP64 defect correction to 1e-10"
+        "Z4 x 12 spin-colour dilution, 4 sets (1584 RHS), mixed FP32 BiCGStab + FP64 defect correction to 1e-10"
         if not small else "wilson24 small: 16^3x32, (p,k)=(4,2), 1 Z4 set, 12x dilution",
         kappa=0.124, link_seed=1234, plain_subset=[3])
     return {"lap16": lap, "wilson24": wil}
@@ -189,7 +189,7 @@ def run_ours(args):
     N = W.N
     set0, _ = sharding.rank_sets(rank, W.n_sets)      # weak scaling: each rank its own noise sets
 
-    def step(prec="mixed_fp32", set_base=set0, n_sets=W.n_sets, c=cols, mm=m):
+    def step(prec=args.prec, set_base=set0, n_sets=W.n_sets, c=cols, mm=m):
         return pt.trace_multi(op, c, mm, W.mu, W.p_contract, W.noise, SEED, set_base, n_sets, True, prec,
                               TOL, MAXIT)
 
@@ -199,8 +199,8 @@ def run_ours(args):
 
     # autotune the engine on trial probes of the largest colouring (set-up, untimed)
     big = int(np.argmax(m))
-    tuning = pt.autotune(op, cols[big].contiguous(), m[big], W.mu, W.noise, SEED + 7, "mixed_fp32", TOL, MAXIT,
-                         64 if W.kind == "lap" else 24) if not args.no_tune else pt.get_tuning(op, "mixed_fp32")
+    tuning = pt.autotune(op, cols[big].contiguous(), m[big], W.mu, W.noise, SEED + 7, args.prec, TOL, MAXIT,
+                         64 if W.kind == "lap" else 24) if not args.no_tune else pt.get_tuning(op, args.prec)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -237,11 +237,13 @@ def run_ours(args):
 
     peak, peak_kind = peaks()
     b_rhs, b_launch = W.apply_bytes()
+    if args.prec == "mixed_bf16":              # half the bytes of every inner vector and link
+        b_rhs, b_launch = b_rhs / 2, (b_launch / 2 if W.kind == "lap" else 36 * 4.0)
     applies_per_iter = 1 if W.kind == "lap" else 2
     apply_bytes = inner_iters * applies_per_iter * N * b_rhs + apply_launches * N * b_launch
     achieved = apply_bytes / (apply_ms / 1e3) / 1e9 if apply_ms > 0 else None
     traffic = None
-    if W.kind == "lap" and APPLY_NCU_TRAFFIC_PER_SITE_RHS and apply_launches:
+    if W.kind == "lap" and args.prec == "mixed_fp32" and APPLY_NCU_TRAFFIC_PER_SITE_RHS and apply_launches:
         traffic = APPLY_NCU_TRAFFIC_PER_SITE_RHS * inner_iters * N / apply_launches
     roofline = {"bound": "hbm",
                 "kernel": "k_cg_apply_v4<float> (p update + stencil + p.q)" if W.kind == "lap"
@@ -259,7 +261,9 @@ def run_ours(args):
 
     out = {"metric": METRIC, "value": value, "unit": "site*RHS/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 inner / f64 outer" if args.prec == "mixed_fp32" else "bf16 storage, f32 arith / f64 outer",
+           "data": "synthetic",
            "config": {"workload": W.desc, "lattice": W.dims, "n_rhs_per_step": int(stats[-1]["n_rhs"]),
                       "n_colours": m, "parallelism": "rhs-batched, %d rank(s), weak" % world,
                       "tuning": tuning,
@@ -521,6 +525,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--skip-baselines", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="use the engine's default parameters")
+    ap.add_argument("--prec", default="mixed_fp32", choices=["mixed_fp32", "mixed_bf16"],
+                    help="inner Krylov storage: FP32, or BF16 (FP32 arithmetic); FP64 outer either way")
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: one colouring and few right-hand sides (for profiler captures)")
     args = ap.parse_args()

@@ -312,6 +312,70 @@ def test_grad_kappa_finite_difference_gpu(pt, ctx):
     assert abs(dk - fd) <= 1e-5 * abs(fd)
 
 
+def test_grad_fd_8to4_kappa_and_links(pt, ctx):
+    """The finite-difference check of the adjoint at its stated size: 8^4,
+    kappa = 0.12, central differences with step 1e-5 of FP64 GPU traces, for
+    dT/dkappa and for the real and imaginary parts of sampled link entries."""
+    import torch
+    dims, kappa, p, mu = [8, 8, 8, 8], 0.12, 1, 2
+    U = inputs.gauge_links(dims, 4321)
+    colv, m = greedy_colour(dims, mu, [p], 1, 0)
+    col = _t(colv)
+    Ud = _t(U)
+    op = pt.wilson(ctx, dims, Ud, kappa, True)
+    _, dk, G, Gb, _ = pt.grad(op, col, m, mu, p, "z4", 17, 0, 1, False, "fp64", 1e-12, 5000, links=True)
+    G, Gb = G.cpu().numpy(), Gb.cpu().numpy()
+    h = 1e-5
+
+    def T(kap, Udev):
+        o = pt.wilson(ctx, dims, Udev, kap, True)
+        est = pt.trace(o, col, m, mu, [p], "z4", 17, 0, 1, False, "fp64", 1e-13, 5000)[0]
+        o.close()
+        return est[0, 0]
+
+    fd = (T(kappa + h, Ud) - T(kappa - h, Ud)) / (2 * h)
+    assert abs(dk - fd) <= 1e-5 * abs(fd)
+    r = np.random.default_rng(1)
+    for _ in range(3):
+        n, nu, a, b = int(r.integers(4096)), int(r.integers(4)), int(r.integers(3)), int(r.integers(3))
+        for part, dz in (("re", h), ("im", 1j * h)):
+            Up, Um = Ud.clone(), Ud.clone()
+            Up[n, nu, a, b] += dz
+            Um[n, nu, a, b] -= dz
+            fdl = (T(kappa, Up) - T(kappa, Um)) / (2 * h)
+            an = (G + Gb)[n, nu, a, b] if part == "re" else 1j * (G - Gb)[n, nu, a, b]
+            assert abs(an - fdl) <= 1e-5 * max(abs(fdl), 1e-2 * np.max(np.abs(G))), (n, nu, a, b, part)
+
+
+def test_wilson_8c16_mixed_vs_fp64_and_sampled_oracle(pt, ctx):
+    """The 8^3 x 16 Wilson configuration (kappa 0.12, antiperiodic t, (p, 2)
+    colourings for displacements along z, Z4 noise, 12x dilution): mixed FP32
+    and BF16-storage estimates equal the FP64 ones to 1e-8 for every
+    displacement p = 1..8 contracted from one solve per probe, and a sample of
+    the probes solved one by one matches the oracle's BiCGStab solutions."""
+    dims, kappa, mu = [8, 8, 8, 16], 0.12, 2
+    U = inputs.gauge_links(dims, 1234)
+    op = pt.wilson(ctx, dims, _t(U), kappa, True)
+    plist = list(range(1, 9))
+    for p in (1, 4):
+        colv, m = greedy_colour(dims, mu, [p], 2, 1)
+        col = _t(colv)
+        e64 = pt.trace(op, col, m, mu, plist, "z4", 1000, 0, 1, True, "fp64", 1e-10, 5000)[0]
+        for prec in ("mixed_fp32", "mixed_bf16"):
+            e = pt.trace(op, col, m, mu, plist, "z4", 1000, 0, 1, True, prec, 1e-10, 5000)[0]
+            assert np.allclose(e, e64, rtol=1e-8, atol=1e-6), (p, prec)
+    # sampled solves against the oracle
+    from oracle.estimator import Wilson
+    ow = Wilson(dims, U, kappa)
+    colv, m = greedy_colour(dims, mu, [4], 2, 1)
+    for c, a in ((0, 0), (m - 1, 7)):
+        v = o_probe(colv, c, 1000, 0, 1, 12, a)
+        x_o, _, _ = ow.solve(v, 1e-12)
+        X, _, rel, _ = pt.solve(op, _t(v.reshape(1, -1, 4, 3)), "mixed_fp32", 1e-10, 5000)
+        x = X.cpu().numpy().reshape(-1, 12)
+        assert np.linalg.norm(x - x_o) <= 1e-8 * np.linalg.norm(x_o)
+
+
 # ------------------------------------------------------------------ autotuner
 def test_autotune_then_parity(pt, ctx):
     """The autotuner picks parameters from its candidate sets, stores them for
