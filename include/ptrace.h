@@ -225,6 +225,50 @@ PT_API int pt_colour_conflicts(pt_ctx *ctx, const int dims[4], int mu, const int
 PT_API int pt_colour_conflicts_noalloc(void *stream, const int dims[4], int mu, const int *p_list, int n_p,
                                        int k, const int32_t *col_dev, int64_t *n_conflicts);
 
+/* ------------------------------------------------------------------ tiles */
+
+/* Tile of Sec. 3.5 for a (p_list, k)-colouring of the lattice `dims`
+ * (host-only, no GPU needed).  A tile holds a whole neighbourhood: every side
+ * at least 2k + 1, the side along mu at least 2(max p + k) + 1.  Its sides
+ * divide the lattice's: each is the smallest divisor of the lattice side at
+ * or above the minimum (the smallest power of two above it on power-of-two
+ * lattices, as in Table 2), else the lattice side.  tile_out: 4 ints (host).
+ * PT_ERR_ARG on a NULL pointer, mu outside 0..3, k outside 0..64, n_p outside
+ * 1..64 or p outside 0..4096. */
+PT_API int pt_tile_dims(const int dims[4], int mu, const int *p_list, int n_p, int k, int tile_out[4]);
+
+/* Repeat a tile's colouring over the lattice (Sec. 3.5):
+ * col[x] = tile_col[x mod tile_dims].  tile_col_dev: int32 [prod tile_dims]
+ * (device, read); col_dev: int32 [prod dims] (device, written); the two must
+ * not overlap.  Every tile side must divide the lattice side (PT_ERR_ARG).
+ * Asynchronous on the context stream. */
+PT_API int pt_tile_replicate(pt_ctx *ctx, const int tile_dims[4], const int32_t *tile_col_dev, const int dims[4],
+                             int32_t *col_dev);
+
+/* pt_colour on the tile of pt_tile_dims, repeated over the lattice by
+ * pt_tile_replicate.  col_dev: int32 [N] of the lattice (device, written);
+ * *n_colours (host): the tile's colour count; tile_out (host, 4 ints): the
+ * tile used.  The tile's colours live in a temporary device buffer
+ * (stream-ordered allocation, freed before returning).  Synchronises the
+ * context stream. */
+PT_API int pt_colour_tiled(pt_ctx *ctx, const int dims[4], int mu, const int *p_list, int n_p, int k, int order,
+                           int32_t *col_dev, int *n_colours, int tile_out[4]);
+
+/* Clearance of a colouring at other displacements (Thm 3.6; Sec. 4.3, Table
+ * 5).  For every displacement p = p_list[i] along mu and distance
+ * k = k_list[j], the shell S_x(p, k) is the set of nodes y != x of the torus
+ * whose L1 distance to the nearer of x + p e_mu and x - p e_mu is exactly k
+ * (each node counted once).  Outputs (host, int64 [n_p][n_k], row i = p):
+ *   matches_out[i][j] = sum over x of #{y in S_x(p, k) : col(y) = col(x)},
+ *   shell_out[i][j]   = |S_x(p, k)| (the same for every x).
+ * The average percentage of uncleared neighbours printed in Table 5 is
+ * 100 matches / (N |S|).  col_dev: int32 [N] (device, read).  Lattice sides
+ * 1..65535, 1 <= n_p, n_k <= 64, p in 0..4096, k in 0..32; all distinct
+ * offsets of the requested shells together at most 524,280.  Synchronises
+ * the context stream. */
+PT_API int pt_clearance(pt_ctx *ctx, const int dims[4], int mu, const int32_t *col_dev, const int *p_list, int n_p,
+                        const int *k_list, int n_k, int64_t *matches_out, int64_t *shell_out);
+
 /* ------------------------------------------------------------------- probes */
 
 /* Materialise one probing vector (Eq. (3) with the noise of Eq. (5) and the

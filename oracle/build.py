@@ -10,7 +10,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liboracle.so")
-SOURCES = [os.path.join(HERE, "greedy_colour.c")]
+SOURCES = [os.path.join(HERE, "greedy_colour.c"), os.path.join(HERE, "clearance.c")]
 
 
 def build(force=False):

@@ -75,3 +75,27 @@ def tile_replicate(tile_col, tile_dims, dims):
             raise ValueError("tile side must divide the lattice side")
     xs = coords(dims)
     return np.asarray(tile_col)[index_of(xs % np.asarray(tile_dims), tile_dims)]
+
+
+def first_fit_violations(col, dims, mu, p_list, k, order, sites):
+    """Sites x (of `sites`) whose colour is not the smallest colour absent
+    among the neighbours of N(x, p, k) visited before x (Algorithm 1).  When
+    no site of the lattice violates it, `col` is the greedy colouring itself
+    (by induction over the visit order), so a sample of sites checks a
+    colouring too large to recompute."""
+    d = len(dims)
+    st = displaced_stencil(d, mu, p_list, k)
+    visit = visit_order(dims, mu, order)
+    rank = np.empty_like(visit)
+    rank[visit] = np.arange(visit.shape[0])
+    col = np.asarray(col)
+    xs = coords(dims)
+    bad = []
+    for x in sites:
+        nb = index_of(xs[x][None, :] + st, dims)
+        nb = nb[(nb != x) & (rank[nb] < rank[x])]
+        earlier = np.zeros(len(st) + 2, dtype=bool)
+        earlier[col[nb]] = True
+        if int(col[x]) != int(np.argmin(earlier)):
+            bad.append(int(x))
+    return bad

@@ -20,11 +20,19 @@ int oracle_greedy_colour(int d, const int *dims, int n_off, const int *offsets,
     for (int mu = 0; mu < d; ++mu) N *= dims[mu];
     for (int64_t i = 0; i < N; ++i) col[i] = -1;
 
+    /* each offset reduced once to [0, D_mu) per dimension, so that the
+     * neighbour's coordinate needs at most one subtraction of D_mu */
+    int *red = (int *)malloc(sizeof(int) * (size_t)(n_off > 0 ? n_off : 1) * (size_t)d);
     /* used[c] == stamp  <=>  colour c is taken in the current neighbourhood */
     int64_t *used = (int64_t *)calloc((size_t)n_off + 2, sizeof(int64_t));
-    if (!used) return -1;
+    if (!used || !red) { free(used); free(red); return -1; }
+    for (int o = 0; o < n_off; ++o)
+        for (int mu = 0; mu < d; ++mu) {
+            int c = offsets[o * d + mu] % dims[mu];
+            red[o * d + mu] = c < 0 ? c + dims[mu] : c;
+        }
     int n_colours = 0;
-    int x[8], y[8];
+    int x[8];
     for (int64_t t = 0; t < N; ++t) {
         int64_t site = visit[t];
         int64_t stamp = t + 1;
@@ -33,11 +41,9 @@ int oracle_greedy_colour(int d, const int *dims, int n_off, const int *offsets,
         for (int o = 0; o < n_off; ++o) {
             int64_t idx = 0, stride = 1;
             for (int mu = 0; mu < d; ++mu) {
-                int c = x[mu] + offsets[o * d + mu];
-                c %= dims[mu];
-                if (c < 0) c += dims[mu];
-                y[mu] = c;
-                idx += (int64_t)y[mu] * stride;
+                int c = x[mu] + red[o * d + mu];
+                if (c >= dims[mu]) c -= dims[mu];
+                idx += (int64_t)c * stride;
                 stride *= dims[mu];
             }
             if (idx == site) continue;          /* x is excluded from N(x,p,k) */
@@ -49,6 +55,7 @@ int oracle_greedy_colour(int d, const int *dims, int n_off, const int *offsets,
         col[site] = c;
         if (c + 1 > n_colours) n_colours = c + 1;
     }
+    free(red);
     free(used);
     return n_colours;
 }

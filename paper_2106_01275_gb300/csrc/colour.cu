@@ -9,6 +9,7 @@
 // free colour with ballots.  Colours live in shared memory (16-bit) when the
 // lattice fits, else in global memory.  Two bit masks alternate so that each
 // node needs two barriers.
+#include <limits.h>
 #include <string.h>
 
 #include <algorithm>
@@ -71,62 +72,103 @@ __device__ __forceinline__ int offset_site(const Geom &g, const int x[4], int4 o
 }
 
 #define PT_UNCOLOURED 0xFFFFu
+#define PT_WALK_U 16
 
-template <bool SHARED_COL>
-__global__ void __launch_bounds__(1024) k_colour_walk(Geom g, const int4 *__restrict__ off, int n_off,
-                                                      const int *__restrict__ visit, int32_t *col, int n_words,
+// Walk offsets: every stencil offset reduced to [0, D_mu) per dimension and
+// packed as two 16-bit pairs (o0 | o1 << 16, o2 | o3 << 16).  Offsets equal
+// modulo the lattice reach the same node and are merged; the one equal to 0
+// (x itself, excluded from N(x, p, k)) is dropped.  The neighbour's
+// coordinate is then x + o with at most one subtraction of D.
+__device__ __forceinline__ int walk_site(const Geom &g, const int x[4], uint2 o) {
+    int c0 = x[0] + (int)(o.x & 0xffffu); c0 -= (c0 >= g.D[0]) ? g.D[0] : 0;
+    int c1 = x[1] + (int)(o.x >> 16);     c1 -= (c1 >= g.D[1]) ? g.D[1] : 0;
+    int c2 = x[2] + (int)(o.y & 0xffffu); c2 -= (c2 >= g.D[2]) ? g.D[2] : 0;
+    int c3 = x[3] + (int)(o.y >> 16);     c3 -= (c3 >= g.D[3]) ? g.D[3] : 0;
+    return c0 + g.stride[1] * c1 + g.stride[2] * c2 + g.stride[3] * c3;
+}
+
+// One node per step, three phases and two barriers per node:
+//   gather  every thread takes its share of the offsets, loads the colours of
+//           the neighbours (PT_WALK_U loads in flight before any is used) and
+//           stamps each colour seen: stamp[c] = step (a plain store; threads
+//           that see the same colour write the same value);
+//   search  the first colour c in [0, m] without this step's stamp, m the
+//           colours used so far: each thread checks its stride of c, warps
+//           reduce, one shared atomicMin per warp;
+//   commit  every thread reads the winner; thread 0 stores it.
+// Stamps grow with the step, so they are never cleared.  The node coloured in
+// one step may be a neighbour of the next node before its colour store is
+// visible to the other threads, so every thread keeps (node, colour) of the
+// previous step and uses it in the next gather.  Shared memory: the stamps
+// (n_stamp ints), then (SHARED_OFF) the packed offsets, then (SHARED_COL) the
+// 16-bit colours of all N nodes.
+template <bool SHARED_COL, bool SHARED_OFF>
+__global__ void __launch_bounds__(1024, 1) k_colour_walk(Geom g, const uint2 *__restrict__ off_g, int n_off,
+                                                      const int *__restrict__ visit, int32_t *col, int n_stamp,
                                                       int *out) {
-    extern __shared__ unsigned smem[];
-    unsigned *used0 = smem;
-    unsigned *used1 = smem + n_words;
-    unsigned short *scol = reinterpret_cast<unsigned short *>(smem + 2 * n_words);
-    __shared__ int s_max;
+    extern __shared__ int smem_i[];
+    int *stamp = smem_i;
+    uint2 *soff = reinterpret_cast<uint2 *>(smem_i + ((n_stamp + 1) & ~1));
+    unsigned short *scol = reinterpret_cast<unsigned short *>(soff + (SHARED_OFF ? n_off : 0));
+    const uint2 *off = SHARED_OFF ? soff : off_g;
+    __shared__ int s_found[2];
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int w = tid; w < 2 * n_words; w += nt) smem[w] = 0u;
+    for (int c = tid; c < n_stamp; c += nt) stamp[c] = 0;
+    if (SHARED_OFF)
+        for (int o = tid; o < n_off; o += nt) soff[o] = off_g[o];
     if (SHARED_COL)
         for (int i = tid; i < g.N; i += nt) scol[i] = PT_UNCOLOURED;
     else
         for (int i = tid; i < g.N; i += nt) col[i] = -1;
-    if (tid == 0) s_max = 0;
+    if (tid == 0) s_found[0] = s_found[1] = INT_MAX;
     __syncthreads();
+    int m = 0;                       // colours used so far (the same in every thread)
+    int prev_x = -1, prev_c = -1;    // node and colour of the previous step
+    int xs_next = visit[0];
     for (int t = 0; t < g.N; ++t) {
-        unsigned *used = (t & 1) ? used1 : used0;
-        unsigned *other = (t & 1) ? used0 : used1;
-        const int xs = visit[t];
+        const int step = t + 1;
+        const int xs = xs_next;
+        if (t + 1 < g.N) xs_next = visit[t + 1];          // in flight during this node's gather
         int x[4];
         site_coords(g, xs, x);
-        // clear the mask of the next node while gathering this one
-        for (int w = tid; w < n_words; w += nt) other[w] = 0u;
-        for (int o = tid; o < n_off; o += nt) {
-            int y = offset_site(g, x, off[o]);
-            if (y == xs) continue;                       // x is not its own neighbour
-            int c = SHARED_COL ? (int)scol[y] : col[y];
-            if (SHARED_COL ? (c != (int)PT_UNCOLOURED) : (c >= 0)) atomicOr(&used[c >> 5], 1u << (c & 31));
-        }
-        __syncthreads();
-        if (tid < 32) {
-            int found = -1;
-            for (int base = 0; base < n_words && found < 0; base += 32) {
-                int w = base + tid;
-                unsigned inv = (w < n_words) ? ~used[w] : 0u;
-                unsigned bal = __ballot_sync(0xffffffffu, inv != 0u);
-                if (bal) {
-                    int l = __ffs(bal) - 1;
-                    unsigned v = __shfl_sync(0xffffffffu, inv, l);
-                    found = (base + l) * 32 + __ffs(v) - 1;
+        for (int base = tid; base < n_off; base += nt * PT_WALK_U) {
+            int cv[PT_WALK_U];
+#pragma unroll
+            for (int u = 0; u < PT_WALK_U; ++u) {
+                const int o = base + u * nt;
+                cv[u] = -1;
+                if (o < n_off) {
+                    const int y = walk_site(g, x, off[o]);
+                    int c = SHARED_COL ? (int)scol[y] : col[y];
+                    if (SHARED_COL && c == (int)PT_UNCOLOURED) c = -1;
+                    cv[u] = (y == prev_x) ? prev_c : c;
                 }
             }
-            if (tid == 0) {
-                if (SHARED_COL) scol[xs] = (unsigned short)found;
-                else col[xs] = found;
-                if (found + 1 > s_max) s_max = found + 1;
-            }
+#pragma unroll
+            for (int u = 0; u < PT_WALK_U; ++u)
+                if (cv[u] >= 0) stamp[cv[u]] = step;
         }
         __syncthreads();
+        int best = INT_MAX;
+        for (int c = tid; c <= m; c += nt)
+            if (stamp[c] != step) { best = c; break; }
+        best = __reduce_min_sync(0xffffffffu, best);
+        if ((tid & 31) == 0 && best != INT_MAX) atomicMin(&s_found[t & 1], best);
+        __syncthreads();
+        const int found = s_found[t & 1];
+        if (tid == 0) {
+            if (SHARED_COL) scol[xs] = (unsigned short)found;
+            else col[xs] = found;
+            s_found[(t + 1) & 1] = INT_MAX;               // read by nobody before the next step's first barrier
+        }
+        if (found + 1 > m) m = found + 1;
+        prev_x = xs;
+        prev_c = found;
     }
+    __syncthreads();
     if (SHARED_COL)
         for (int i = tid; i < g.N; i += nt) col[i] = (int32_t)scol[i];
-    if (tid == 0) out[0] = s_max;
+    if (tid == 0) out[0] = m;
 }
 
 __global__ void k_colour_conflicts(Geom g, const int4 *__restrict__ off, int n_off, const int32_t *__restrict__ col,
@@ -196,30 +238,70 @@ static int prep(pt_ctx *c, const int dims[4], int mu, const int *p_list, int n_p
     return PT_OK;
 }
 
+// Offsets of the walk: reduced modulo the lattice, merged, x itself dropped,
+// packed (see walk_site).  Sides are below 65536 (PT_CHECK in the caller).
+static std::vector<uint2> walk_offsets(const std::vector<int> &st, const int dims[4]) {
+    std::vector<uint64_t> keys;
+    keys.reserve(st.size() / 4);
+    for (size_t i = 0; i < st.size(); i += 4) {
+        uint64_t key = 0;
+        bool zero = true;
+        for (int nu = 0; nu < 4; ++nu) {
+            int c = st[i + nu] % dims[nu];
+            if (c < 0) c += dims[nu];
+            zero = zero && c == 0;
+            key |= (uint64_t)c << (16 * nu);
+        }
+        if (!zero) keys.push_back(key);
+    }
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    std::vector<uint2> out(keys.size());
+    for (size_t i = 0; i < keys.size(); ++i) out[i] = make_uint2((unsigned)keys[i], (unsigned)(keys[i] >> 32));
+    return out;
+}
+
 extern "C" int pt_colour(pt_ctx *c, const int dims[4], int mu, const int *p_list, int n_p, int k, int order,
                          int32_t *col_dev, int *n_colours) {
     PT_CHECK_ARG(c && col_dev && n_colours, "pt_colour: NULL argument");
+    PT_CHECK_ARG(dims && dims[0] < 65536 && dims[1] < 65536 && dims[2] < 65536 && dims[3] < 65536,
+                 "pt_colour: lattice sides must be below 65536");
     PT_CUDA(cudaSetDevice(c->device));
     ColourPrep cp;
     int rc = prep(c, dims, mu, p_list, n_p, k, order, true, cp);
     if (rc) return rc;
     Geom g = make_geom(dims);
-    int n_words = (cp.n_off + 2 + 31) / 32;
-    size_t mask_b = 2 * (size_t)n_words * sizeof(unsigned);
-    size_t shared_b = mask_b + (size_t)g.N * sizeof(unsigned short);
+    std::vector<int> st;
+    build_stencil(mu, p_list, n_p, k, st);
+    std::vector<uint2> wo = walk_offsets(st, dims);
+    const int n_off = (int)wo.size();
+    // the packed offsets take the place of the int4 stencil in the workspace (8 <= 16 bytes per row)
+    uint2 *d_off = reinterpret_cast<uint2 *>(cp.d_off);
+    if (n_off) PT_CUDA(cudaMemcpyAsync(d_off, wo.data(), wo.size() * sizeof(uint2), cudaMemcpyHostToDevice, c->stream));
+    // a node's colour never exceeds its number of neighbours: stamps for 0..n_off
+    const int n_stamp = n_off + 2;
+    const size_t stamp_b = (size_t)((n_stamp + 1) & ~1) * sizeof(int);
+    size_t off_b = (size_t)n_off * sizeof(uint2);
+    size_t col_b = (size_t)g.N * sizeof(unsigned short);
     int max_smem = 0;
     PT_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     max_smem -= 1024;  // static shared memory of the kernel
-    if (shared_b <= (size_t)max_smem) {
-        PT_CUDA(cudaFuncSetAttribute(k_colour_walk<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shared_b));
-        k_colour_walk<true><<<1, 1024, shared_b, c->stream>>>(g, cp.d_off, cp.n_off, cp.d_visit, col_dev, n_words,
-                                                              cp.d_out);
-    } else {
-        PT_CHECK_ARG(mask_b <= (size_t)max_smem, "pt_colour: stencil too large for the shared bit mask");
-        PT_CUDA(cudaFuncSetAttribute(k_colour_walk<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mask_b));
-        k_colour_walk<false><<<1, 1024, mask_b, c->stream>>>(g, cp.d_off, cp.n_off, cp.d_visit, col_dev, n_words,
-                                                             cp.d_out);
-    }
+    PT_CHECK_ARG(stamp_b <= (size_t)max_smem, "pt_colour: stencil too large for the shared colour stamps");
+    const bool sh_col = stamp_b + col_b <= (size_t)max_smem;
+    const bool sh_off = stamp_b + off_b + (sh_col ? col_b : 0) <= (size_t)max_smem;
+    size_t shared_b = stamp_b + (sh_off ? off_b : 0) + (sh_col ? col_b : 0);
+#define PT_WALK(SC, SO)                                                                                          \
+    do {                                                                                                         \
+        PT_CUDA(cudaFuncSetAttribute(k_colour_walk<SC, SO>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+                                     (int)shared_b));                                                            \
+        k_colour_walk<SC, SO><<<1, 1024, shared_b, c->stream>>>(g, d_off, n_off, cp.d_visit, col_dev, n_stamp,   \
+                                                                cp.d_out);                                       \
+    } while (0)
+    if (sh_col && sh_off) PT_WALK(true, true);
+    else if (sh_col) PT_WALK(true, false);
+    else if (sh_off) PT_WALK(false, true);
+    else PT_WALK(false, false);
+#undef PT_WALK
     ++pt_kernel_launch_count;
     PT_CUDA(cudaGetLastError());
     PT_CUDA(cudaMemcpyAsync(c->h_flags, cp.d_out, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -245,5 +327,248 @@ extern "C" int pt_colour_conflicts(pt_ctx *c, const int dims[4], int mu, const i
     PT_CUDA(cudaStreamSynchronize(c->stream));
     memcpy(&h, c->h_flags, sizeof(h));
     *n_conflicts = (int64_t)h;
+    return PT_OK;
+}
+
+// ------------------------------------------------------------------ tiles
+// Tile policy of Sec. 3.5: every side at least 2k + 1, the displaced side at
+// least 2(p_max + k) + 1, each side the smallest divisor of the lattice side
+// at or above that minimum (a power of two for power-of-two lattices), else
+// the lattice side itself.
+
+static int tile_side(int D, int need) {
+    for (int t = 1; t <= D; ++t)
+        if (D % t == 0 && t >= need) return t;
+    return D;
+}
+
+extern "C" int pt_tile_dims(const int dims[4], int mu, const int *p_list, int n_p, int k, int tile_out[4]) {
+    PT_CHECK_ARG(dims && p_list && tile_out && n_p >= 1 && n_p <= 64 && mu >= 0 && mu <= 3 && k >= 0 && k <= 64,
+                 "pt_tile_dims: invalid arguments");
+    int pmax = 0;
+    for (int n = 0; n < n_p; ++n) {
+        PT_CHECK_ARG(p_list[n] >= 0 && p_list[n] <= 4096, "pt_tile_dims: displacement %d out of range", p_list[n]);
+        pmax = std::max(pmax, p_list[n]);
+    }
+    for (int nu = 0; nu < 4; ++nu) {
+        PT_CHECK_ARG(dims[nu] >= 1, "pt_tile_dims: bad lattice side");
+        int need = (nu == mu) ? 2 * (pmax + k) + 1 : 2 * k + 1;
+        tile_out[nu] = tile_side(dims[nu], need);
+    }
+    return PT_OK;
+}
+
+__global__ void k_tile_replicate(Geom g, Geom tg, const int32_t *__restrict__ tcol, int32_t *__restrict__ col) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += gridDim.x * blockDim.x) {
+        int x[4];
+        site_coords(g, i, x);
+        int j = (x[0] % tg.D[0]) + tg.stride[1] * (x[1] % tg.D[1]) + tg.stride[2] * (x[2] % tg.D[2]) +
+                tg.stride[3] * (x[3] % tg.D[3]);
+        col[i] = tcol[j];
+    }
+}
+
+extern "C" int pt_tile_replicate(pt_ctx *c, const int tile_dims[4], const int32_t *tile_col_dev, const int dims[4],
+                                 int32_t *col_dev) {
+    PT_CHECK_ARG(c && tile_dims && tile_col_dev && dims && col_dev, "pt_tile_replicate: NULL argument");
+    for (int nu = 0; nu < 4; ++nu)
+        PT_CHECK_ARG(tile_dims[nu] >= 1 && dims[nu] >= 1 && dims[nu] % tile_dims[nu] == 0,
+                     "pt_tile_replicate: tile side %d does not divide lattice side %d", tile_dims[nu], dims[nu]);
+    Geom g = make_geom(dims), tg = make_geom(tile_dims);
+    PT_CHECK_ARG(tile_col_dev + tg.N <= col_dev || col_dev + g.N <= tile_col_dev,
+                 "pt_tile_replicate: tile and lattice colourings overlap");
+    PT_CUDA(cudaSetDevice(c->device));
+    int blocks = (int)std::min<long>(((long)g.N + 255) / 256, 16L * c->num_sms);
+    k_tile_replicate<<<blocks, 256, 0, c->stream>>>(g, tg, tile_col_dev, col_dev);
+    ++pt_kernel_launch_count;
+    PT_CUDA(cudaGetLastError());
+    return PT_OK;
+}
+
+extern "C" int pt_colour_tiled(pt_ctx *c, const int dims[4], int mu, const int *p_list, int n_p, int k, int order,
+                               int32_t *col_dev, int *n_colours, int tile_out[4]) {
+    PT_CHECK_ARG(c && dims && col_dev && n_colours && tile_out, "pt_colour_tiled: NULL argument");
+    int rc = pt_tile_dims(dims, mu, p_list, n_p, k, tile_out);
+    if (rc) return rc;
+    if (tile_out[0] == dims[0] && tile_out[1] == dims[1] && tile_out[2] == dims[2] && tile_out[3] == dims[3])
+        return pt_colour(c, dims, mu, p_list, n_p, k, order, col_dev, n_colours);
+    PT_CUDA(cudaSetDevice(c->device));
+    size_t nt = (size_t)tile_out[0] * tile_out[1] * tile_out[2] * tile_out[3];
+    int32_t *tcol = nullptr;
+    PT_CUDA(cudaMallocAsync((void **)&tcol, nt * sizeof(int32_t), c->stream));
+    rc = pt_colour(c, tile_out, mu, p_list, n_p, k, order, tcol, n_colours);
+    if (rc == PT_OK) rc = pt_tile_replicate(c, tile_out, tcol, dims, col_dev);
+    cudaFreeAsync(tcol, c->stream);
+    if (rc == PT_OK) PT_CUDA(cudaStreamSynchronize(c->stream));
+    return rc;
+}
+
+// -------------------------------------------------------------- clearance
+// Table 5 (Sec. 4.3): for displacement p and distance k, the shell S(p, k) is
+// the set of nodes y != x whose distance to the nearer of x + p e_mu and
+// x - p e_mu is exactly k; the statistic is the number of (x, y in S_x) pairs
+// with equal colours.  On the torus the shell's offsets, reduced mod D, are
+// the same for every x, so the count is a sum over the shell's offsets of
+// F(o) = #{x : col(x) = col(x + o)}.  F is computed once per distinct offset
+// of all requested shells, then summed per shell.
+
+static uint64_t pack_offset(const int o[4], const int dims[4], bool *zero) {
+    uint64_t key = 0;
+    *zero = true;
+    for (int nu = 0; nu < 4; ++nu) {
+        int c = o[nu] % dims[nu];
+        if (c < 0) c += dims[nu];
+        *zero = *zero && c == 0;
+        key |= (uint64_t)c << (16 * nu);
+    }
+    return key;
+}
+
+static void shell_keys(const int dims[4], int mu, int p, int k, std::vector<uint64_t> &keys) {
+    keys.clear();
+    int rest[3], r = 0;
+    for (int nu = 0; nu < 4; ++nu)
+        if (nu != mu) rest[r++] = nu;
+    for (int a = -k; a <= k; ++a)
+        for (int b = -(k - abs(a)); b <= k - abs(a); ++b)
+            for (int e = -(k - abs(a) - abs(b)); e <= k - abs(a) - abs(b); ++e) {
+                const int t = k - abs(a) - abs(b) - abs(e);  // distance left along mu
+                const int cand[4] = {p + t, p - t, t - p, -p - t};
+                for (int q = 0; q < 4; ++q) {
+                    const int om = cand[q];
+                    if (std::min(abs(om - p), abs(om + p)) != t) continue;
+                    int o[4];
+                    o[mu] = om;
+                    o[rest[0]] = a;
+                    o[rest[1]] = b;
+                    o[rest[2]] = e;
+                    bool zero;
+                    uint64_t key = pack_offset(o, dims, &zero);
+                    if (!zero) keys.push_back(key);
+                }
+            }
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+}
+
+#define PT_CLR_OB 8
+#define PT_CLR_SITES 4096
+
+// F(o) for a block of PT_CLR_OB offsets over a block of PT_CLR_SITES nodes:
+// every thread keeps one counter per offset, warps reduce, the CTA adds one
+// value per offset to F.
+__global__ void __launch_bounds__(256) k_offset_matches(Geom g, const int32_t *__restrict__ col,
+                                                        const uint2 *__restrict__ off, int n_off,
+                                                        unsigned long long *__restrict__ F) {
+    __shared__ uint2 so[PT_CLR_OB];
+    __shared__ unsigned sc[PT_CLR_OB];
+    const int o0 = blockIdx.y * PT_CLR_OB;
+    const int nb = min(PT_CLR_OB, n_off - o0);
+    if (threadIdx.x < PT_CLR_OB) {
+        so[threadIdx.x] = (int)threadIdx.x < nb ? off[o0 + threadIdx.x] : make_uint2(0u, 0u);
+        sc[threadIdx.x] = 0u;
+    }
+    __syncthreads();
+    unsigned cnt[PT_CLR_OB];
+#pragma unroll
+    for (int o = 0; o < PT_CLR_OB; ++o) cnt[o] = 0u;
+    const int begin = blockIdx.x * PT_CLR_SITES;
+    const int end = min(g.N, begin + PT_CLR_SITES);
+    for (int xs = begin + threadIdx.x; xs < end; xs += blockDim.x) {
+        int x[4];
+        site_coords(g, xs, x);
+        const int cx = col[xs];
+#pragma unroll
+        for (int o = 0; o < PT_CLR_OB; ++o) cnt[o] += (unsigned)(col[walk_site(g, x, so[o])] == cx);
+    }
+#pragma unroll
+    for (int o = 0; o < PT_CLR_OB; ++o) {
+        unsigned v = __reduce_add_sync(0xffffffffu, cnt[o]);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&sc[o], v);
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nb && sc[threadIdx.x]) atomicAdd(&F[o0 + threadIdx.x], (unsigned long long)sc[threadIdx.x]);
+}
+
+// one CTA per shell: the sum of F over the shell's offsets
+__global__ void __launch_bounds__(256) k_shell_sums(const unsigned long long *__restrict__ F,
+                                                    const int *__restrict__ idx, const int *__restrict__ start,
+                                                    unsigned long long *__restrict__ out) {
+    __shared__ unsigned long long sh[8];
+    unsigned long long s = 0;
+    for (int i = start[blockIdx.x] + threadIdx.x; i < start[blockIdx.x + 1]; i += blockDim.x) s += F[idx[i]];
+    for (int d = 16; d; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        out[blockIdx.x] = t;
+    }
+}
+
+extern "C" int pt_clearance(pt_ctx *c, const int dims[4], int mu, const int32_t *col_dev, const int *p_list, int n_p,
+                            const int *k_list, int n_k, int64_t *matches_out, int64_t *shell_out) {
+    PT_CHECK_ARG(c && dims && col_dev && p_list && k_list && matches_out && shell_out, "pt_clearance: NULL argument");
+    PT_CHECK_ARG(mu >= 0 && mu <= 3 && n_p >= 1 && n_p <= 64 && n_k >= 1 && n_k <= 64,
+                 "pt_clearance: mu in 0..3, 1 <= n_p, n_k <= 64");
+    for (int nu = 0; nu < 4; ++nu)
+        PT_CHECK_ARG(dims[nu] >= 1 && dims[nu] < 65536, "pt_clearance: lattice sides must be in 1..65535");
+    for (int i = 0; i < n_p; ++i) PT_CHECK_ARG(p_list[i] >= 0 && p_list[i] <= 4096, "pt_clearance: bad p");
+    for (int j = 0; j < n_k; ++j) PT_CHECK_ARG(k_list[j] >= 0 && k_list[j] <= 32, "pt_clearance: k in 0..32");
+    PT_CUDA(cudaSetDevice(c->device));
+    Geom g = make_geom(dims);
+    const int n_pairs = n_p * n_k;
+    std::vector<std::vector<uint64_t>> shells(n_pairs);
+    std::vector<uint64_t> all;
+    for (int i = 0; i < n_p; ++i)
+        for (int j = 0; j < n_k; ++j) {
+            shell_keys(dims, mu, p_list[i], k_list[j], shells[i * n_k + j]);
+            all.insert(all.end(), shells[i * n_k + j].begin(), shells[i * n_k + j].end());
+        }
+    std::sort(all.begin(), all.end());
+    all.erase(std::unique(all.begin(), all.end()), all.end());
+    const int n_off = (int)all.size();
+    PT_CHECK_ARG((n_off + PT_CLR_OB - 1) / PT_CLR_OB <= 65535, "pt_clearance: %d distinct offsets exceed one launch",
+                 n_off);
+    std::vector<int> start(n_pairs + 1, 0), idx;
+    for (int q = 0; q < n_pairs; ++q) {
+        for (uint64_t key : shells[q]) idx.push_back((int)(std::lower_bound(all.begin(), all.end(), key) - all.begin()));
+        start[q + 1] = (int)idx.size();
+        shell_out[q] = (int64_t)shells[q].size();
+    }
+    std::vector<uint2> off(n_off);
+    for (int i = 0; i < n_off; ++i) off[i] = make_uint2((unsigned)all[i], (unsigned)(all[i] >> 32));
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t off_b = al(off.size() * sizeof(uint2) + 8), F_b = al((size_t)n_off * 8 + 8),
+                 idx_b = al(idx.size() * sizeof(int) + 4), st_b = al(start.size() * sizeof(int)),
+                 out_b = al((size_t)n_pairs * 8);
+    void *ws;
+    int rc = pt_workspace(c, off_b + F_b + idx_b + st_b + out_b, &ws);
+    if (rc) return rc;
+    char *p = (char *)ws;
+    uint2 *d_off = (uint2 *)p;
+    unsigned long long *d_F = (unsigned long long *)(p + off_b);
+    int *d_idx = (int *)(p + off_b + F_b);
+    int *d_start = (int *)(p + off_b + F_b + idx_b);
+    unsigned long long *d_out = (unsigned long long *)(p + off_b + F_b + idx_b + st_b);
+    if (n_off) PT_CUDA(cudaMemcpyAsync(d_off, off.data(), off.size() * sizeof(uint2), cudaMemcpyHostToDevice, c->stream));
+    if (!idx.empty())
+        PT_CUDA(cudaMemcpyAsync(d_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    PT_CUDA(cudaMemcpyAsync(d_start, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    PT_CUDA(cudaMemsetAsync(d_F, 0, (size_t)n_off * 8 + 8, c->stream));
+    if (n_off) {
+        dim3 grid((unsigned)((g.N + PT_CLR_SITES - 1) / PT_CLR_SITES), (unsigned)((n_off + PT_CLR_OB - 1) / PT_CLR_OB));
+        k_offset_matches<<<grid, 256, 0, c->stream>>>(g, col_dev, d_off, n_off, d_F);
+        ++pt_kernel_launch_count;
+        PT_CUDA(cudaGetLastError());
+    }
+    k_shell_sums<<<n_pairs, 256, 0, c->stream>>>(d_F, d_idx, d_start, d_out);
+    ++pt_kernel_launch_count;
+    PT_CUDA(cudaGetLastError());
+    std::vector<unsigned long long> h(n_pairs);
+    PT_CUDA(cudaMemcpyAsync(h.data(), d_out, (size_t)n_pairs * 8, cudaMemcpyDeviceToHost, c->stream));
+    PT_CUDA(cudaStreamSynchronize(c->stream));
+    for (int q = 0; q < n_pairs; ++q) matches_out[q] = (int64_t)h[q];
     return PT_OK;
 }

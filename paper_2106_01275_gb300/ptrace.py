@@ -80,6 +80,11 @@ _SIGS = {
                              ctypes.POINTER(ctypes.c_int64)], _I),
     "pt_colour_conflicts_noalloc": ([_P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _I, _I, _P,
                                      ctypes.POINTER(ctypes.c_int64)], _I),
+    "pt_tile_dims": ([ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _I, _I, ctypes.POINTER(_I)], _I),
+    "pt_tile_replicate": ([_P, ctypes.POINTER(_I), _P, ctypes.POINTER(_I), _P], _I),
+    "pt_colour_tiled": ([_P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _I, _I, _I, _P, ctypes.POINTER(_I),
+                         ctypes.POINTER(_I)], _I),
+    "pt_clearance": ([_P, ctypes.POINTER(_I), _I, _P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _I, _P, _P], _I),
     "pt_make_probes": ([_P, _P, ctypes.c_int64, _I, _I, ctypes.c_uint64, _I, _I, _I, _P], _I),
     "pt_solve": ([_P, _P, _P, _P, _I, _I, _D, _I, _P, _P, ctypes.POINTER(Stats)], _I),
     "pt_trace_PAinv": ([_P, _P, _P, _I, _I, ctypes.POINTER(_I), _I, _I, ctypes.c_uint64, _I, _I, _I, _I, _D, _I,
@@ -307,6 +312,45 @@ def conflicts_noalloc(dims, mu, p_list, k, col, stream=None):
     _check(lib().pt_colour_conflicts_noalloc(ctypes.c_void_p(handle), _ints(dims), int(mu), _ints(p_list),
                                              len(p_list), int(k), _ptr(col), ctypes.byref(n)))
     return n.value
+
+
+def tile_dims(dims, mu, p_list, k):
+    """Tile of Sec. 3.5 (pt_tile_dims; host only)."""
+    out = (_I * 4)()
+    _check(lib().pt_tile_dims(_ints(dims), int(mu), _ints(p_list), len(p_list), int(k), out))
+    return list(out)
+
+
+def tile_replicate(ctx, tile, tile_col, dims, out=None):
+    """Repeat a tile's colouring over the lattice (pt_tile_replicate)."""
+    import torch
+    N = int(np.prod(dims))
+    col = out if out is not None else torch.empty(N, dtype=torch.int32, device="cuda:%d" % ctx.device)
+    _check(lib().pt_tile_replicate(ctx.handle, _ints(tile), _ptr(tile_col), _ints(dims), _ptr(col)))
+    return col
+
+
+def colour_tiled(ctx, dims, mu, p_list, k, order="natural", out=None):
+    """Colour the Sec. 3.5 tile and repeat it (pt_colour_tiled): (col, m, tile)."""
+    import torch
+    N = int(np.prod(dims))
+    col = out if out is not None else torch.empty(N, dtype=torch.int32, device="cuda:%d" % ctx.device)
+    m = _I()
+    tile = (_I * 4)()
+    _check(lib().pt_colour_tiled(ctx.handle, _ints(dims), int(mu), _ints(p_list), len(p_list), int(k),
+                                 ORDER[order] if isinstance(order, str) else int(order), _ptr(col), ctypes.byref(m),
+                                 tile))
+    return col, m.value, list(tile)
+
+
+def clearance(ctx, dims, mu, col, p_list, k_list):
+    """Table 5 statistic (pt_clearance): (matches, shell_sizes), int64 arrays
+    [len(p_list), len(k_list)]; percentage = 100 matches / (N shell_size)."""
+    m = np.zeros((len(p_list), len(k_list)), dtype=np.int64)
+    s = np.zeros_like(m)
+    _check(lib().pt_clearance(ctx.handle, _ints(dims), int(mu), _ptr(col), _ints(p_list), len(p_list),
+                              _ints(k_list), len(k_list), _np_ptr(m), _np_ptr(s)))
+    return m, s
 
 
 def make_probe(ctx, col, colour_index, noise, seed, set_index, dof, component):

@@ -55,3 +55,17 @@ def test_bad_arguments_are_rejected_without_a_gpu(ptlib):
     buf = ctypes.create_string_buffer(256)
     L.pt_last_error(buf, 256)
     assert b"pt_stencil" in buf.value
+
+
+def test_tile_dims_match_oracle_without_a_gpu(ptlib):
+    """pt_tile_dims is host-only: Table 2's tiles and ragged lattices agree
+    with the oracle's tile policy (Sec. 3.5)."""
+    from oracle.tiles import tile_dims
+    cases = [([32, 32, 32, 64], 2, [p], k) for p in range(9) for k in range(1, 11)]
+    cases += [([24, 24, 24, 48], 2, [8], 2), ([24, 24, 24, 48], 2, [0, 4], 3), ([12, 18, 30, 7], 1, [2], 1),
+              ([64, 64, 64, 64], 0, [8], 8), ([5, 5, 5, 5], 3, [1], 4)]
+    for dims, mu, p_list, k in cases:
+        assert ptlib.tile_dims(dims, mu, p_list, k) == tile_dims(dims, mu, p_list, k), (dims, mu, p_list, k)
+    import ctypes
+    out = (ctypes.c_int * 4)()
+    assert ptlib.lib().pt_tile_dims(ptlib._ints([8, 8, 8, 8]), 4, ptlib._ints([1]), 1, 1, out) == ptlib.PT_ERR_ARG

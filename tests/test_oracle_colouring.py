@@ -159,3 +159,16 @@ def test_redblack_order_is_parity_split():
     n_even = int((L.parity(dims) == 0).sum())
     assert np.all(par[:n_even] == 0) and np.all(par[n_even:] == 1)
     assert sorted(o.tolist()) == list(range(120))
+
+
+def test_first_fit_checker_accepts_greedy_and_flags_changes():
+    """The sampled checker used at full size: silent on the greedy colouring
+    (all sites), and flags a site whose colour is changed."""
+    from oracle.colouring import first_fit_violations
+    dims = [6, 4, 8, 4]
+    for order in (0, 1):
+        col, m = greedy_colour(dims, 2, [2], 2, order)
+        assert first_fit_violations(col, dims, 2, [2], 2, order, range(col.size)) == []
+        bad = col.copy()
+        bad[100] = (bad[100] + 1) % m
+        assert 100 in first_fit_violations(bad, dims, 2, [2], 2, order, range(col.size))
