@@ -4,11 +4,12 @@
 // The greedy walk is sequential by definition (Sec. 4: the visit of each node
 // depends on the colours of the nodes visited before it), so one CTA walks the
 // visit order.  What is parallel is the gather of the neighbourhood's colours
-// (Sec. 4 notes it is read-only): the CTA's threads split the stencil, OR the
-// colours they see into a shared-memory bit mask, and one warp finds the first
-// free colour with ballots.  Colours live in shared memory (16-bit) when the
-// lattice fits, else in global memory.  Two bit masks alternate so that each
-// node needs two barriers.
+// (Sec. 4 notes it is read-only): the CTA's threads split the stencil, stamp
+// the colours they see into a shared-memory table, and search it for the
+// first free colour.  Lattices whose 16-bit colours fit in shared memory keep
+// them there (k_colour_walk); larger ones keep them in an extended array in
+// global memory, read through L1, with two nodes in flight per barrier
+// (k_colour_walk_ext).
 #include <limits.h>
 #include <string.h>
 
@@ -238,6 +239,152 @@ static int prep(pt_ctx *c, const int dims[4], int mu, const int *p_list, int n_p
     return PT_OK;
 }
 
+// Walk with the colours in an extended array: the lattice plus halos wide
+// enough that every neighbour x + o is a plain index offset,
+// colext[b(x) + delta_o], with no wrap arithmetic; a node's colour is written
+// to each of its periodic images in the array (at most two per dimension).
+//
+// One barrier per node, two nodes in flight: between two barriers the CTA
+// commits the colour of node t-1 (found by the previous search), gathers the
+// neighbourhood of node t+1 into one stamp buffer and searches node t's
+// (gathered before the previous barrier) in the other.  A gather cannot see
+// the colours of the two nodes before it (one not yet found, one being
+// written), so the search of node t skips those two colours itself when the
+// nodes are neighbours of t: the L1 distance to the nearer displaced image
+// (Eq. (9)), tested one node ahead by two threads and kept in shared memory.
+// Each thread holds its U offsets' deltas in registers for the whole walk
+// and issues all its loads of a gather before using any of them; both stamp
+// buffers live in shared memory, the colours come through L1.
+#define PT_EXT_NT 1024
+struct ExtGeom {
+    int lo[4];      // smallest offset coordinate per dimension (<= 0)
+    int E[4];       // extended sides
+    int ES[4];      // extended strides
+    int mu, k, n_p;
+    int p[64];      // displacements reduced mod D_mu
+};
+
+// distance to the nearest multiple of D, for |v| < 2D
+__device__ __forceinline__ int dist_mod(int v, int D) {
+    v += (v < 0) ? D : 0;
+    v += (v < 0) ? D : 0;
+    v -= (v >= D) ? D : 0;
+    return min(v, D - v);
+}
+
+// is node a (coordinates) in N(b, p, k) for some p of the list?
+__device__ __forceinline__ bool ext_neighbour(const Geom &g, const ExtGeom &eg, const int a[4], const int b[4]) {
+    int rest = 0, dm = 0, Dm = 1;
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu) {
+        const int dd = a[nu] - b[nu];
+        if (nu == eg.mu) { dm = dd; Dm = g.D[nu]; }
+        else rest += dist_mod(dd, g.D[nu]);
+    }
+    int best = INT_MAX;
+    for (int n = 0; n < eg.n_p; ++n) best = min(best, min(dist_mod(dm - eg.p[n], Dm), dist_mod(dm + eg.p[n], Dm)));
+    return rest + best <= eg.k;
+}
+
+__device__ __forceinline__ int ext_base(const ExtGeom &eg, const int x[4]) {
+    return (x[0] - eg.lo[0]) + eg.ES[1] * (x[1] - eg.lo[1]) + eg.ES[2] * (x[2] - eg.lo[2]) + eg.ES[3] * (x[3] - eg.lo[3]);
+}
+
+// stamp[c] = value for the colour of every neighbour that has one; this
+// thread's n_mine offsets are dlt[0..n_mine)
+template <int U>
+__device__ __forceinline__ void ext_gather(const int (&dlt)[U], int n_mine, const unsigned short *colext, int b,
+                                           int *stamp, int value) {
+    unsigned short cv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) cv[u] = (u < n_mine) ? colext[b + dlt[u]] : (unsigned short)PT_UNCOLOURED;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+        if (cv[u] != PT_UNCOLOURED) stamp[cv[u]] = value;
+}
+
+template <int U>
+__global__ void __launch_bounds__(PT_EXT_NT, 1) k_colour_walk_ext(Geom g, ExtGeom eg, const int *__restrict__ delta,
+                                                                  int n_off, const int *__restrict__ visit,
+                                                                  unsigned short *colext, int32_t *col,
+                                                                  int n_stamp, int *out) {
+    extern __shared__ int sm_ext[];  // two stamp buffers of n_stamp ints
+    __shared__ int s_found[3];       // search results, one slot per node mod 3
+    __shared__ int s_nb[4];          // [parity of node][0: node - 1 is a neighbour, 1: node - 2 is]
+    const int tid = threadIdx.x;
+    for (int c = tid; c < 2 * n_stamp; c += PT_EXT_NT) sm_ext[c] = 0;
+    int dlt[U];                      // this thread's offsets: tid, tid + NT, ...
+#pragma unroll
+    for (int u = 0; u < U; ++u) dlt[u] = (tid + u * PT_EXT_NT < n_off) ? delta[tid + u * PT_EXT_NT] : 0;
+    const int n_mine = (n_off > tid) ? (n_off - tid + PT_EXT_NT - 1) / PT_EXT_NT : 0;
+    if (tid < 3) s_found[tid] = INT_MAX;
+    if (tid < 4) s_nb[tid] = 0;
+    __syncthreads();
+    // node history: x0 = node t, x1 = t - 1, x2 = t - 2, xn = t + 1 (coordinates and index)
+    int x0[4], x1[4], x2[4], xn[4];
+    int i0 = visit[0], i1 = -1, i2 = -1, in_ = -1;
+    site_coords(g, i0, x0);
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu) x1[nu] = x2[nu] = xn[nu] = 0;
+    int f1 = -1, f2 = -1;            // colours of nodes t - 1 and t - 2
+    int m = 0;                       // colours used by nodes before t
+    int i_next = (g.N > 1) ? visit[1] : 0;
+    ext_gather<U>(dlt, n_mine, colext, ext_base(eg, x0), sm_ext, 1);
+    __syncthreads();
+    for (int t = 0; t < g.N; ++t) {
+        // commit node t - 1, whose colour the previous search found
+        if (t >= 1) {
+            const int f = s_found[(t - 1) % 3];
+            if (tid < 16) {
+                int e = 0, ok = 1;
+#pragma unroll
+                for (int nu = 0; nu < 4; ++nu) {
+                    int ev = x1[nu] - eg.lo[nu];                 // in [0, 2D): one reduction
+                    ev -= (ev >= g.D[nu]) ? g.D[nu] : 0;
+                    ev += ((tid >> nu) & 1) * g.D[nu];
+                    ok &= ev < eg.E[nu];
+                    e += ev * eg.ES[nu];
+                }
+                if (ok) colext[e] = (unsigned short)f;
+            }
+            if (tid == 0) col[i1] = f;
+            f2 = f1;
+            f1 = f;
+            if (f + 1 > m) m = f + 1;
+        }
+        if (tid == 0) s_found[(t + 1) % 3] = INT_MAX;      // last read before the previous barrier
+        // gather node t + 1
+        if (t + 1 < g.N) {
+            in_ = i_next;
+            if (t + 2 < g.N) i_next = visit[t + 2];
+            site_coords(g, in_, xn);
+            // for the search of node t + 1: are nodes t and t - 1 its neighbours?
+            if (tid == 32) s_nb[2 * ((t + 1) & 1)] = ext_neighbour(g, eg, x0, xn);
+            if (tid == 64) s_nb[2 * ((t + 1) & 1) + 1] = (i1 >= 0) && ext_neighbour(g, eg, x1, xn);
+            ext_gather<U>(dlt, n_mine, colext, ext_base(eg, xn), sm_ext + ((t + 1) & 1) * n_stamp, t + 2);
+        }
+        // search node t: smallest colour in [0, m] not stamped and not held by a neighbouring t-1 or t-2
+        const int skip1 = s_nb[2 * (t & 1)] ? f1 : -1;
+        const int skip2 = s_nb[2 * (t & 1) + 1] ? f2 : -1;
+        const int *st = sm_ext + (t & 1) * n_stamp;
+        int best = INT_MAX;
+        for (int c = tid; c <= m; c += PT_EXT_NT)
+            if (st[c] != t + 1 && c != skip1 && c != skip2) { best = c; break; }
+        best = __reduce_min_sync(0xffffffffu, best);
+        if ((tid & 31) == 0 && best != INT_MAX) atomicMin(&s_found[t % 3], best);
+        __syncthreads();
+        // shift the history
+        i2 = i1; i1 = i0; i0 = in_;
+#pragma unroll
+        for (int nu = 0; nu < 4; ++nu) { x2[nu] = x1[nu]; x1[nu] = x0[nu]; x0[nu] = xn[nu]; }
+    }
+    if (tid == 0) {
+        const int f = s_found[(g.N - 1) % 3];
+        col[i1] = f;
+        out[0] = (f + 1 > m) ? f + 1 : m;
+    }
+}
+
 // Offsets of the walk: reduced modulo the lattice, merged, x itself dropped,
 // packed (see walk_site).  Sides are below 65536 (PT_CHECK in the caller).
 static std::vector<uint2> walk_offsets(const std::vector<int> &st, const int dims[4]) {
@@ -290,6 +437,74 @@ extern "C" int pt_colour(pt_ctx *c, const int dims[4], int mu, const int *p_list
     const bool sh_col = stamp_b + col_b <= (size_t)max_smem;
     const bool sh_off = stamp_b + off_b + (sh_col ? col_b : 0) <= (size_t)max_smem;
     size_t shared_b = stamp_b + (sh_off ? off_b : 0) + (sh_col ? col_b : 0);
+    // large lattices: the extended-array walk (two stamp buffers in shared memory, deltas in registers)
+    const size_t ext_smem = (size_t)(2 * n_stamp) * sizeof(int);
+    if (!sh_col && ext_smem <= (size_t)max_smem && n_p <= 64 && n_off <= PT_EXT_NT * 24) {
+        ExtGeom eg;
+        eg.mu = mu;
+        eg.k = k;
+        eg.n_p = n_p;
+        for (int n = 0; n < n_p; ++n) eg.p[n] = p_list[n] % dims[mu];
+        // per dimension: signed offsets if the largest minimal image R fits (2R + 1 <= D), else [0, D)
+        int sgn[4];
+        long E = 1;
+        for (int nu = 0; nu < 4; ++nu) {
+            int R = 0, hi = 0;
+            for (const uint2 &o : wo) {
+                const unsigned w = (nu < 2) ? o.x : o.y;
+                const int r = (int)((nu & 1) ? (w >> 16) : (w & 0xffffu));
+                R = std::max(R, std::min(r, dims[nu] - r));
+                hi = std::max(hi, r);
+            }
+            sgn[nu] = 2 * R + 1 <= dims[nu];
+            eg.lo[nu] = sgn[nu] ? -R : 0;
+            eg.E[nu] = dims[nu] + (sgn[nu] ? 2 * R : hi);
+            eg.ES[nu] = (int)E;
+            E *= eg.E[nu];
+        }
+        PT_CHECK_ARG(E < (1L << 31), "pt_colour: extended lattice too large");
+        std::vector<int> delta(n_off);
+        for (int i = 0; i < n_off; ++i) {
+            long dl = 0;
+            for (int nu = 0; nu < 4; ++nu) {
+                const unsigned w = (nu < 2) ? wo[i].x : wo[i].y;
+                const int r = (int)((nu & 1) ? (w >> 16) : (w & 0xffffu));
+                const int o = (sgn[nu] && r > dims[nu] - r) ? r - dims[nu] : r;
+                dl += (long)o * eg.ES[nu];
+            }
+            delta[i] = (int)dl;
+        }
+        unsigned short *d_ext = nullptr;
+        int *d_delta = nullptr;
+        PT_CUDA(cudaMallocAsync((void **)&d_ext, (size_t)E * sizeof(unsigned short), c->stream));
+        PT_CUDA(cudaMallocAsync((void **)&d_delta, (size_t)std::max(n_off, 1) * sizeof(int), c->stream));
+        PT_CUDA(cudaMemsetAsync(d_ext, 0xff, (size_t)E * sizeof(unsigned short), c->stream));
+        if (n_off)
+            PT_CUDA(cudaMemcpyAsync(d_delta, delta.data(), delta.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                    c->stream));
+#define PT_EXT(U)                                                                                                \
+    do {                                                                                                         \
+        PT_CUDA(cudaFuncSetAttribute(k_colour_walk_ext<U>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+                                     (int)ext_smem));                                                            \
+        k_colour_walk_ext<U><<<1, PT_EXT_NT, ext_smem, c->stream>>>(g, eg, d_delta, n_off, cp.d_visit, d_ext,    \
+                                                                    col_dev, n_stamp, cp.d_out);                 \
+    } while (0)
+        if (n_off <= PT_EXT_NT * 4) PT_EXT(4);
+        else if (n_off <= PT_EXT_NT * 8) PT_EXT(8);
+        else if (n_off <= PT_EXT_NT * 12) PT_EXT(12);
+        else if (n_off <= PT_EXT_NT * 16) PT_EXT(16);
+        else if (n_off <= PT_EXT_NT * 20) PT_EXT(20);
+        else PT_EXT(24);
+#undef PT_EXT
+        ++pt_kernel_launch_count;
+        PT_CUDA(cudaGetLastError());
+        PT_CUDA(cudaFreeAsync(d_ext, c->stream));
+        PT_CUDA(cudaFreeAsync(d_delta, c->stream));
+        PT_CUDA(cudaMemcpyAsync(c->h_flags, cp.d_out, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        PT_CUDA(cudaStreamSynchronize(c->stream));
+        *n_colours = c->h_flags[0];
+        return PT_OK;
+    }
 #define PT_WALK(SC, SO)                                                                                          \
     do {                                                                                                         \
         PT_CUDA(cudaFuncSetAttribute(k_colour_walk<SC, SO>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \

@@ -46,6 +46,20 @@ def test_colouring_with_wrapping_offsets(pt, ctx, dims, mu, p, k, order):
     assert np.array_equal(col.cpu().numpy(), want)
 
 
+# lattices whose colours do not fit in shared memory: the extended-array walk
+# (signed halos; sides shorter than the stencil's reach; several displacements)
+EXT_CASES = [([30, 20, 18, 12], 1, [3], 2, 1), ([4, 4, 64, 128], 3, [2], 3, 0), ([24, 24, 24, 12], 2, [1, 4], 1, 1),
+             ([16, 16, 32, 16], 2, [5], 3, 0), ([16, 16, 32, 16], 2, [7], 7, 1)]
+
+
+@pytest.mark.parametrize("dims,mu,p,k,order", EXT_CASES)
+def test_colouring_large_lattices(pt, ctx, dims, mu, p, k, order):
+    want, m_want = greedy_colour(dims, mu, p, k, order)
+    col, m = pt.colour(ctx, dims, mu, p, k, order)
+    assert m == m_want
+    assert np.array_equal(col.cpu().numpy(), want)
+
+
 @pytest.mark.parametrize("dims,mu,p,k,order", [([16, 16, 16, 32], 2, [2], 2, 1), ([24, 24, 24, 48], 2, [4], 2, 0),
                                                ([12, 12, 24, 12], 2, [1, 2], 1, 1)])
 def test_colour_tiled_matches_oracle(pt, ctx, dims, mu, p, k, order):
