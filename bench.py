@@ -275,6 +275,23 @@ def run_ours(args):
            "mean_outer_iters_per_rhs": stats[-1]["outer_iters"] / stats[-1]["n_rhs"],
            "solves_per_s": stats[-1]["n_rhs"] / step_s}
 
+    if W.kind == "lap" and rank == 0:
+        # the hierarchical reading of "k = 1..4 grown at runtime": colourings nested level by level
+        # (pt_colour_nested), reported beside the independent ones the step solves
+        nested = {}
+        for p in sorted({pk[0] for pk in W.pk}):
+            ks = sorted(k for (pp, k) in W.pk if pp == p)
+            if ks != list(range(1, ks[-1] + 1)):
+                continue
+            par, mp_ = pt.colour(ctx, W.dims, W.mu, [p], 1, "natural")
+            counts = [mp_]
+            for k in ks[1:]:
+                par, mp_ = pt.colour_nested(ctx, W.dims, W.mu, [p], k, par, mp_, "natural")
+                counts.append(mp_)
+            nested["p=%d" % p] = counts
+        if nested:
+            out["config"]["nested_colours_natural_k1_up"] = nested
+
     if rank == 0 and world == 1 and not args.skip_baselines:
         # time to sigma: the estimators reach the sigma of their W.n_sets sets in one step
         out["time_to_sigma_s"] = step_s

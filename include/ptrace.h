@@ -119,19 +119,22 @@ PT_API int pt_set_max_slots(pt_ctx *ctx, int n);
  *                by site block, so that they share the links through L2
  *   graph_iters  engine iterations captured in one CUDA graph (host polls
  *                the completion flag once per graph launch)
+ *   rhs_block    right-hand sides per work item of the Wilson applies in
+ *                the mixed-precision inner solve: 1, or 2 (each link load
+ *                then serves two right-hand sides); 0 means 1
  * seconds_per_rhs is an output of pt_autotune (device time per trial RHS). */
 typedef struct pt_tune {
     double delta;
     int32_t group;
     int32_t graph_iters;
-    int32_t pad;
+    int32_t rhs_block;
     double seconds_per_rhs;
 } pt_tune;
 
 /* Autotuner: solves the same trial right-hand sides (up to trial_rhs probes
  * of one noise set spread over the colours of col_dev) with candidate
- * parameters, by coordinate descent over delta (mixed precision), group
- * (Wilson) and graph_iters, keeps the fastest, and stores it in the context
+ * parameters, by coordinate descent over delta (mixed precision), rhs_block
+ * and group (Wilson) and graph_iters, keeps the fastest, and stores it in the context
  * for this operator's (kind, precision, lattice); later solves, traces and
  * gradients with that key use it.  *best (host) receives it.  Synchronises. */
 PT_API int pt_autotune(pt_ctx *ctx, const pt_op *op, const int32_t *col_dev, int n_colours, int mu, int noise,
@@ -198,6 +201,22 @@ PT_API int pt_stencil(int mu, const int *p_list, int n_p, int k, int *offsets_ou
  * (host) receives m.  Synchronises the context stream. */
 PT_API int pt_colour(pt_ctx *ctx, const int dims[4], int mu, const int *p_list, int n_p, int k,
               int order, int32_t *col_dev, int *n_colours);
+
+/* Nested ("hierarchical") colouring: a colouring at distance k grown from a
+ * coarser one (the paper leaves hierarchical probing of displaced colourings
+ * to its Sec. 2.3 discussion; this is the reading used for a colouring grown
+ * from k1 to k > k1).  The greedy walk of pt_colour in which a node only
+ * sees the neighbours of N(x, p, k) that share its parent colour
+ * parent_dev[x]; the colour of x is the pair (parent colour, local first-fit
+ * colour), the pairs numbered 0, 1, ... in the order the walk first meets
+ * them.  Nodes with the same colour share the parent colour, so every parent
+ * class is a union of classes, and no two neighbours share a colour.
+ * parent_dev: int32 [N] (device, read) with values in [0, n_parent)
+ * (PT_ERR_ARG otherwise); col_dev: int32 [N] (device, written); *n_colours
+ * (host).  With a constant parent the result is pt_colour's.  Uses a
+ * temporary stream-ordered allocation; synchronises the context stream. */
+PT_API int pt_colour_nested(pt_ctx *ctx, const int dims[4], int mu, const int *p_list, int n_p, int k, int order,
+                            const int32_t *parent_dev, int n_parent, int32_t *col_dev, int *n_colours);
 
 /* Count ordered pairs (x, y), y in N(x,p,k), y != x, with equal colours: zero
  * for a valid colouring (Sec. 3.1).  *n_conflicts is host.  Synchronises. */
@@ -324,6 +343,26 @@ PT_API int pt_trace_PAinv_multi(pt_ctx *ctx, const pt_op *op, int n_col, const i
                                 const int *n_colours, int mu, const int *p_list, int n_p, int noise,
                                 uint64_t seed, int set0, int n_sets, int dilute, int prec, double tol,
                                 int maxit, double *est_out, pt_stats *stats);
+
+/* Estimates at every level of a nested colouring from the solves of its
+ * finest level only (the hierarchical reading of a colouring grown from k1 up
+ * to k; see pt_colour_nested).  cols_dev[l * N .. (l+1) * N), l = 0 (coarsest)
+ * .. n_lev - 1 (finest), must be nested: nodes with the same level-(l+1)
+ * colour share their level-l colour (PT_ERR_ARG otherwise).  Only the probes
+ * of the finest classes are solved; since the probes of the finer classes
+ * inside a level-l class sum to its probe (Eq. (3), shared noise), the
+ * level-l solution of that class is the sum of theirs, and each finest solve
+ * is contracted with its ancestor's probe at every level:
+ *   est_out[l][s][n] (host complex128 [n_lev][n_sets][n_p])
+ *     = sum_{c_l} sum_a v_{s,c_l,a}^H P_{p_n} A^{-1} v_{s,c_l,a},
+ * the pt_trace_PAinv_multi result for colouring l, at the cost of the finest
+ * level's solves.  n_lev * n_p <= 16.  A temporary stream-ordered
+ * allocation holds the ancestor table.  Other arguments as pt_trace_PAinv.
+ * Synchronises. */
+PT_API int pt_trace_PAinv_nested(pt_ctx *ctx, const pt_op *op, int n_lev, const int32_t *cols_dev,
+                                 const int *n_colours, int mu, const int *p_list, int n_p, int noise,
+                                 uint64_t seed, int set0, int n_sets, int dilute, int prec, double tol,
+                                 int maxit, double *est_out, pt_stats *stats);
 
 /* Adjoint gradient of the probed estimate T = sum_s est[s] for one
  * displacement p (not in the paper): with x = A^{-1} v, y = A^{-+} P^T v,

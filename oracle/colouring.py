@@ -55,6 +55,45 @@ def greedy_colour(dims, mu, p_list, k, order=0, visit=None):
     return col, int(m)
 
 
+def nested_colour(dims, mu, p_list, k, parent, order=0):
+    """Nested colouring at distance k under a coarser colouring `parent` (the
+    hierarchical mode: a colouring grown from k1 to k > k1).  Greedy walk of
+    Algorithm 1 in which a node only sees the neighbours of N(x, p, k) that
+    share its parent colour; the colour of x is the pair (parent(x), local
+    first-fit colour), the pairs numbered 0, 1, ... in the order the walk
+    first meets them.  Nodes with the same colour then share the parent
+    colour, and two neighbours never share a colour (different parents, or
+    the same parent and different local colours).  Returns (col, n_colours)."""
+    d = len(dims)
+    st = displaced_stencil(d, mu, p_list, k).astype(np.int32)
+    visit = np.ascontiguousarray(visit_order(dims, mu, order), dtype=np.int64)
+    N = volume(dims)
+    parent = np.ascontiguousarray(parent, dtype=np.int32)
+    assert parent.shape == (N,)
+    local = np.empty(N, dtype=np.int32)
+    lib = _load()
+    fn = lib.oracle_greedy_colour_nested
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    st_c = np.ascontiguousarray(st.reshape(-1))
+    m_local = fn(d, (ctypes.c_int * d)(*[int(D) for D in dims]), int(st.shape[0]),
+                 st_c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                 visit.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                 parent.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                 local.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if m_local < 0:
+        raise MemoryError("oracle colouring failed")
+    ids = {}
+    col = np.empty(N, dtype=np.int32)
+    for x in visit:
+        key = (int(parent[x]), int(local[x]))
+        if key not in ids:
+            ids[key] = len(ids)
+        col[x] = ids[key]
+    return col, len(ids)
+
+
 def conflicts(col, dims, mu, p_list, k):
     """Number of ordered pairs (x, y), y in N(x,p,k), y != x, sharing a colour.
     A valid distance-k colouring of the displaced graph has none."""

@@ -59,3 +59,45 @@ int oracle_greedy_colour(int d, const int *dims, int n_off, const int *offsets,
     free(used);
     return n_colours;
 }
+
+/*
+ * Nested variant (the hierarchical reading of a colouring grown from k1 to
+ * k2 > k1): the same walk, but a node only sees the neighbours that share its
+ * parent colour parent[] (the k1 colouring).  The colours returned are local
+ * to each parent class; the caller pairs them with the parent colour.
+ */
+int oracle_greedy_colour_nested(int d, const int *dims, int n_off, const int *offsets, const int64_t *visit,
+                                const int32_t *parent, int32_t *col)
+{
+    int64_t N = 1;
+    for (int mu = 0; mu < d; ++mu) N *= dims[mu];
+    for (int64_t i = 0; i < N; ++i) col[i] = -1;
+    int64_t *used = (int64_t *)calloc((size_t)n_off + 2, sizeof(int64_t));
+    if (!used) return -1;
+    int n_colours = 0;
+    int x[8];
+    for (int64_t t = 0; t < N; ++t) {
+        int64_t site = visit[t];
+        int64_t stamp = t + 1;
+        int64_t rem = site;
+        for (int mu = 0; mu < d; ++mu) { x[mu] = (int)(rem % dims[mu]); rem /= dims[mu]; }
+        for (int o = 0; o < n_off; ++o) {
+            int64_t idx = 0, stride = 1;
+            for (int mu = 0; mu < d; ++mu) {
+                int c = (x[mu] + offsets[o * d + mu]) % dims[mu];
+                if (c < 0) c += dims[mu];
+                idx += (int64_t)c * stride;
+                stride *= dims[mu];
+            }
+            if (idx == site || parent[idx] != parent[site]) continue;
+            int32_t cy = col[idx];
+            if (cy >= 0 && cy <= n_off) used[cy] = stamp;
+        }
+        int c = 0;
+        while (used[c] == stamp) ++c;
+        col[site] = c;
+        if (c + 1 > n_colours) n_colours = c + 1;
+    }
+    free(used);
+    return n_colours;
+}

@@ -102,11 +102,13 @@ __device__ __forceinline__ int walk_site(const Geom &g, const int x[4], uint2 o)
 // visible to the other threads, so every thread keeps (node, colour) of the
 // previous step and uses it in the next gather.  Shared memory: the stamps
 // (n_stamp ints), then (SHARED_OFF) the packed offsets, then (SHARED_COL) the
-// 16-bit colours of all N nodes.
-template <bool SHARED_COL, bool SHARED_OFF>
+// 16-bit colours of all N nodes.  NESTED: a node only sees the neighbours
+// with its own parent colour (parent[], the coarser colouring), and the
+// colours found are local to each parent class.
+template <bool SHARED_COL, bool SHARED_OFF, bool NESTED>
 __global__ void __launch_bounds__(1024, 1) k_colour_walk(Geom g, const uint2 *__restrict__ off_g, int n_off,
                                                       const int *__restrict__ visit, int32_t *col, int n_stamp,
-                                                      int *out) {
+                                                      int *out, const int32_t *__restrict__ parent) {
     extern __shared__ int smem_i[];
     int *stamp = smem_i;
     uint2 *soff = reinterpret_cast<uint2 *>(smem_i + ((n_stamp + 1) & ~1));
@@ -132,6 +134,7 @@ __global__ void __launch_bounds__(1024, 1) k_colour_walk(Geom g, const uint2 *__
         if (t + 1 < g.N) xs_next = visit[t + 1];          // in flight during this node's gather
         int x[4];
         site_coords(g, xs, x);
+        const int px = NESTED ? parent[xs] : 0;
         for (int base = tid; base < n_off; base += nt * PT_WALK_U) {
             int cv[PT_WALK_U];
 #pragma unroll
@@ -143,6 +146,7 @@ __global__ void __launch_bounds__(1024, 1) k_colour_walk(Geom g, const uint2 *__
                     int c = SHARED_COL ? (int)scol[y] : col[y];
                     if (SHARED_COL && c == (int)PT_UNCOLOURED) c = -1;
                     cv[u] = (y == prev_x) ? prev_c : c;
+                    if (NESTED && parent[y] != px) cv[u] = -1;
                 }
             }
 #pragma unroll
@@ -408,13 +412,15 @@ static std::vector<uint2> walk_offsets(const std::vector<int> &st, const int dim
     return out;
 }
 
-extern "C" int pt_colour(pt_ctx *c, const int dims[4], int mu, const int *p_list, int n_p, int k, int order,
-                         int32_t *col_dev, int *n_colours) {
+// The greedy walk of pt_colour (parent == NULL) and of pt_colour_nested (the
+// local colours of each parent class).  *m receives the colour count; the
+// visit order stays in the work space (ColourPrep) for the caller.
+static int colour_walk(pt_ctx *c, const int dims[4], int mu, const int *p_list, int n_p, int k, int order,
+                       const int32_t *parent, int32_t *col_dev, int *n_colours, ColourPrep &cp) {
     PT_CHECK_ARG(c && col_dev && n_colours, "pt_colour: NULL argument");
     PT_CHECK_ARG(dims && dims[0] < 65536 && dims[1] < 65536 && dims[2] < 65536 && dims[3] < 65536,
                  "pt_colour: lattice sides must be below 65536");
     PT_CUDA(cudaSetDevice(c->device));
-    ColourPrep cp;
     int rc = prep(c, dims, mu, p_list, n_p, k, order, true, cp);
     if (rc) return rc;
     Geom g = make_geom(dims);
@@ -439,7 +445,7 @@ extern "C" int pt_colour(pt_ctx *c, const int dims[4], int mu, const int *p_list
     size_t shared_b = stamp_b + (sh_off ? off_b : 0) + (sh_col ? col_b : 0);
     // large lattices: the extended-array walk (two stamp buffers in shared memory, deltas in registers)
     const size_t ext_smem = (size_t)(2 * n_stamp) * sizeof(int);
-    if (!sh_col && ext_smem <= (size_t)max_smem && n_p <= 64 && n_off <= PT_EXT_NT * 24) {
+    if (!parent && !sh_col && ext_smem <= (size_t)max_smem && n_p <= 64 && n_off <= PT_EXT_NT * 24) {
         ExtGeom eg;
         eg.mu = mu;
         eg.k = k;
@@ -505,21 +511,117 @@ extern "C" int pt_colour(pt_ctx *c, const int dims[4], int mu, const int *p_list
         *n_colours = c->h_flags[0];
         return PT_OK;
     }
-#define PT_WALK(SC, SO)                                                                                          \
+#define PT_WALK(SC, SO, NE)                                                                                      \
     do {                                                                                                         \
-        PT_CUDA(cudaFuncSetAttribute(k_colour_walk<SC, SO>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+        PT_CUDA(cudaFuncSetAttribute(k_colour_walk<SC, SO, NE>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                      (int)shared_b));                                                            \
-        k_colour_walk<SC, SO><<<1, 1024, shared_b, c->stream>>>(g, d_off, n_off, cp.d_visit, col_dev, n_stamp,   \
-                                                                cp.d_out);                                       \
+        k_colour_walk<SC, SO, NE><<<1, 1024, shared_b, c->stream>>>(g, d_off, n_off, cp.d_visit, col_dev,        \
+                                                                    n_stamp, cp.d_out, parent);                  \
     } while (0)
-    if (sh_col && sh_off) PT_WALK(true, true);
-    else if (sh_col) PT_WALK(true, false);
-    else if (sh_off) PT_WALK(false, true);
-    else PT_WALK(false, false);
+    if (parent) {
+        if (sh_col && sh_off) PT_WALK(true, true, true);
+        else if (sh_col) PT_WALK(true, false, true);
+        else if (sh_off) PT_WALK(false, true, true);
+        else PT_WALK(false, false, true);
+    } else {
+        if (sh_col && sh_off) PT_WALK(true, true, false);
+        else if (sh_col) PT_WALK(true, false, false);
+        else if (sh_off) PT_WALK(false, true, false);
+        else PT_WALK(false, false, false);
+    }
 #undef PT_WALK
     ++pt_kernel_launch_count;
     PT_CUDA(cudaGetLastError());
     PT_CUDA(cudaMemcpyAsync(c->h_flags, cp.d_out, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PT_CUDA(cudaStreamSynchronize(c->stream));
+    *n_colours = c->h_flags[0];
+    return PT_OK;
+}
+
+extern "C" int pt_colour(pt_ctx *c, const int dims[4], int mu, const int *p_list, int n_p, int k, int order,
+                         int32_t *col_dev, int *n_colours) {
+    ColourPrep cp;
+    return colour_walk(c, dims, mu, p_list, n_p, k, order, nullptr, col_dev, n_colours, cp);
+}
+
+// ------------------------------------------------------------ nested colouring
+// The colour of a node is the pair (parent colour, local colour); pairs are
+// numbered in the order the walk first meets them: each pair's first visit
+// rank (atomicMin over its nodes), then its position among the pairs sorted
+// by that rank, then the number written to every node.
+
+#define PT_PAIR_UNSET 0x7f7f7f7f      // bytes 0x7f: larger than any visit rank
+
+__global__ void k_visit_rank(int N, const int *__restrict__ visit, int *rank) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N; t += gridDim.x * blockDim.x) rank[visit[t]] = t;
+}
+
+__global__ void k_pair_first(int N, const int32_t *__restrict__ parent, int n_parent, const int32_t *__restrict__ local,
+                             int m_local, const int *__restrict__ rank, int *first, int *bad) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
+        const int pa = parent[x], lo = local[x];
+        if (pa < 0 || pa >= n_parent || lo < 0 || lo >= m_local) { atomicOr(bad, 1); continue; }
+        atomicMin(&first[(size_t)pa * m_local + lo], rank[x]);
+    }
+}
+
+// id of a used pair = number of used pairs met earlier; *n_used counts them
+__global__ void k_pair_ids(int K, const int *__restrict__ first, int *id, int *n_used) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < K; q += gridDim.x * blockDim.x) {
+        const int f = first[q];
+        if (f == PT_PAIR_UNSET) { id[q] = -1; continue; }
+        int n = 0;
+        for (int r = 0; r < K; ++r) n += first[r] < f;
+        id[q] = n;
+        atomicAdd(n_used, 1);
+    }
+}
+
+__global__ void k_pair_assign(int N, const int32_t *__restrict__ parent, int m_local, const int *__restrict__ id,
+                              int32_t *col) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x)
+        col[x] = id[(size_t)parent[x] * m_local + col[x]];
+}
+
+extern "C" int pt_colour_nested(pt_ctx *c, const int dims[4], int mu, const int *p_list, int n_p, int k, int order,
+                                const int32_t *parent_dev, int n_parent, int32_t *col_dev, int *n_colours) {
+    PT_CHECK_ARG(c && parent_dev && col_dev && n_colours, "pt_colour_nested: NULL argument");
+    PT_CHECK_ARG(n_parent >= 1, "pt_colour_nested: n_parent must be at least 1");
+    ColourPrep cp;
+    int m_local = 0;
+    int rc = colour_walk(c, dims, mu, p_list, n_p, k, order, parent_dev, col_dev, &m_local, cp);
+    if (rc) return rc;
+    Geom g = make_geom(dims);
+    const long K = (long)n_parent * m_local;
+    PT_CHECK_ARG(g.N < PT_PAIR_UNSET, "pt_colour_nested: lattice too large");
+    PT_CHECK_ARG(K <= (1L << 24), "pt_colour_nested: %ld (parent, local) pairs exceed the table", K);
+    // work space after the visit order: rank [N], first [K], id [K], two flags
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t rank_b = al((size_t)g.N * sizeof(int)), k_b = al((size_t)K * sizeof(int));
+    int32_t *tmp = nullptr;
+    PT_CUDA(cudaMallocAsync((void **)&tmp, rank_b + 2 * k_b + 256, c->stream));
+    int *rank = (int *)tmp, *first = (int *)((char *)tmp + rank_b), *id = (int *)((char *)tmp + rank_b + k_b);
+    int *flags = (int *)((char *)tmp + rank_b + 2 * k_b);
+    PT_CUDA(cudaMemsetAsync(first, 0x7f, (size_t)K * sizeof(int), c->stream));   // PT_PAIR_UNSET
+    PT_CUDA(cudaMemsetAsync(flags, 0, 2 * sizeof(int), c->stream));
+    const int blocks = (int)std::min<long>(((long)g.N + 255) / 256, 16L * c->num_sms);
+    const int kblocks = (int)std::min<long>((K + 255) / 256, 16L * c->num_sms);
+    k_visit_rank<<<blocks, 256, 0, c->stream>>>(g.N, cp.d_visit, rank);
+    k_pair_first<<<blocks, 256, 0, c->stream>>>(g.N, parent_dev, n_parent, col_dev, m_local, rank, first, flags);
+    pt_kernel_launch_count += 2;
+    PT_CUDA(cudaGetLastError());
+    PT_CUDA(cudaMemcpyAsync(c->h_flags, flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PT_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->h_flags[0]) {
+        cudaFreeAsync(tmp, c->stream);
+        PT_CHECK_ARG(false, "pt_colour_nested: parent colours must lie in [0, n_parent)");
+    }
+    k_pair_ids<<<kblocks, 256, 0, c->stream>>>((int)K, first, id, flags + 1);
+    k_pair_assign<<<blocks, 256, 0, c->stream>>>(g.N, parent_dev, m_local, id, col_dev);
+    pt_kernel_launch_count += 2;
+    PT_CUDA(cudaGetLastError());
+    PT_CUDA(cudaMemcpyAsync(c->h_flags, flags + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PT_CUDA(cudaFreeAsync(tmp, c->stream));
     PT_CUDA(cudaStreamSynchronize(c->stream));
     *n_colours = c->h_flags[0];
     return PT_OK;

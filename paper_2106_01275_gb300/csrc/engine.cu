@@ -55,6 +55,13 @@ struct TaskStat {
 struct EP {
     Geom g;
     int kind, nsb, R, gs, vec4;
+    int rhs_block;             // Wilson applies: right-hand sides per item (1 or 2)
+    // nested trace mode (n_lev > 0): the tasks are the classes of the finest of
+    // n_lev nested colourings lev_cols [n_lev][N]; output q = l * n_pr + n is the
+    // contraction with the level-l probe (ancestor class lev_anc[l][colour])
+    int n_lev, n_pr, m_fin;
+    const int32_t *lev_cols;
+    const int *lev_anc;
     int64_t L;                 // reals per slot field
     double diag, kappa;
     int antip;
@@ -403,7 +410,11 @@ __global__ void __launch_bounds__(PT_BLOCK) k_contract(EP P) {
         const uint64_t key = pt_set_key(P.seed, tk.set);
         const int32_t *col = P.col + (size_t)tk.cidx * N;
         SITE_LOOP(KIND)
-            if (col[idx] != tk.colour) continue;
+            if (P.n_lev) {                 // the coarsest ancestor class holds every finer one
+                if (P.lev_cols[idx] != P.lev_anc[tk.colour]) continue;
+            } else if (col[idx] != tk.colour) {
+                continue;
+            }
             int xc[4];
             site_coords(P.g, idx, xc);
             const int dof = KIND ? 12 : 1;
@@ -414,6 +425,11 @@ __global__ void __launch_bounds__(PT_BLOCK) k_contract(EP P) {
 #pragma unroll
                 for (int n = 0; n < PT_MAX_P; ++n) {
                     if (n >= P.n_p) break;
+                    if (P.n_lev) {
+                        const int l = n / P.n_pr;
+                        if (l > 0 && P.lev_cols[(size_t)l * N + idx] != P.lev_anc[(size_t)l * P.m_fin + tk.colour])
+                            continue;
+                    }
                     int y = shift_site(P.g, idx, xc, P.mu, P.p[n]);
                     Cx<double> q = cconjmul(z, Fld<KIND, double>::ld(x, N, a, y));
                     acc[2 * n] += q.re;
@@ -799,9 +815,12 @@ __global__ void __launch_bounds__(PT_BLOCK) k_cg_update_v4(EP P) {
 }
 
 // ------------------------------------------------------------------ BiCGStab (Wilson)
+#ifndef PT_WIL_MINB
+#define PT_WIL_MINB 3    // resident CTAs per SM the FP32/BF16 Wilson applies are compiled for
+#endif
 // v = A p;  partial (r0, v)
 template <typename S, typename LS>
-__global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 : 3) k_bicg_apply1(EP P) {
+__global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 : PT_WIL_MINB) k_bicg_apply1(EP P) {
     typedef Fld<1, S> F;
     typedef typename F::R R;
     __shared__ double sh[32 * 2];
@@ -880,7 +899,7 @@ __global__ void __launch_bounds__(PT_BLOCK) k_bicg_s(EP P) {
 
 // t = A s;  partials (t, s), |t|^2
 template <typename S, typename LS>
-__global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 : 3) k_bicg_apply2(EP P) {
+__global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 : PT_WIL_MINB) k_bicg_apply2(EP P) {
     typedef Fld<1, S> F;
     typedef typename F::R R;
     __shared__ double sh[32 * 3];
@@ -894,12 +913,15 @@ __global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 :
         SITE_LOOP(1)
             int xc[4];
             site_coords(P.g, idx, xc);
-            Cx<R> av[12];
-            apply_site<1, R, S, LS>(P, s, (const LS *)P.U, idx, xc, av);
-            Cx<R> sp[4][3];
-            load_spinor<S, R>(s, N, idx, sp);
+            Cx<R> acc[4][3], sp[4][3], av[12];
+            wilson_hop_site<R, S, LS>(P.g, s, (const LS *)P.U, P.antip, idx, xc, acc);
+            load_spinor<S, R>(s, N, idx, sp);                  // the own spinor, loaded once
+            const R kap = (R)P.kappa;
 #pragma unroll
-            for (int c = 0; c < 12; ++c) av[c] = Cx<R>{rnd<S, R>(av[c].re), rnd<S, R>(av[c].im)};
+            for (int c = 0; c < 12; ++c) {
+                const Cx<R> w = csub(sp[c / 3][c % 3], cscale(acc[c / 3][c % 3], kap));
+                av[c] = Cx<R>{rnd<S, R>(w.re), rnd<S, R>(w.im)};
+            }
             store_spinor<S, R>(t, N, idx, av);
 #pragma unroll
             for (int c = 0; c < 12; ++c) {
@@ -912,6 +934,114 @@ __global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 :
         SITE_LOOP_END
         item_store_r<3>(P, j, b, vr, sh);
     ITEM_LOOP_END
+}
+
+// Two right-hand sides per item (rhs_block = 2): the items pair consecutive
+// entries of the work list, site block by site block within slot groups of
+// max(1, gs / 2) pairs; every link is loaded once per site for both.  A pair
+// whose second slot is missing or not iterating computes the first twice and
+// keeps one result.
+#define ITEM2_LOOP(LIST)                                                        \
+    const int cnt = P.counts[LIST];                                             \
+    const int *lst = P.lists + (size_t)(LIST) * P.R;                            \
+    const int npairs_ = (cnt + 1) / 2;                                          \
+    const int gp_ = max(1, P.gs / 2);                                           \
+    const int64_t n_items = (int64_t)npairs_ * P.nsb;                           \
+    const int64_t gitems_ = (int64_t)gp_ * P.nsb;                               \
+    for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {              \
+        const int64_t g_ = it / gitems_;                                        \
+        const int base_ = (int)(g_ * gp_);                                      \
+        const int gsz_ = min(gp_, npairs_ - base_);                             \
+        const int rem_ = (int)(it - g_ * gitems_);                              \
+        const int b = rem_ / gsz_;                                              \
+        const int q_ = base_ + rem_ % gsz_;                                     \
+        const int ja = lst[2 * q_];                                             \
+        const int jb = (2 * q_ + 1 < cnt) ? lst[2 * q_ + 1] : -1;
+#define ITEM2_LOOP_END }
+
+// v = A p for two slots;  partials (r0, v) of each
+template <typename S, typename LS>
+__global__ void __launch_bounds__(PT_BLOCK, 2) k_bicg_apply1_x2(EP P) {
+    typedef Fld<1, S> F;
+    typedef typename F::R R;
+    __shared__ double sh[32 * 2];
+    const int N = P.g.N;
+    ITEM2_LOOP(LIST_INNER)
+        const bool act_a = P.slots[ja].phase == PH_INNER;
+        const bool act_b = jb >= 0 && P.slots[jb].phase == PH_INNER;
+        if (!act_a && !act_b) continue;
+        const int j0 = act_a ? ja : jb, j1 = (act_a && act_b) ? jb : j0;
+        const S *const pv[2] = {slot_cptr<S>(P.pv, j0, P.L), slot_cptr<S>(P.pv, j1, P.L)};
+        S *const q[2] = {slot_ptr<S>(P.q, j0, P.L), slot_ptr<S>(P.q, j1, P.L)};
+        const S *const r0[2] = {slot_cptr<S>(P.r0, j0, P.L), slot_cptr<S>(P.r0, j1, P.L)};
+        R vr[2][2] = {{R(0), R(0)}, {R(0), R(0)}};
+        SITE_LOOP(1)
+            int xc[4];
+            site_coords(P.g, idx, xc);
+            Cx<R> acc[2][4][3];
+            wilson_hop_multi<R, S, LS, 2>(P.g, pv, (const LS *)P.U, P.antip, idx, xc, acc);
+            const R kap = (R)P.kappa;
+#pragma unroll
+            for (int n = 0; n < 2; ++n) {
+                Cx<R> ps[4][3], z[4][3], av[12];
+                load_spinor<S, R>(pv[n], N, idx, ps);
+                load_spinor<S, R>(r0[n], N, idx, z);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) {
+                    const Cx<R> w = csub(ps[c / 3][c % 3], cscale(acc[n][c / 3][c % 3], kap));
+                    av[c] = Cx<R>{rnd<S, R>(w.re), rnd<S, R>(w.im)};
+                    const Cx<R> zc = z[c / 3][c % 3];
+                    vr[n][0] += zc.re * av[c].re + zc.im * av[c].im;
+                    vr[n][1] += zc.re * av[c].im - zc.im * av[c].re;
+                }
+                if (n == 0 || j1 != j0) store_spinor<S, R>(q[n], N, idx, av);
+            }
+        SITE_LOOP_END
+        item_store_r<2>(P, j0, b, vr[0], sh);
+        if (j1 != j0) item_store_r<2>(P, j1, b, vr[1], sh);
+    ITEM2_LOOP_END
+}
+
+// t = A s for two slots;  partials (t, s), |t|^2 of each
+template <typename S, typename LS>
+__global__ void __launch_bounds__(PT_BLOCK, 2) k_bicg_apply2_x2(EP P) {
+    typedef Fld<1, S> F;
+    typedef typename F::R R;
+    __shared__ double sh[32 * 3];
+    const int N = P.g.N;
+    ITEM2_LOOP(LIST_INNER)
+        const bool act_a = P.slots[ja].phase == PH_INNER;
+        const bool act_b = jb >= 0 && P.slots[jb].phase == PH_INNER;
+        if (!act_a && !act_b) continue;
+        const int j0 = act_a ? ja : jb, j1 = (act_a && act_b) ? jb : j0;
+        const S *const sv_[2] = {slot_cptr<S>(P.s, j0, P.L), slot_cptr<S>(P.s, j1, P.L)};
+        S *const t[2] = {slot_ptr<S>(P.t, j0, P.L), slot_ptr<S>(P.t, j1, P.L)};
+        R vr[2][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
+        SITE_LOOP(1)
+            int xc[4];
+            site_coords(P.g, idx, xc);
+            Cx<R> acc[2][4][3];
+            wilson_hop_multi<R, S, LS, 2>(P.g, sv_, (const LS *)P.U, P.antip, idx, xc, acc);
+            const R kap = (R)P.kappa;
+#pragma unroll
+            for (int n = 0; n < 2; ++n) {
+                Cx<R> sp[4][3], av[12];
+                load_spinor<S, R>(sv_[n], N, idx, sp);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) {
+                    const Cx<R> w = csub(sp[c / 3][c % 3], cscale(acc[n][c / 3][c % 3], kap));
+                    av[c] = Cx<R>{rnd<S, R>(w.re), rnd<S, R>(w.im)};
+                    const Cx<R> tv = av[c], sc = sp[c / 3][c % 3];
+                    vr[n][0] += tv.re * sc.re + tv.im * sc.im;
+                    vr[n][1] += tv.re * sc.im - tv.im * sc.re;
+                    vr[n][2] += tv.re * tv.re + tv.im * tv.im;
+                }
+                if (n == 0 || j1 != j0) store_spinor<S, R>(t[n], N, idx, av);
+            }
+        SITE_LOOP_END
+        item_store_r<3>(P, j0, b, vr[0], sh);
+        if (j1 != j0) item_store_r<3>(P, j1, b, vr[1], sh);
+    ITEM2_LOOP_END
 }
 
 __global__ void k_fin_bicg_omega(EP P) {
@@ -1035,6 +1165,7 @@ struct EngineRun {
     int kernels_per_iter;
     // persistent grid of each item kernel: SMs x its own resident CTAs per SM
     int g_contract, g_oupd, g_ores, g_apply1, g_apply2, g_upd, g_s, g_dir;
+    int g_apply1_x2, g_apply2_x2;
 };
 
 template <typename K>
@@ -1079,12 +1210,22 @@ static void enqueue_iteration(const EngineRun &E, cudaStream_t st, const cudaEve
         ev_rec(ev, 2, st);
     } else {
         ev_rec(ev, 0, st);
-        k_bicg_apply1<S, LS><<<E.g_apply1, PT_BLOCK, 0, st>>>(P);
+        if constexpr (!std::is_same<S, double>::value) {
+            if (P.rhs_block == 2) k_bicg_apply1_x2<S, LS><<<E.g_apply1_x2, PT_BLOCK, 0, st>>>(P);
+            else k_bicg_apply1<S, LS><<<E.g_apply1, PT_BLOCK, 0, st>>>(P);
+        } else {
+            k_bicg_apply1<S, LS><<<E.g_apply1, PT_BLOCK, 0, st>>>(P);
+        }
         ev_rec(ev, 1, st);
         k_fin_bicg_alpha<<<W, 256, 0, st>>>(P);
         k_bicg_s<S><<<E.g_s, PT_BLOCK, 0, st>>>(P);
         ev_rec(ev, 2, st);
-        k_bicg_apply2<S, LS><<<E.g_apply2, PT_BLOCK, 0, st>>>(P);
+        if constexpr (!std::is_same<S, double>::value) {
+            if (P.rhs_block == 2) k_bicg_apply2_x2<S, LS><<<E.g_apply2_x2, PT_BLOCK, 0, st>>>(P);
+            else k_bicg_apply2<S, LS><<<E.g_apply2, PT_BLOCK, 0, st>>>(P);
+        } else {
+            k_bicg_apply2<S, LS><<<E.g_apply2, PT_BLOCK, 0, st>>>(P);
+        }
         ev_rec(ev, 3, st);
         k_fin_bicg_omega<<<W, 256, 0, st>>>(P);
         k_bicg_update<S><<<E.g_upd, PT_BLOCK, 0, st>>>(P);
@@ -1115,6 +1256,9 @@ struct EngineRequest {
     int maxit;
     int prec;
     int R_force;               // >0: exact slot count (grad mode)
+    int n_lev = 0, n_pr = 0, m_fin = 0;   // nested trace mode (see EP)
+    const int32_t *lev_cols = nullptr;
+    const int *lev_anc = nullptr;
     // outputs
     std::vector<double> task_out;   // trace: [n_tasks][n_p] complex
     std::vector<TaskStat> tstat;
@@ -1140,6 +1284,7 @@ static pt_ctx::Tune engine_tuning(const pt_ctx *c, const pt_op *op, int prec) {
     d.delta = prec == PT_PREC_FP64 ? 0.0 : (prec == PT_PREC_MIXED_FP32 ? 1e-5 : 1e-2);
     d.group = op->kind ? 8 : 1;
     d.graph_iters = 8;
+    d.rhs_block = 1;
     return d;
 }
 
@@ -1185,6 +1330,7 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     P.R = R;
     const pt_ctx::Tune tn = engine_tuning(c, op, rq.prec);
     P.gs = tn.group;
+    P.rhs_block = (KIND == 1 && !std::is_same<S, double>::value && tn.rhs_block == 2) ? 2 : 1;
     P.vec4 = (KIND == 0 && g.D[0] % 4 == 0) ? 1 : 0;
     P.L = L;
     P.diag = 8.0 + op->m2;
@@ -1201,6 +1347,11 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     P.noise = rq.noise;
     P.mu = rq.mu;
     P.n_p = rq.n_p;
+    P.n_lev = rq.n_lev;
+    P.n_pr = rq.n_pr;
+    P.m_fin = rq.m_fin;
+    P.lev_cols = rq.lev_cols;
+    P.lev_anc = rq.lev_anc;
     P.dilute = rq.dilute;
     P.pshift = rq.pshift;
     for (int n = 0; n < rq.n_p && n < PT_MAX_P; ++n) P.p[n] = rq.p_list[n];
@@ -1258,6 +1409,12 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     } else {
         E.g_apply1 = persistent_grid(k_bicg_apply1<S, LS>, ns);
         E.g_apply2 = persistent_grid(k_bicg_apply2<S, LS>, ns);
+        if constexpr (!std::is_same<S, double>::value) {
+            E.g_apply1_x2 = persistent_grid(k_bicg_apply1_x2<S, LS>, ns);
+            E.g_apply2_x2 = persistent_grid(k_bicg_apply2_x2<S, LS>, ns);
+        } else {
+            E.g_apply1_x2 = E.g_apply2_x2 = 0;
+        }
         E.g_upd = persistent_grid(k_bicg_update<S>, ns);
         E.g_s = persistent_grid(k_bicg_s<S>, ns);
         E.g_dir = persistent_grid(k_bicg_dir<S>, ns);
@@ -1510,6 +1667,103 @@ extern "C" int pt_trace_PAinv(pt_ctx *c, const pt_op *op, const int32_t *col_dev
     return rc;
 }
 
+// ------------------------------------------------------------------ nested trace
+// Ancestor table anc[l][c] = level-l colour of the nodes of finest class c, and
+// a flag when some node's level-l colour differs from it (not nested) or a
+// finest colour is out of range.
+__global__ void k_nest_anc(int N, int n_lev, int m_fin, const int32_t *__restrict__ cols, int *anc, int *bad) {
+    const int32_t *fin = cols + (size_t)(n_lev - 1) * N;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
+        const int c = fin[x];
+        if (c < 0 || c >= m_fin) { atomicOr(bad, 1); continue; }
+        for (int l = 0; l < n_lev; ++l) anc[(size_t)l * m_fin + c] = cols[(size_t)l * N + x];
+    }
+}
+
+__global__ void k_nest_check(int N, int n_lev, int m_fin, const int32_t *__restrict__ cols,
+                             const int *__restrict__ anc, int *bad) {
+    const int32_t *fin = cols + (size_t)(n_lev - 1) * N;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N; x += gridDim.x * blockDim.x) {
+        const int c = fin[x];
+        if (c < 0 || c >= m_fin) continue;
+        for (int l = 0; l < n_lev; ++l)
+            if (cols[(size_t)l * N + x] != anc[(size_t)l * m_fin + c]) atomicOr(bad, 2);
+    }
+}
+
+extern "C" int pt_trace_PAinv_nested(pt_ctx *c, const pt_op *op, int n_lev, const int32_t *cols_dev,
+                                     const int *n_colours, int mu, const int *p_list, int n_p, int noise,
+                                     uint64_t seed, int set0, int n_sets, int dilute, int prec, double tol, int maxit,
+                                     double *est_out, pt_stats *stats) {
+    PT_CHECK_ARG(c && op && op->ctx == c, "pt_trace_PAinv_nested: bad context/operator");
+    PT_CHECK_ARG(cols_dev && est_out && n_colours && p_list && n_lev >= 1, "pt_trace_PAinv_nested: NULL argument");
+    PT_CHECK_ARG(n_p >= 1 && n_lev * n_p <= PT_MAX_P, "pt_trace_PAinv_nested: need n_lev * n_p <= %d", PT_MAX_P);
+    PT_CHECK_ARG(n_sets >= 1 && set0 >= 0 && mu >= 0 && mu < 4, "pt_trace_PAinv_nested: bad sets or mu");
+    PT_CHECK_ARG(noise == PT_NOISE_Z2 || (noise == PT_NOISE_Z4 && op->dof == 12),
+                 "pt_trace_PAinv_nested: Z4 noise needs the complex (Wilson) operator");
+    const int m_fin = n_colours[n_lev - 1];
+    PT_CHECK_ARG(m_fin >= 1 && m_fin <= op->g.N, "pt_trace_PAinv_nested: n_colours out of range");
+    int rc = check_solver_args(prec, tol, maxit);
+    if (rc) return rc;
+    PT_CUDA(cudaSetDevice(c->device));
+    const int N = op->g.N;
+    int *anc = nullptr;
+    PT_CUDA(cudaMallocAsync((void **)&anc, ((size_t)n_lev * m_fin + 64) * sizeof(int), c->stream));
+    int *bad = anc + (size_t)n_lev * m_fin;
+    PT_CUDA(cudaMemsetAsync(anc, 0xff, ((size_t)n_lev * m_fin + 64) * sizeof(int), c->stream));
+    PT_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+    const int blocks = (int)std::min<long>(((long)N + 255) / 256, 16L * c->num_sms);
+    k_nest_anc<<<blocks, 256, 0, c->stream>>>(N, n_lev, m_fin, cols_dev, anc, bad);
+    k_nest_check<<<blocks, 256, 0, c->stream>>>(N, n_lev, m_fin, cols_dev, anc, bad);
+    pt_kernel_launch_count += 2;
+    PT_CUDA(cudaGetLastError());
+    PT_CUDA(cudaMemcpyAsync(c->h_flags, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PT_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->h_flags[0]) {
+        const int f = c->h_flags[0];
+        cudaFreeAsync(anc, c->stream);
+        PT_CHECK_ARG(false, "pt_trace_PAinv_nested: %s", (f & 1) ? "finest colours outside [0, n_colours)"
+                                                                   : "colourings are not nested");
+    }
+    std::vector<Task> tasks;
+    build_probe_tasks(0, m_fin, set0, n_sets, op->dof, dilute, 0, tasks);
+    std::vector<int> p_ext((size_t)n_lev * n_p);
+    for (int q = 0; q < n_lev * n_p; ++q) p_ext[q] = p_list[q % n_p];
+    EngineRequest rq;
+    rq.mode = MODE_TRACE;
+    rq.n_tasks = (int)tasks.size();
+    rq.h_tasks = tasks.data();
+    rq.col = cols_dev + (size_t)(n_lev - 1) * N;
+    rq.seed = seed;
+    rq.noise = noise; rq.mu = mu; rq.n_p = n_lev * n_p; rq.dilute = dilute ? 1 : 0; rq.pshift = 0;
+    rq.p_list = p_ext.data();
+    rq.B_user = nullptr;
+    rq.X_user = nullptr;
+    rq.tol = tol;
+    rq.maxit = maxit;
+    rq.prec = prec;
+    rq.R_force = 0;
+    rq.n_lev = n_lev;
+    rq.n_pr = n_p;
+    rq.m_fin = m_fin;
+    rq.lev_cols = cols_dev;
+    rq.lev_anc = anc;
+    rc = run_engine(op, rq, stats);
+    cudaFreeAsync(anc, c->stream);
+    if (rc != PT_OK && rc != PT_ERR_NOCONV) return rc;
+    // est[l][s][n] = sum over the finest classes of their contraction with the level-l probe
+    const int Q = n_lev * n_p;
+    for (size_t i = 0; i < (size_t)n_lev * n_sets * n_p * 2; ++i) est_out[i] = 0.0;
+    for (size_t t = 0; t < tasks.size(); ++t)
+        for (int q = 0; q < Q; ++q) {
+            const int l = q / n_p, n = q % n_p;
+            const size_t o = (((size_t)l * n_sets + (tasks[t].set - set0)) * n_p + n) * 2;
+            est_out[o] += rq.task_out[(t * Q + q) * 2];
+            est_out[o + 1] += rq.task_out[(t * Q + q) * 2 + 1];
+        }
+    return rc;
+}
+
 // ------------------------------------------------------------------ pt_grad
 // per probe pair (slot 2i = x, slot 2i+1 = w, y = g5 w for Wilson, y = w for the
 // Laplacian): dots y^H x and y^H v, and for Wilson the link outer products.
@@ -1741,6 +1995,7 @@ static int store_tuning(pt_ctx *c, const pt_op *op, int prec, const pt_tune *t) 
     e.delta = t->delta;
     e.group = t->group;
     e.graph_iters = t->graph_iters;
+    e.rhs_block = t->rhs_block == 2 ? 2 : 1;
     return PT_OK;
 }
 
@@ -1752,6 +2007,7 @@ extern "C" int pt_set_tuning(pt_ctx *c, const pt_op *op, int prec, const pt_tune
         PT_CHECK_ARG(t->delta >= 0.0 && t->delta < 1.0, "pt_set_tuning: delta must be in [0, 1)");
         PT_CHECK_ARG(t->group >= 1 && t->group <= 64, "pt_set_tuning: group must be in [1, 64]");
         PT_CHECK_ARG(t->graph_iters >= 1 && t->graph_iters <= 64, "pt_set_tuning: graph_iters must be in [1, 64]");
+        PT_CHECK_ARG(t->rhs_block >= 0 && t->rhs_block <= 2, "pt_set_tuning: rhs_block must be 0, 1 or 2");
     }
     return store_tuning(c, op, prec, t);
 }
@@ -1762,7 +2018,7 @@ extern "C" int pt_get_tuning(pt_ctx *c, const pt_op *op, int prec, pt_tune *t) {
     t->delta = e.delta;
     t->group = e.group;
     t->graph_iters = e.graph_iters;
-    t->pad = 0;
+    t->rhs_block = e.rhs_block;
     t->seconds_per_rhs = 0.0;
     return PT_OK;
 }
@@ -1824,12 +2080,16 @@ extern "C" int pt_autotune(pt_ctx *c, const pt_op *op, const int32_t *col_dev, i
     std::vector<int> groups;
     if (op->kind == 1) groups = {1, 2, 4, 8, 16};
     const std::vector<int> iters = {4, 8, 16};
-    for (int pass = 0; pass < 3 && !rc; ++pass) {
-        const size_t nc = pass == 0 ? deltas.size() : pass == 1 ? groups.size() : iters.size();
+    std::vector<int> blocks;
+    if (op->kind == 1 && prec != PT_PREC_FP64) blocks = {1, 2};
+    for (int pass = 0; pass < 4 && !rc; ++pass) {
+        const size_t nc = pass == 0 ? deltas.size() : pass == 1 ? blocks.size() : pass == 2 ? groups.size()
+                                                                                              : iters.size();
         for (size_t i = 0; i < nc && !rc; ++i) {
             pt_ctx::Tune cand = cur;
             if (pass == 0) cand.delta = deltas[i];
-            else if (pass == 1) cand.group = groups[i];
+            else if (pass == 1) cand.rhs_block = blocks[i];
+            else if (pass == 2) cand.group = groups[i];
             else cand.graph_iters = iters[i];
             if (!memcmp(&cand, &cur, sizeof(cand))) continue;
             double t = 0.0;
@@ -1844,7 +2104,7 @@ extern "C" int pt_autotune(pt_ctx *c, const pt_op *op, const int32_t *col_dev, i
     best->delta = cur.delta;
     best->group = cur.group;
     best->graph_iters = cur.graph_iters;
-    best->pad = 0;
+    best->rhs_block = cur.rhs_block;
     best->seconds_per_rhs = t_best / trial.size();
     return store_tuning(c, op, prec, best);
 }

@@ -372,6 +372,68 @@ __device__ __forceinline__ void wilson_hop_site(const Geom &g, const S *f, const
     }
 }
 
+// (H psi_n)(x) for NB right-hand sides at one site: every link is loaded once
+// and applied to the NB spin-projected neighbours (the links of a site block
+// are shared by the right-hand sides of the block).
+template <typename R, typename S, typename LS, int NB>
+__device__ __forceinline__ void wilson_hop_multi(const Geom &g, const S *const (&f)[NB], const LS *U, int antip,
+                                                 int idx, const int x[4], Cx<R> (&acc)[NB][4][3]) {
+    const int N = g.N;
+#pragma unroll
+    for (int n = 0; n < NB; ++n)
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[n][s][a] = Cx<R>{R(0), R(0)};
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        {   // forward hop: (1 - g_mu) U_mu(x) psi(x + mu)
+            const int y = nb_fwd(g, idx, x, mu);
+            const R eta = (antip && mu == 3 && x[3] == g.D[3] - 1) ? R(-1) : R(1);
+            Cx<R> u[3][3];
+            load_link<R, LS>(U, N, mu, idx, u);
+#pragma unroll
+            for (int n = 0; n < NB; ++n) {
+                Cx<R> ps[4][3], h[2][3], uh[2][3];
+                load_spinor<S, R>(f[n], N, y, ps);
+                spin_project<R>(mu, R(-1), ps, h);
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        Cx<R> t = cmul(u[a][0], h[k][0]);
+                        t = cadd(t, cmul(u[a][1], h[k][1]));
+                        t = cadd(t, cmul(u[a][2], h[k][2]));
+                        uh[k][a] = t;
+                    }
+                spin_accumulate<R>(mu, R(-1), eta, uh, acc[n]);
+            }
+        }
+        {   // backward hop: (1 + g_mu) U_mu(x - mu)^dagger psi(x - mu)
+            const int y = nb_bwd(g, idx, x, mu);
+            const R eta = (antip && mu == 3 && x[3] == 0) ? R(-1) : R(1);
+            Cx<R> u[3][3];
+            load_link<R, LS>(U, N, mu, y, u);
+#pragma unroll
+            for (int n = 0; n < NB; ++n) {
+                Cx<R> ps[4][3], h[2][3], uh[2][3];
+                load_spinor<S, R>(f[n], N, y, ps);
+                spin_project<R>(mu, R(1), ps, h);
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        Cx<R> t = cconjmul(u[0][a], h[k][0]);
+                        t = cadd(t, cconjmul(u[1][a], h[k][1]));
+                        t = cadd(t, cconjmul(u[2][a], h[k][2]));
+                        uh[k][a] = t;
+                    }
+                spin_accumulate<R>(mu, R(1), eta, uh, acc[n]);
+            }
+        }
+    }
+}
+
 // Laplacian: (A f)(x) = (8 + m2) f(x) - sum_mu [f(x+mu) + f(x-mu)]
 template <typename R, typename S>
 __device__ __forceinline__ R lap_site(const Geom &g, const S *f, R diag, int idx, const int x[4]) {
@@ -424,7 +486,7 @@ struct pt_ctx {
     struct Tune {
         int used, kind, prec, dims[4];
         double delta;
-        int group, graph_iters;
+        int group, graph_iters, rhs_block;
     } tune[16], trial;
     int in_trial;
     // grow-only work space

@@ -45,11 +45,11 @@ class Stats(ctypes.Structure):
 
 class Tune(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("group", ctypes.c_int32), ("graph_iters", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("seconds_per_rhs", ctypes.c_double)]
+                ("rhs_block", ctypes.c_int32), ("seconds_per_rhs", ctypes.c_double)]
 
     def as_dict(self):
         return {"delta": self.delta, "group": self.group, "graph_iters": self.graph_iters,
-                "seconds_per_rhs": self.seconds_per_rhs}
+                "rhs_block": self.rhs_block, "seconds_per_rhs": self.seconds_per_rhs}
 
 
 _lib = None
@@ -76,6 +76,8 @@ _SIGS = {
     "pt_apply": ([_P, _P, _P, _P, _I, _I], _I),
     "pt_stencil": ([_I, ctypes.POINTER(_I), _I, _I, ctypes.POINTER(_I), _I, ctypes.POINTER(_I)], _I),
     "pt_colour": ([_P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _I, _I, _I, _P, ctypes.POINTER(_I)], _I),
+    "pt_colour_nested": ([_P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _I, _I, _I, _P, _I, _P,
+                          ctypes.POINTER(_I)], _I),
     "pt_colour_conflicts": ([_P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _I, _I, _P,
                              ctypes.POINTER(ctypes.c_int64)], _I),
     "pt_colour_conflicts_noalloc": ([_P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _I, _I, _P,
@@ -91,6 +93,8 @@ _SIGS = {
                         _P, _P, _P, ctypes.POINTER(Stats)], _I),
     "pt_trace_PAinv_multi": ([_P, _P, _I, _P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _I, _I, ctypes.c_uint64,
                               _I, _I, _I, _I, _D, _I, _P, ctypes.POINTER(Stats)], _I),
+    "pt_trace_PAinv_nested": ([_P, _P, _I, _P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _I, _I, ctypes.c_uint64,
+                               _I, _I, _I, _I, _D, _I, _P, ctypes.POINTER(Stats)], _I),
     "pt_grad": ([_P, _P, _P, _I, _I, _I, _I, ctypes.c_uint64, _I, _I, _I, _I, _D, _I, _P, _P, _P, _P,
                  ctypes.POINTER(Stats)], _I),
 }
@@ -293,6 +297,19 @@ def colour(ctx, dims, mu, p_list, k, order="natural", out=None):
     return col, m.value
 
 
+def colour_nested(ctx, dims, mu, p_list, k, parent, n_parent, order="natural", out=None):
+    """Colouring at distance k nested in the coarser colouring `parent`
+    (pt_colour_nested): (col, m)."""
+    import torch
+    N = int(np.prod(dims))
+    col = out if out is not None else torch.empty(N, dtype=torch.int32, device="cuda:%d" % ctx.device)
+    m = _I()
+    _check(lib().pt_colour_nested(ctx.handle, _ints(dims), int(mu), _ints(p_list), len(p_list), int(k),
+                                  ORDER[order] if isinstance(order, str) else int(order), _ptr(parent),
+                                  int(n_parent), _ptr(col), ctypes.byref(m)))
+    return col, m.value
+
+
 def conflicts(ctx, dims, mu, p_list, k, col):
     n = ctypes.c_int64()
     _check(lib().pt_colour_conflicts(ctx.handle, _ints(dims), mu, _ints(p_list), len(p_list), k, _ptr(col),
@@ -407,13 +424,14 @@ def autotune(op, col, n_colours, mu, noise="z2", seed=0, prec="mixed_fp32", tol=
     return t.as_dict()
 
 
-def set_tuning(op, prec, delta=None, group=None, graph_iters=None, reset=False):
+def set_tuning(op, prec, delta=None, group=None, graph_iters=None, rhs_block=None, reset=False):
     if reset:
         _check(lib().pt_set_tuning(op.ctx.handle, op._h, PREC[prec], None))
         return
     cur = get_tuning(op, prec)
     t = Tune(cur["delta"] if delta is None else float(delta), cur["group"] if group is None else int(group),
-             cur["graph_iters"] if graph_iters is None else int(graph_iters), 0, 0.0)
+             cur["graph_iters"] if graph_iters is None else int(graph_iters),
+             cur["rhs_block"] if rhs_block is None else int(rhs_block), 0.0)
     _check(lib().pt_set_tuning(op.ctx.handle, op._h, PREC[prec], ctypes.byref(t)))
 
 
@@ -436,6 +454,23 @@ def trace_multi(op, cols, n_colours, mu, p_list, noise="z2", seed=0, set0=0, n_s
                                     _ints(p_list), n_p, NOISE[noise] if isinstance(noise, str) else int(noise),
                                     int(seed), int(set0), int(n_sets), 1 if dilute else 0, PREC[prec], float(tol),
                                     int(maxit), _np_ptr(est), ctypes.byref(st))
+    _check(rc)
+    return est, st.as_dict()
+
+
+def trace_nested(op, cols, n_colours, mu, p_list, noise="z2", seed=0, set0=0, n_sets=1, dilute=True,
+                 prec="mixed_fp32", tol=1e-10, maxit=20000):
+    """Estimates at every level of nested colourings cols [n_lev, N] (coarsest
+    first) from the finest level's solves.  Returns (est[n_lev, n_sets, n_p], stats)."""
+    n_lev = len(n_colours)
+    assert cols.shape[0] == n_lev and cols.is_contiguous()
+    n_p = len(p_list)
+    est = np.zeros((n_lev, n_sets, n_p), dtype=np.complex128)
+    st = Stats()
+    rc = lib().pt_trace_PAinv_nested(op.ctx.handle, op._h, n_lev, _ptr(cols), _ints(n_colours), int(mu),
+                                     _ints(p_list), n_p, NOISE[noise] if isinstance(noise, str) else int(noise),
+                                     int(seed), int(set0), int(n_sets), 1 if dilute else 0, PREC[prec], float(tol),
+                                     int(maxit), _np_ptr(est), ctypes.byref(st))
     _check(rc)
     return est, st.as_dict()
 

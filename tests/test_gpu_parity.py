@@ -398,12 +398,40 @@ def test_autotune_then_parity(pt, ctx):
     bw = pt.autotune(opw, _t(colw), mw, mu, "z4", 5, "mixed_fp32", 1e-10, 5000, 12)
     assert bw["group"] in (1, 2, 4, 8, 16)
     pt.set_tuning(opw, "mixed_fp32", delta=1e-3, group=2, graph_iters=4)
-    assert pt.get_tuning(opw, "mixed_fp32") == {"delta": 1e-3, "group": 2, "graph_iters": 4, "seconds_per_rhs": 0.0}
+    assert pt.get_tuning(opw, "mixed_fp32") == {"delta": 1e-3, "group": 2, "graph_iters": 4, "rhs_block": 1,
+                                                "seconds_per_rhs": 0.0}
     est, _, _, _ = pt.trace(opw, _t(colw), mw, mu, [1], "z4", 5, 0, 1, True, "mixed_fp32", 1e-10, 5000)
     want = OE.probed_estimates(OE.Wilson(dims, U, kappa), colw, mw, 5, 1, 1, mu, [1], 1e-12)
     assert np.allclose(est, want, rtol=1e-8, atol=1e-7)
     pt.set_tuning(opw, "mixed_fp32", reset=True)
     pt.set_tuning(op, "mixed_fp32", reset=True)
+
+
+@pytest.mark.parametrize("prec,group", [("mixed_fp32", 8), ("mixed_fp32", 1), ("mixed_bf16", 4)])
+def test_wilson_two_rhs_items_parity(pt, ctx, prec, group):
+    """rhs_block = 2 (two right-hand sides per item, one link load for both):
+    traces match the oracle, and solves of an odd number of sources (a pair
+    with one member) match the one-per-item engine."""
+    import torch
+    dims, kappa, mu = [4, 6, 4, 8], 0.12, 2
+    U = inputs.gauge_links(dims, 77)
+    col, m = greedy_colour(dims, mu, [2], 1, 1)
+    op = pt.wilson(ctx, dims, _t(U), kappa, True)
+    pt.set_tuning(op, prec, group=group, rhs_block=2)
+    assert pt.get_tuning(op, prec)["rhs_block"] == 2
+    est, _, _, st = pt.trace(op, _t(col), m, mu, [0, 2], "z4", 9, 0, 2, True, prec, 1e-10, 5000)
+    want = OE.probed_estimates(OE.Wilson(dims, U, kappa), col, m, 9, 2, 1, mu, [0, 2], 1e-12)
+    assert np.allclose(est, want, rtol=1e-8, atol=1e-7)
+    assert st["max_relres"] <= 1e-10
+    N = int(np.prod(dims))
+    rng = np.random.default_rng(4)
+    B = torch.as_tensor(rng.standard_normal((3, N, 4, 3, 2))).cuda().contiguous()
+    X2, _, r2, _ = pt.solve(op, B, prec, 1e-10, 5000)
+    pt.set_tuning(op, prec, rhs_block=1)
+    X1, _, r1, _ = pt.solve(op, B, prec, 1e-10, 5000)
+    assert max(r1) <= 1e-10 and max(r2) <= 1e-10
+    assert torch.allclose(X2, X1, rtol=1e-8, atol=1e-9 * X1.abs().max().item())
+    pt.set_tuning(op, prec, reset=True)
 
 
 # ------------------------------------------------------------------ edge cases

@@ -123,3 +123,79 @@ def test_table5_on_the_32cube_x_64_lattice(pt, ctx):
     pct = _half_up(100.0 * matches / (N * size))
     for j, k in enumerate(ks):
         assert np.allclose(pct[:, j], want[k], atol=1e-9), (k, pct[:, j], want[k])
+
+
+NESTED_CASES = [([16, 16, 16, 16], 3, [2], 0), ([16, 16, 16, 16], 3, [4], 1), ([6, 5, 8, 4], 2, [1], 1),
+                ([24, 24, 24, 12], 2, [1], 0)]          # the last: colours beyond shared memory
+
+
+@pytest.mark.parametrize("dims,mu,p,order", NESTED_CASES)
+def test_nested_colouring_bit_exact(pt, ctx, dims, mu, p, order):
+    """Colourings grown k = 1 -> 2 -> 3 (-> 4 on 16^4, the lap16 lattice):
+    every level bit-exact against the oracle, valid, and nested."""
+    from oracle.colouring import nested_colour
+    kmax = 4 if dims == [16, 16, 16, 16] else 3
+    prev, m_prev = pt.colour(ctx, dims, mu, p, 1, order)
+    want_prev, _ = greedy_colour(dims, mu, p, 1, order)
+    assert np.array_equal(prev.cpu().numpy(), want_prev)
+    for k in range(2, kmax + 1):
+        want, m_want = nested_colour(dims, mu, p, k, want_prev, order)
+        col, m = pt.colour_nested(ctx, dims, mu, p, k, prev, m_prev, order)
+        assert m == m_want
+        assert np.array_equal(col.cpu().numpy(), want)
+        assert pt.conflicts(ctx, dims, mu, p, k, col) == 0
+        prev, m_prev, want_prev = col, m, want
+
+
+def test_nested_rejects_parent_out_of_range(pt, ctx):
+    import torch
+    dims = [4, 4, 8, 4]
+    parent = torch.full((512,), 3, dtype=torch.int32, device="cuda")
+    with pytest.raises(pt.PtraceError):
+        pt.colour_nested(ctx, dims, 2, [1], 2, parent, 2)       # parent colour 3 >= n_parent 2
+    col, m = pt.colour_nested(ctx, dims, 2, [1], 2, parent, 4)   # and the context is still usable
+    want, mw = greedy_colour(dims, 2, [1], 2, 0)
+    assert m == mw and np.array_equal(col.cpu().numpy(), want)
+
+
+def test_nested_trace_matches_independent_levels(pt, ctx):
+    """Solving only the finest of nested colourings k = 1, 2, 3 gives, at every
+    level, the estimate the oracle gets by solving that level's own probes."""
+    import torch
+    import oracle.estimator as OE
+    from oracle.colouring import nested_colour
+    dims, m2, mu, ps = [8, 8, 8, 8], 0.05, 3, [0, 1, 2]
+    c1, m1 = greedy_colour(dims, mu, [2], 1, 0)
+    c2, m2_ = nested_colour(dims, mu, [2], 2, c1, 0)
+    c3, m3 = nested_colour(dims, mu, [2], 3, c2, 0)
+    cols = torch.as_tensor(np.stack([c1, c2, c3])).cuda().contiguous()
+    op = pt.laplacian(ctx, dims, m2)
+    est, st = pt.trace_nested(op, cols, [m1, m2_, m3], mu, ps, "z2", 21, 0, 2, True, "mixed_fp32", 1e-10, 5000)
+    assert st["n_rhs"] == 2 * m3
+    lap = OE.Laplacian(dims, m2)
+    for l, (c, m) in enumerate([(c1, m1), (c2, m2_), (c3, m3)]):
+        want = OE.probed_estimates(lap, c, m, 21, 2, 0, mu, ps, 1e-12)
+        assert np.allclose(est[l], want, rtol=1e-8, atol=1e-8), l
+    # colourings that are not nested are refused
+    bad = torch.as_tensor(np.stack([c2, c1])).cuda().contiguous()
+    with pytest.raises(pt.PtraceError):
+        pt.trace_nested(op, bad, [m2_, m1], mu, ps, "z2", 21, 0, 1, True, "mixed_fp32", 1e-10, 5000)
+
+
+def test_nested_trace_wilson_diluted(pt, ctx):
+    import torch
+    import oracle.estimator as OE
+    from oracle.colouring import nested_colour
+    from paper_2106_01275_gb300 import inputs
+    dims, kappa, mu = [4, 4, 8, 4], 0.12, 2
+    U = inputs.gauge_links(dims, 5)
+    c1, m1 = greedy_colour(dims, mu, [1], 1, 1)
+    c2, m2 = nested_colour(dims, mu, [1], 2, c1, 1)
+    cols = torch.as_tensor(np.stack([c1, c2])).cuda().contiguous()
+    op = pt.wilson(ctx, dims, torch.as_tensor(U).cuda(), kappa, True)
+    est, st = pt.trace_nested(op, cols, [m1, m2], mu, [0, 1], "z4", 3, 0, 1, True, "mixed_fp32", 1e-10, 5000)
+    assert st["n_rhs"] == 12 * m2
+    W = OE.Wilson(dims, U, kappa)
+    for l, (c, m) in enumerate([(c1, m1), (c2, m2)]):
+        want = OE.probed_estimates(W, c, m, 3, 1, 1, mu, [0, 1], 1e-12)
+        assert np.allclose(est[l], want, rtol=1e-8, atol=1e-7), l

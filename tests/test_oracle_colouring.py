@@ -172,3 +172,81 @@ def test_first_fit_checker_accepts_greedy_and_flags_changes():
         bad = col.copy()
         bad[100] = (bad[100] + 1) % m
         assert 100 in first_fit_violations(bad, dims, 2, [2], 2, order, range(col.size))
+
+
+def _first_fit_nested(col_local_pairs, parent, dims, mu, p, k, order):
+    """Independent check of the nested definition: per node, the local colour
+    is the smallest absent among earlier-visited neighbours of the same parent
+    class; pairs are numbered in first-visit order."""
+    st = displaced_stencil(4, mu, [p], k)
+    visit = L.visit_order(dims, mu, order)
+    rank = np.empty_like(visit)
+    rank[visit] = np.arange(visit.shape[0])
+    xs = L.coords(dims)
+    nb = L.index_of(xs[:, None, :] + st[None], dims)
+    col = col_local_pairs
+    # recover local colours: within a parent class, number the child classes by first visit
+    seen, numbering = {}, []
+    for x in visit:
+        c = int(col[x])
+        if c not in seen:
+            seen[c] = len(seen)
+            numbering.append(c)
+    assert numbering == list(range(len(numbering)))               # first-visit order
+    local = {}
+    for x in visit:
+        pa, c = int(parent[x]), int(col[x])
+        earlier = {local[int(y)] for y in nb[x] if y != x and rank[y] < rank[x] and parent[y] == pa}
+        lo = 0
+        while lo in earlier:
+            lo += 1
+        local[int(x)] = lo
+    # equal colour <=> equal (parent, local)
+    key = {}
+    for x in range(col.size):
+        kk = (int(parent[x]), local[x])
+        assert key.setdefault(int(col[x]), kk) == kk
+
+
+@pytest.mark.parametrize("dims,mu,p,order", [([8, 8, 8, 8], 3, 2, 0), ([8, 8, 8, 8], 3, 0, 1), ([6, 4, 8, 4], 2, 1, 1)])
+def test_nested_colouring_levels(dims, mu, p, order):
+    """Nested colourings for k = 1..3: valid at each level, every class inside
+    one parent class, local first-fit within each parent class, pairs numbered
+    in first-visit order."""
+    from oracle.colouring import nested_colour
+    prev, _ = greedy_colour(dims, mu, [p], 1, order)
+    for k in (2, 3):
+        col, m = nested_colour(dims, mu, [p], k, prev, order)
+        assert conflicts(col, dims, mu, [p], k) == 0
+        assert set(np.unique(col).tolist()) == set(range(m))
+        for c in range(m):
+            assert np.unique(prev[col == c]).size == 1             # nesting
+        _first_fit_nested(col, prev, dims, mu, p, k, order)
+        prev = col
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_nested_with_one_parent_is_algorithm_1(order):
+    """A constant parent colouring leaves nothing to nest: the result is the
+    plain greedy colouring (first-fit colours already appear in order)."""
+    from oracle.colouring import nested_colour
+    for dims, mu, p, k in [([8, 8, 8, 8], 3, 2, 2), ([5, 6, 7, 3], 2, 1, 2)]:
+        want, mw = greedy_colour(dims, mu, [p], k, order)
+        got, mg = nested_colour(dims, mu, [p], k, np.zeros(int(np.prod(dims)), np.int32), order)
+        assert mg == mw and np.array_equal(got, want)
+
+
+def test_nested_probes_sum_to_parent_probe():
+    """The point of nesting: the probes of the child classes of a parent class
+    sum to the parent's probe (Eq. (3) with shared noise), so solves at the
+    finer level give the coarser estimate by linearity."""
+    from oracle.colouring import nested_colour
+    from oracle.probes import probe
+    dims, mu, p = [8, 8, 8, 8], 3, 2
+    par, mp_ = greedy_colour(dims, mu, [p], 1, 0)
+    ch, mc = nested_colour(dims, mu, [p], 2, par, 0)
+    for kind in (0, 1):                                             # Z2, Z4
+        for c1 in range(mp_):
+            kids = np.unique(ch[par == c1])
+            s = sum(probe(ch, int(c2), 11, 0, kind) for c2 in kids)
+            assert np.array_equal(s, probe(par, c1, 11, 0, kind))
