@@ -356,7 +356,7 @@ PT_API int pt_trace_PAinv_multi(pt_ctx *ctx, const pt_op *op, int n_col, const i
  *   est_out[l][s][n] (host complex128 [n_lev][n_sets][n_p])
  *     = sum_{c_l} sum_a v_{s,c_l,a}^H P_{p_n} A^{-1} v_{s,c_l,a},
  * the pt_trace_PAinv_multi result for colouring l, at the cost of the finest
- * level's solves.  n_lev * n_p <= 16.  A temporary stream-ordered
+ * level's solves.  n_lev * n_p <= 32.  A temporary stream-ordered
  * allocation holds the ancestor table.  Other arguments as pt_trace_PAinv.
  * Synchronises. */
 PT_API int pt_trace_PAinv_nested(pt_ctx *ctx, const pt_op *op, int n_lev, const int32_t *cols_dev,

@@ -240,11 +240,12 @@ __device__ __forceinline__ void item_store_r(const EP &P, int j, int b, R vr[K],
 
 // contraction partials: only the first K = 2 n_p of the 2 PT_MAX_P entries are
 // reduced (FP64 throughout: these are the trace accumulations); the rest are zero
-__device__ __forceinline__ void item_store_contract(const EP &P, int j, int b, double acc[2 * PT_MAX_P], int K,
+template <int MAXQ>
+__device__ __forceinline__ void item_store_contract(const EP &P, int j, int b, double acc[2 * MAXQ], int K,
                                                     double *sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
-    for (int k = 0; k < 2 * PT_MAX_P; ++k) {
+    for (int k = 0; k < 2 * MAXQ; ++k) {
         if (k < K) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
@@ -253,7 +254,7 @@ __device__ __forceinline__ void item_store_contract(const EP &P, int j, int b, d
     __syncthreads();
     if (lane == 0)
 #pragma unroll
-        for (int k = 0; k < 2 * PT_MAX_P; ++k)
+        for (int k = 0; k < 2 * MAXQ; ++k)
             if (k < K) sh[warp * 2 * PT_MAX_P + k] = acc[k];
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -380,7 +381,8 @@ __global__ void __launch_bounds__(1024) k_schedule(EP P) {
 // ------------------------------------------------------------------ contract / copy-out
 // trace mode: q_n = sum_x conj(v(x)) x(x + p_n e_mu) for every displacement
 // (the shifted dot of Eq. (1) with P_{p_n}); solve mode: copy x to the user.
-template <int KIND>
+// MAXQ: compiled bound on the outputs per solve (displacements x nested levels)
+template <int KIND, int MAXQ>
 __global__ void __launch_bounds__(PT_BLOCK) k_contract(EP P) {
     __shared__ double sh[32 * 2 * PT_MAX_P];
     const int N = P.g.N;
@@ -404,9 +406,9 @@ __global__ void __launch_bounds__(PT_BLOCK) k_contract(EP P) {
             SITE_LOOP_END
             continue;
         }
-        double acc[2 * PT_MAX_P];
+        double acc[2 * MAXQ];
 #pragma unroll
-        for (int n = 0; n < 2 * PT_MAX_P; ++n) acc[n] = 0.0;
+        for (int n = 0; n < 2 * MAXQ; ++n) acc[n] = 0.0;
         const uint64_t key = pt_set_key(P.seed, tk.set);
         const int32_t *col = P.col + (size_t)tk.cidx * N;
         SITE_LOOP(KIND)
@@ -423,7 +425,7 @@ __global__ void __launch_bounds__(PT_BLOCK) k_contract(EP P) {
                 Cx<double> z = P.dilute ? pt_noise(key, (uint64_t)idx, P.noise)
                                         : pt_noise(key, (uint64_t)idx * dof + a, P.noise);
 #pragma unroll
-                for (int n = 0; n < PT_MAX_P; ++n) {
+                for (int n = 0; n < MAXQ; ++n) {
                     if (n >= P.n_p) break;
                     if (P.n_lev) {
                         const int l = n / P.n_pr;
@@ -437,7 +439,7 @@ __global__ void __launch_bounds__(PT_BLOCK) k_contract(EP P) {
                 }
             }
         SITE_LOOP_END
-        item_store_contract(P, j, b, acc, 2 * P.n_p, sh);
+        item_store_contract<MAXQ>(P, j, b, acc, 2 * P.n_p, sh);
     ITEM_LOOP_END
 }
 
@@ -1165,7 +1167,7 @@ struct EngineRun {
     int kernels_per_iter;
     // persistent grid of each item kernel: SMs x its own resident CTAs per SM
     int g_contract, g_oupd, g_ores, g_apply1, g_apply2, g_upd, g_s, g_dir;
-    int g_apply1_x2, g_apply2_x2;
+    int g_apply1_x2, g_apply2_x2, g_contract32;
 };
 
 template <typename K>
@@ -1191,7 +1193,8 @@ static void enqueue_iteration(const EngineRun &E, cudaStream_t st, const cudaEve
     const int W = E.grid_warps;
     ev_rec(ev, 7, st);
     k_schedule<<<1, 1024, 0, st>>>(P);
-    k_contract<KIND><<<E.g_contract, PT_BLOCK, 0, st>>>(P);
+    if (P.n_p <= 16) k_contract<KIND, 16><<<E.g_contract, PT_BLOCK, 0, st>>>(P);
+    else k_contract<KIND, PT_MAX_P><<<E.g_contract32, PT_BLOCK, 0, st>>>(P);
     k_fin_contract<<<W, 256, 0, st>>>(P);
     ev_rec(ev, 5, st);
     k_outer_update<KIND, S><<<E.g_oupd, PT_BLOCK, 0, st>>>(P);
@@ -1399,7 +1402,8 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     occ = std::max(occ, 1);
     E.grid_items = c->num_sms * occ;
     const int ns = c->num_sms;
-    E.g_contract = persistent_grid(k_contract<KIND>, ns);
+    E.g_contract = persistent_grid(k_contract<KIND, 16>, ns);
+    E.g_contract32 = persistent_grid(k_contract<KIND, PT_MAX_P>, ns);
     E.g_oupd = persistent_grid(k_outer_update<KIND, S>, ns);
     E.g_ores = persistent_grid(k_outer_residual<KIND, S>, ns);
     if constexpr (KIND == 0) {

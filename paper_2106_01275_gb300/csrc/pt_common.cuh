@@ -24,7 +24,7 @@
 
 #include "../../include/ptrace.h"
 
-#define PT_MAX_P 16          // displacements contracted in one call
+#define PT_MAX_P 32          // displacements (times nested levels) contracted in one call
 #define PT_BS 128            // sites per CTA work item
 
 // ------------------------------------------------------------------ errors
