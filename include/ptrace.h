@@ -122,12 +122,17 @@ PT_API int pt_set_max_slots(pt_ctx *ctx, int n);
  *   rhs_block    right-hand sides per work item of the Wilson applies in
  *                the mixed-precision inner solve: 1, or 2 (each link load
  *                then serves two right-hand sides); 0 means 1
+ *   overlap      1: within an engine iteration the contraction and the FP64
+ *                outer steps run as CUDA-graph branches beside the inner
+ *                Krylov kernels (they work on disjoint right-hand sides);
+ *                0: one kernel after another
  * seconds_per_rhs is an output of pt_autotune (device time per trial RHS). */
 typedef struct pt_tune {
     double delta;
     int32_t group;
     int32_t graph_iters;
     int32_t rhs_block;
+    int32_t overlap;
     double seconds_per_rhs;
 } pt_tune;
 

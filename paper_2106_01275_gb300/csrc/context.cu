@@ -53,6 +53,8 @@ extern "C" int pt_create(pt_ctx **out, int device, void *stream) {
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     cudaError_t e = cudaMallocHost((void **)&c->h_flags, 64 * sizeof(int));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&c->cap_side[i], cudaStreamNonBlocking);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&c->cap_ev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         if (c->h_flags) cudaFreeHost(c->h_flags);
         if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -70,6 +72,8 @@ extern "C" int pt_destroy(pt_ctx *c) {
     if (c->ws) cudaFree(c->ws);
     if (c->h_flags) cudaFreeHost(c->h_flags);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (int i = 0; i < 2; ++i) if (c->cap_side[i]) cudaStreamDestroy(c->cap_side[i]);
+    for (int i = 0; i < 3; ++i) if (c->cap_ev[i]) cudaEventDestroy(c->cap_ev[i]);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     free(c);
     return PT_OK;

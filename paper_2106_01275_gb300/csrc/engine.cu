@@ -56,6 +56,7 @@ struct EP {
     Geom g;
     int kind, nsb, R, gs, vec4;
     int rhs_block;             // Wilson applies: right-hand sides per item (1 or 2)
+    int overlap;               // groups run as graph branches: the inner list holds PH_INNER slots only
     // nested trace mode (n_lev > 0): the tasks are the classes of the finest of
     // n_lev nested colourings lev_cols [n_lev][N]; output q = l * n_pr + n is the
     // contraction with the level-l probe (ancestor class lev_anc[l][colour])
@@ -357,7 +358,9 @@ __global__ void __launch_bounds__(1024) k_schedule(EP P) {
         // work lists
         int in_c = (ph == PH_CONTRACT);
         int in_o = (ph == PH_START || ph == PH_OUTER);
-        int in_i = (ph == PH_START || ph == PH_OUTER || ph == PH_INNER);
+        // serial iterations let a slot leaving the outer step start its inner solve at once; with
+        // the groups as concurrent branches the inner list must not share slots with the outer one
+        int in_i = P.overlap ? (ph == PH_INNER) : (ph == PH_START || ph == PH_OUTER || ph == PH_INNER);
         int busy = (ph >= PH_START && ph <= PH_CONTRACT);
         int tc, to, ti, tb;
         int rc = block_exclusive_scan(in_c, sh, tc);
@@ -1168,6 +1171,7 @@ struct EngineRun {
     // persistent grid of each item kernel: SMs x its own resident CTAs per SM
     int g_contract, g_oupd, g_ores, g_apply1, g_apply2, g_upd, g_s, g_dir;
     int g_apply1_x2, g_apply2_x2, g_contract32;
+    double *part_con, *part_outer;   // partial-sum regions of the contraction and outer kernel groups
 };
 
 template <typename K>
@@ -1187,20 +1191,40 @@ static inline void ev_rec(const cudaEvent_t *ev, int i, cudaStream_t st) {
     if (ev) cudaEventRecordWithFlags(ev[i], st, cudaEventRecordExternal);
 }
 
+// One engine iteration.  With `side` (two capture side streams and three
+// events; P.overlap set, so that the scheduler's three work lists are
+// disjoint: a slot leaving the outer step starts its inner solve one
+// iteration later) the contraction and the outer steps run as graph branches
+// beside the inner kernels, each group on its own slots and its own
+// partial-sum region: the FP64 residual (FP64-pipe bound) can share the GPU
+// with the memory-bound inner kernels.  The branches join before the next
+// iteration's scheduler.
 template <int KIND, typename S, typename LS>
-static void enqueue_iteration(const EngineRun &E, cudaStream_t st, const cudaEvent_t *ev) {
+static void enqueue_iteration(const EngineRun &E, cudaStream_t st, const cudaEvent_t *ev, const cudaStream_t *side,
+                              const cudaEvent_t *sev) {
     const EP &P = E.P;
+    EP Pc = P, Po = P;               // the same parameters with the groups' own partial-sum regions
+    Pc.partials = E.part_con;
+    Po.partials = E.part_outer;
     const int W = E.grid_warps;
     ev_rec(ev, 7, st);
     k_schedule<<<1, 1024, 0, st>>>(P);
-    if (P.n_p <= 16) k_contract<KIND, 16><<<E.g_contract, PT_BLOCK, 0, st>>>(P);
-    else k_contract<KIND, PT_MAX_P><<<E.g_contract32, PT_BLOCK, 0, st>>>(P);
-    k_fin_contract<<<W, 256, 0, st>>>(P);
-    ev_rec(ev, 5, st);
-    k_outer_update<KIND, S><<<E.g_oupd, PT_BLOCK, 0, st>>>(P);
-    k_outer_residual<KIND, S><<<E.g_ores, PT_BLOCK, 0, st>>>(P);
-    k_fin_outer<<<W, 256, 0, st>>>(P);
-    ev_rec(ev, 6, st);
+    cudaStream_t s_con = st, s_out = st;
+    if (side) {
+        cudaEventRecord(sev[0], st);
+        cudaStreamWaitEvent(side[0], sev[0], 0);
+        cudaStreamWaitEvent(side[1], sev[0], 0);
+        s_con = side[0];
+        s_out = side[1];
+    }
+    if (P.n_p <= 16) k_contract<KIND, 16><<<E.g_contract, PT_BLOCK, 0, s_con>>>(Pc);
+    else k_contract<KIND, PT_MAX_P><<<E.g_contract32, PT_BLOCK, 0, s_con>>>(Pc);
+    k_fin_contract<<<W, 256, 0, s_con>>>(Pc);
+    ev_rec(ev, 5, s_out);
+    k_outer_update<KIND, S><<<E.g_oupd, PT_BLOCK, 0, s_out>>>(Po);
+    k_outer_residual<KIND, S><<<E.g_ores, PT_BLOCK, 0, s_out>>>(Po);
+    k_fin_outer<<<W, 256, 0, s_out>>>(Po);
+    ev_rec(ev, 6, s_out);
     if constexpr (KIND == 0) {
         ev_rec(ev, 0, st);
         if (P.vec4) k_cg_apply_v4<S><<<E.g_apply1, PT_BLOCK, 0, st>>>(P);
@@ -1235,6 +1259,12 @@ static void enqueue_iteration(const EngineRun &E, cudaStream_t st, const cudaEve
         k_fin_bicg_beta<<<W, 256, 0, st>>>(P);
         k_bicg_dir<S><<<E.g_dir, PT_BLOCK, 0, st>>>(P);
         ev_rec(ev, 4, st);
+    }
+    if (side) {
+        cudaEventRecord(sev[1], side[0]);
+        cudaEventRecord(sev[2], side[1]);
+        cudaStreamWaitEvent(st, sev[1], 0);
+        cudaStreamWaitEvent(st, sev[2], 0);
     }
     ev_rec(ev, 8, st);
 }
@@ -1288,6 +1318,7 @@ static pt_ctx::Tune engine_tuning(const pt_ctx *c, const pt_op *op, int prec) {
     d.group = op->kind ? 8 : 1;
     d.graph_iters = 8;
     d.rhs_block = 1;
+    d.overlap = 0;
     return d;
 }
 
@@ -1311,7 +1342,11 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     size_t o_vec[7];
     for (int v = 0; v < nvec; ++v) o_vec[v] = take((size_t)R * L * sizeof(S));
     size_t o_slots = take((size_t)R * sizeof(Slot));
+    // partial sums per (slot, item): one region per kernel group (contraction, outer, inner), so that
+    // the groups can run concurrently (their reductions use different strides)
     size_t o_part = take((size_t)R * nsb * K_MAX * sizeof(double));
+    size_t o_part_outer = take((size_t)R * nsb * 4 * sizeof(double));
+    size_t o_part_inner = take((size_t)R * nsb * 4 * sizeof(double));
     size_t o_cnt = take((size_t)R * sizeof(int));
     size_t o_lists = take((size_t)3 * R * sizeof(int));
     size_t o_counts = take(4 * sizeof(int));
@@ -1334,6 +1369,7 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     const pt_ctx::Tune tn = engine_tuning(c, op, rq.prec);
     P.gs = tn.group;
     P.rhs_block = (KIND == 1 && !std::is_same<S, double>::value && tn.rhs_block == 2) ? 2 : 1;
+    P.overlap = tn.overlap ? 1 : 0;
     P.vec4 = (KIND == 0 && g.D[0] % 4 == 0) ? 1 : 0;
     P.L = L;
     P.diag = 8.0 + op->m2;
@@ -1367,7 +1403,9 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     if constexpr (KIND == 0) vp[4] = &P.p1;     // CG: e, r, p (two buffers), q
     for (int v = 0; v < nvec; ++v) *vp[v] = base + o_vec[v];
     P.slots = (Slot *)(base + o_slots);
-    P.partials = (double *)(base + o_part);
+    P.partials = (double *)(base + o_part_inner);
+    E.part_con = (double *)(base + o_part);
+    E.part_outer = (double *)(base + o_part_outer);
     P.counters = (int *)(base + o_cnt);
     P.lists = (int *)(base + o_lists);
     P.counts = (int *)(base + o_counts);
@@ -1437,7 +1475,8 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     cudaGraphExec_t exec;
     PT_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < ITERS; ++i)
-        enqueue_iteration<KIND, S, LS>(E, c->cap_stream, c->prof ? &evs[(size_t)i * PT_EV_PER_ITER] : nullptr);
+        enqueue_iteration<KIND, S, LS>(E, c->cap_stream, c->prof ? &evs[(size_t)i * PT_EV_PER_ITER] : nullptr,
+                                       tn.overlap ? c->cap_side : nullptr, c->cap_ev);
     cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &graph);
     if (ce != cudaSuccess) return pt_cuda_fail(ce, "cudaStreamEndCapture", __FILE__, __LINE__);
     ce = cudaGraphInstantiate(&exec, graph, 0);
@@ -2000,6 +2039,7 @@ static int store_tuning(pt_ctx *c, const pt_op *op, int prec, const pt_tune *t) 
     e.group = t->group;
     e.graph_iters = t->graph_iters;
     e.rhs_block = t->rhs_block == 2 ? 2 : 1;
+    e.overlap = t->overlap ? 1 : 0;
     return PT_OK;
 }
 
@@ -2012,6 +2052,7 @@ extern "C" int pt_set_tuning(pt_ctx *c, const pt_op *op, int prec, const pt_tune
         PT_CHECK_ARG(t->group >= 1 && t->group <= 64, "pt_set_tuning: group must be in [1, 64]");
         PT_CHECK_ARG(t->graph_iters >= 1 && t->graph_iters <= 64, "pt_set_tuning: graph_iters must be in [1, 64]");
         PT_CHECK_ARG(t->rhs_block >= 0 && t->rhs_block <= 2, "pt_set_tuning: rhs_block must be 0, 1 or 2");
+        PT_CHECK_ARG(t->overlap == 0 || t->overlap == 1, "pt_set_tuning: overlap must be 0 or 1");
     }
     return store_tuning(c, op, prec, t);
 }
@@ -2023,6 +2064,7 @@ extern "C" int pt_get_tuning(pt_ctx *c, const pt_op *op, int prec, pt_tune *t) {
     t->group = e.group;
     t->graph_iters = e.graph_iters;
     t->rhs_block = e.rhs_block;
+    t->overlap = e.overlap;
     t->seconds_per_rhs = 0.0;
     return PT_OK;
 }
@@ -2086,15 +2128,17 @@ extern "C" int pt_autotune(pt_ctx *c, const pt_op *op, const int32_t *col_dev, i
     const std::vector<int> iters = {4, 8, 16};
     std::vector<int> blocks;
     if (op->kind == 1 && prec != PT_PREC_FP64) blocks = {1, 2};
-    for (int pass = 0; pass < 4 && !rc; ++pass) {
+    const std::vector<int> overlaps = {0, 1};
+    for (int pass = 0; pass < 5 && !rc; ++pass) {
         const size_t nc = pass == 0 ? deltas.size() : pass == 1 ? blocks.size() : pass == 2 ? groups.size()
-                                                                                              : iters.size();
+                          : pass == 3 ? iters.size() : overlaps.size();
         for (size_t i = 0; i < nc && !rc; ++i) {
             pt_ctx::Tune cand = cur;
             if (pass == 0) cand.delta = deltas[i];
             else if (pass == 1) cand.rhs_block = blocks[i];
             else if (pass == 2) cand.group = groups[i];
-            else cand.graph_iters = iters[i];
+            else if (pass == 3) cand.graph_iters = iters[i];
+            else cand.overlap = overlaps[i];
             if (!memcmp(&cand, &cur, sizeof(cand))) continue;
             double t = 0.0;
             rc = time_candidate(cand, &t);
@@ -2109,6 +2153,7 @@ extern "C" int pt_autotune(pt_ctx *c, const pt_op *op, const int32_t *col_dev, i
     best->group = cur.group;
     best->graph_iters = cur.graph_iters;
     best->rhs_block = cur.rhs_block;
+    best->overlap = cur.overlap;
     best->seconds_per_rhs = t_best / trial.size();
     return store_tuning(c, op, prec, best);
 }

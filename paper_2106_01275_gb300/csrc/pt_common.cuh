@@ -476,6 +476,8 @@ struct pt_ctx {
     int device;
     cudaStream_t stream;
     cudaStream_t cap_stream;   // private stream used only to capture graphs (never executes work)
+    cudaStream_t cap_side[2];  // side streams of a capture (branches of one engine iteration)
+    cudaEvent_t cap_ev[3];     // fork / join markers of those branches
     bool own_stream;
     int num_sms;
     size_t mem_budget;
@@ -486,7 +488,7 @@ struct pt_ctx {
     struct Tune {
         int used, kind, prec, dims[4];
         double delta;
-        int group, graph_iters, rhs_block;
+        int group, graph_iters, rhs_block, overlap;
     } tune[16], trial;
     int in_trial;
     // grow-only work space

@@ -45,11 +45,11 @@ class Stats(ctypes.Structure):
 
 class Tune(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("group", ctypes.c_int32), ("graph_iters", ctypes.c_int32),
-                ("rhs_block", ctypes.c_int32), ("seconds_per_rhs", ctypes.c_double)]
+                ("rhs_block", ctypes.c_int32), ("overlap", ctypes.c_int32), ("seconds_per_rhs", ctypes.c_double)]
 
     def as_dict(self):
         return {"delta": self.delta, "group": self.group, "graph_iters": self.graph_iters,
-                "rhs_block": self.rhs_block, "seconds_per_rhs": self.seconds_per_rhs}
+                "rhs_block": self.rhs_block, "overlap": self.overlap, "seconds_per_rhs": self.seconds_per_rhs}
 
 
 _lib = None
@@ -424,14 +424,15 @@ def autotune(op, col, n_colours, mu, noise="z2", seed=0, prec="mixed_fp32", tol=
     return t.as_dict()
 
 
-def set_tuning(op, prec, delta=None, group=None, graph_iters=None, rhs_block=None, reset=False):
+def set_tuning(op, prec, delta=None, group=None, graph_iters=None, rhs_block=None, overlap=None, reset=False):
     if reset:
         _check(lib().pt_set_tuning(op.ctx.handle, op._h, PREC[prec], None))
         return
     cur = get_tuning(op, prec)
     t = Tune(cur["delta"] if delta is None else float(delta), cur["group"] if group is None else int(group),
              cur["graph_iters"] if graph_iters is None else int(graph_iters),
-             cur["rhs_block"] if rhs_block is None else int(rhs_block), 0.0)
+             cur["rhs_block"] if rhs_block is None else int(rhs_block),
+             cur["overlap"] if overlap is None else int(overlap), 0.0)
     _check(lib().pt_set_tuning(op.ctx.handle, op._h, PREC[prec], ctypes.byref(t)))
 
 

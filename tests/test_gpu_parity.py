@@ -397,9 +397,10 @@ def test_autotune_then_parity(pt, ctx):
     opw = pt.wilson(ctx, dims, _t(U), kappa, True)
     bw = pt.autotune(opw, _t(colw), mw, mu, "z4", 5, "mixed_fp32", 1e-10, 5000, 12)
     assert bw["group"] in (1, 2, 4, 8, 16)
-    pt.set_tuning(opw, "mixed_fp32", delta=1e-3, group=2, graph_iters=4)
+    assert bw["rhs_block"] in (1, 2) and bw["overlap"] in (0, 1)
+    pt.set_tuning(opw, "mixed_fp32", delta=1e-3, group=2, graph_iters=4, rhs_block=1, overlap=0)
     assert pt.get_tuning(opw, "mixed_fp32") == {"delta": 1e-3, "group": 2, "graph_iters": 4, "rhs_block": 1,
-                                                "seconds_per_rhs": 0.0}
+                                                "overlap": 0, "seconds_per_rhs": 0.0}
     est, _, _, _ = pt.trace(opw, _t(colw), mw, mu, [1], "z4", 5, 0, 1, True, "mixed_fp32", 1e-10, 5000)
     want = OE.probed_estimates(OE.Wilson(dims, U, kappa), colw, mw, 5, 1, 1, mu, [1], 1e-12)
     assert np.allclose(est, want, rtol=1e-8, atol=1e-7)
@@ -432,6 +433,38 @@ def test_wilson_two_rhs_items_parity(pt, ctx, prec, group):
     assert max(r1) <= 1e-10 and max(r2) <= 1e-10
     assert torch.allclose(X2, X1, rtol=1e-8, atol=1e-9 * X1.abs().max().item())
     pt.set_tuning(op, prec, reset=True)
+
+
+def test_overlapped_iterations_parity(pt, ctx):
+    """overlap = 1 (contraction and FP64 outer steps as graph branches beside
+    the inner kernels): traces still match the oracle, Laplacian and Wilson,
+    with several colourings so that the three groups are busy at once."""
+    import torch
+    dims, m2, mu = [8, 8, 8, 8], 0.05, 3
+    cols, ms = [], []
+    for p, k in [(0, 1), (1, 2), (2, 2)]:
+        c, m = greedy_colour(dims, mu, [p], k, 0)
+        cols.append(c)
+        ms.append(m)
+    op = pt.laplacian(ctx, dims, m2)
+    pt.set_tuning(op, "mixed_fp32", overlap=1, graph_iters=4)
+    est, st = pt.trace_multi(op, torch.as_tensor(np.stack(cols)).cuda().contiguous(), ms, mu, [0, 1, 2], "z2", 8,
+                             0, 2, True, "mixed_fp32", 1e-10, 5000)
+    lap = OE.Laplacian(dims, m2)
+    for i in range(3):
+        want = OE.probed_estimates(lap, cols[i], ms[i], 8, 2, 0, mu, [0, 1, 2], 1e-12)
+        assert np.allclose(est[i], want, rtol=1e-8, atol=1e-8)
+    pt.set_tuning(op, "mixed_fp32", reset=True)
+    dims, kappa, mu = [4, 4, 8, 4], 0.12, 2
+    U = inputs.gauge_links(dims, 31)
+    c0, m0 = greedy_colour(dims, mu, [1], 1, 1)
+    opw = pt.wilson(ctx, dims, _t(U), kappa, True)
+    for prec in ("mixed_fp32", "fp64"):
+        pt.set_tuning(opw, prec, overlap=1, graph_iters=4)
+        est, _, _, st = pt.trace(opw, _t(c0), m0, mu, [0, 1], "z4", 6, 0, 1, True, prec, 1e-10, 5000)
+        want = OE.probed_estimates(OE.Wilson(dims, U, kappa), c0, m0, 6, 1, 1, mu, [0, 1], 1e-12)
+        assert np.allclose(est, want, rtol=1e-8, atol=1e-7)
+        pt.set_tuning(opw, prec, reset=True)
 
 
 # ------------------------------------------------------------------ edge cases
