@@ -245,6 +245,9 @@ def run_ours(args):
     traffic = None
     if W.kind == "lap" and args.prec == "mixed_fp32" and APPLY_NCU_TRAFFIC_PER_SITE_RHS and apply_launches:
         traffic = APPLY_NCU_TRAFFIC_PER_SITE_RHS * inner_iters * N / apply_launches
+    if (W.kind == "wil" and args.prec == "mixed_fp32" and WIL_APPLY_NCU_TRAFFIC_PER_SITE_RHS and apply_launches
+            and tuning.get("rhs_block", 1) == 1):
+        traffic = WIL_APPLY_NCU_TRAFFIC_PER_SITE_RHS * inner_iters * 2 * N / apply_launches
     roofline = {"bound": "hbm",
                 "kernel": "k_cg_apply_v4<float> (p update + stencil + p.q)" if W.kind == "lap"
                 else "k_bicg_apply1/2<float,float> (Wilson apply + dots)",
@@ -366,6 +369,11 @@ def run_ours(args):
 # launch; profiles/k_cg_apply_v4_lap16_small.md).  Set to None whenever the
 # kernel changes until it is captured again.
 APPLY_NCU_TRAFFIC_PER_SITE_RHS = (124.8e6 + 83.0e6) / (238 * 65536)
+# The same for k_bicg_apply1/2<float, float> (one right-hand side per item): the
+# wilson24 small case (48 RHS on 16^3 x 32, all active), apply1 1503.0 + 582.0 MB,
+# apply2 899.4 + 571.6 MB per launch, averaged over the two
+# (profiles/k_bicg_apply_wilson24_small.md).
+WIL_APPLY_NCU_TRAFFIC_PER_SITE_RHS = ((1503.0e6 + 582.0e6) + (899.4e6 + 571.6e6)) / 2 / (48 * 131072)
 
 
 def run_grad(args):
