@@ -190,7 +190,7 @@ PT_API int pt_apply(pt_ctx *ctx, const pt_op *op, const double *x_dev, double *y
 
 /* ---------------------------------------------------------------- colouring */
 
-/* Host-side stencil of the displaced distance-k neighbourhood (Eq. (9), and
+/* Host-side stencil of the displaced distance-k neighbourhood (Eq. (8), and
  * the union over several displacements of Sec. 3.4):
  *   O = { o != 0 : ||o - p_n e_mu||_1 <= k  or  ||o + p_n e_mu||_1 <= k, some n }
  * sorted lexicographically in (o_0, o_1, o_2, o_3).  offsets_out (host) receives
@@ -295,7 +295,7 @@ PT_API int pt_clearance(pt_ctx *ctx, const int dims[4], int mu, const int32_t *c
 
 /* ------------------------------------------------------------------- probes */
 
-/* Materialise one probing vector (Eq. (3) with the noise of Eq. (5) and the
+/* Materialise one probing vector (Eq. (4) with the noise of Eq. (5) and the
  * spin-colour dilution of Sec. 4.2):
  *   v(x, b) = z0_set(x) [col(x) = colour] delta_{b, component}
  * z0 from SplitMix64: h = mix64(key + (x+1) G), key = mix64(seed + (set+1) G),
@@ -320,7 +320,7 @@ PT_API int pt_solve(pt_ctx *ctx, const pt_op *op, const double *B_dev, double *X
 /* ------------------------------------------------------------------ traces */
 
 /* Probed estimates of Tr(P_n A^{-1}) for every displacement p_list[n] along mu
- * (Eqs. (1), (3), (5), spin-colour dilution of Sec. 4.2):
+ * (Eqs. (1), (4), (5), spin-colour dilution of Sec. 4.2):
  *   est[s][n] = sum_{c < n_colours} sum_{a} v_{s,c,a}^H P_{p_n} A^{-1} v_{s,c,a}
  * for noise sets s = set0 .. set0 + n_sets - 1, a over all dof components when
  * dilute != 0, else a = 0 only.  col_dev: int32 [N] colours in [0, n_colours)
@@ -355,7 +355,7 @@ PT_API int pt_trace_PAinv_multi(pt_ctx *ctx, const pt_op *op, int n_col, const i
  * .. n_lev - 1 (finest), must be nested: nodes with the same level-(l+1)
  * colour share their level-l colour (PT_ERR_ARG otherwise).  Only the probes
  * of the finest classes are solved; since the probes of the finer classes
- * inside a level-l class sum to its probe (Eq. (3), shared noise), the
+ * inside a level-l class sum to its probe (Eq. (4), shared noise), the
  * level-l solution of that class is the sum of theirs, and each finest solve
  * is contracted with its ancestor's probe at every level:
  *   est_out[l][s][n] (host complex128 [n_lev][n_sets][n_p])

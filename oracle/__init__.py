@@ -16,14 +16,14 @@ definition states.
 Modules
 -------
 lattice      coordinates, storage index, displacement permutation P (Sec. 3)
-stencil      displaced neighbourhood N(x,p,k), Eq. (9), multi-p union (Sec. 3.4)
+stencil      displaced neighbourhood N(x,p,k), Eq. (8), multi-p union (Sec. 3.4)
 colouring    greedy displaced distance-k colouring, Algorithm 1 (Sec. 3.1)
-bounds       lower bounds on the colour count, Eq. (4), Thms 3.2-3.5, Eq. (13)
+bounds       lower bounds on the colour count, Eq. (9), Thms 3.2-3.5, Eq. (13)
 rng          SplitMix64 counter-based Z2 / Z4 noise (Sec. 1, Rademacher vectors)
-probes       probing vectors, Eq. (3), unbiased form Eq. (5), spin-colour dilution
+probes       probing vectors, Eq. (4), unbiased form Eq. (5), spin-colour dilution
 operators    shifted 4D Laplacian and Wilson-Dirac operators
 solvers      textbook CG and BiCGStab in FP64, dense solve for tiny lattices
-estimator    Hutchinson / probed trace estimate, statistics, Eqs. (1), (6)-(8)
+estimator    Hutchinson / probed trace estimate, statistics, Eqs. (1), (15)-(17)
 variance     exact estimator variance, Eq. (2) generalised to non-symmetric B
 gradient     adjoint gradient of the probed estimate (extension, not in the paper)
 

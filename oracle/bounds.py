@@ -3,7 +3,7 @@
 Sec. 3.2.  All bounds are for the infinite lattice Z^d_inf with the
 displacement p along one dimension (taken as the first in the paper).
 
-* p = 0, Eq. (4): an L1 ball of radius floor(k/2), plus a (d-1)-dimensional
+* p = 0, Eq. (9): an L1 ball of radius floor(k/2), plus a (d-1)-dimensional
   ball of the same radius when k is odd.
 * Thm 3.2: p = k  ->  2k + 1.
 * Thm 3.3: p > k  ->  ceil(2p / (p - k)).
@@ -44,7 +44,7 @@ def clique_size(d, a, b):
 
 
 def lower_bound_p0(d, k):
-    """Eq. (4)."""
+    """Eq. (9)."""
     h = k // 2
     if k % 2 == 0:
         return ball_size(d, h)

@@ -1,7 +1,7 @@
 """Greedy displaced distance-k colouring (Algorithm 1, Sec. 3.1) and checks.
 
 The sequential greedy loop itself is the plain C routine in greedy_colour.c;
-this module prepares its inputs (stencil, Eq. (9); visit order, Sec. 3.1) and
+this module prepares its inputs (stencil, Eq. (8); visit order, Sec. 3.1) and
 provides the validity check used by the tests.
 """
 import ctypes

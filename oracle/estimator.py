@@ -2,14 +2,14 @@
 
 Eq. (1): Hutchinson, Tr(M) ~ (1/s) sum_i z_i^T M z_i.  For complex probes the
 transpose is read as the conjugate transpose (z^H M z).
-Eqs. (3), (5): with a colouring of m colours and s noise vectors z0^(s), one
+Eqs. (4), (5): with a colouring of m colours and s noise vectors z0^(s), one
 estimate per noise vector is
     T_s = sum_{c < m} sum_{a < dof} v_{s,c,a}^H  P  A^{-1}  v_{s,c,a},
 i.e. one Hutchinson step on (P A^{-1}) (.) H H^T (Sec. 2.2).  The unprobed
 Hutchinson estimator is the case m = 1 (every site colour 0).
 Sec. 4.2: estimates are averaged over s; v(.) is the per-vector variance,
-estimated by the sample variance; speedup over Hutchinson Eq. (6), over
-classical probing Eq. (7), normalised relative error Eq. (8).
+estimated by the sample variance; speedup over Hutchinson Eq. (15), over
+classical probing Eq. (16), normalised relative error Eq. (17).
 """
 import numpy as np
 
@@ -115,17 +115,17 @@ def sigma_mean(est):
 
 
 def speedup_over_hutchinson(var_h, var_p, m):
-    """Eq. (6): v(P A^{-1}) / (m v((P A^{-1}) (.) H H^T))."""
+    """Eq. (15): v(P A^{-1}) / (m v((P A^{-1}) (.) H H^T))."""
     return var_h / (m * var_p)
 
 
 def speedup_over_cp(var_cp, m0, var_p, mp):
-    """Eq. (7): v((P_p A^{-1}) (.) H_0 H_0^T) m_0 / (v((P_p A^{-1}) (.) H_p H_p^T) m_p)."""
+    """Eq. (16): v((P_p A^{-1}) (.) H_0 H_0^T) m_0 / (v((P_p A^{-1}) (.) H_p H_p^T) m_p)."""
     return (var_cp * m0) / (var_p * mp)
 
 
 def normalised_relative_error(var, m_p, M, trace):
-    """Eq. (8): sqrt(v m_p / M) / tr."""
+    """Eq. (17): sqrt(v m_p / M) / tr."""
     return np.sqrt(var * m_p / M) / trace
 
 

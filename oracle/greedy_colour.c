@@ -3,7 +3,7 @@
  *
  * Algorithm 1 (Sec. 3.1): visit the lattice nodes in a given order; each node
  * receives the smallest colour not already held by a node of its displaced
- * neighbourhood N(x,p,k) (given as a stencil of coordinate offsets, Eq. (9),
+ * neighbourhood N(x,p,k) (given as a stencil of coordinate offsets, Eq. (8),
  * Algorithm 2).  Nodes not yet visited hold no colour.  Colours are 0-based
  * here (the paper counts from 1).  A used-colour table of |stencil|+1 entries
  * suffices because a node has at most |stencil| neighbours (Sec. 3.1).

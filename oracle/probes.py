@@ -1,6 +1,6 @@
 """Probing vectors.
 
-Eq. (3), Sec. 2.1: z_j(i) = 1 if colour(i) = j, else 0.
+Eq. (4), Sec. 2.1: z_j(i) = 1 if colour(i) = j, else 0.
 Eq. (5), Sec. 2.2: the unbiased probes are z_0 (.) z_j with z_0 a Rademacher
 vector; s independent z_0 give s Hutchinson steps on A^{-1} (.) H H^T.
 Sec. 4.2: spin-colour dilution is the Kronecker product with the 12 x 12
@@ -36,7 +36,7 @@ def probe(col, colour, seed, s, kind, dof=1, component=0):
 
 
 def probing_indicator(col, m):
-    """H: the N x m matrix whose columns are the vectors of Eq. (3)."""
+    """H: the N x m matrix whose columns are the vectors of Eq. (4)."""
     col = np.asarray(col)
     H = np.zeros((col.shape[0], m))
     H[np.arange(col.shape[0]), col] = 1.0

@@ -1,7 +1,7 @@
 """Displaced distance-k neighbourhood as a stencil of coordinate offsets.
 
-Eq. (9), Sec. 3: N(x,p,k) = {y : ||y - x^+||_1 <= k} U {y : ||y - x^-||_1 <= k}
-with x^{+-} = x +- p (Eq. (8)); x itself is excluded during colouring.
+Eq. (8), Sec. 3: N(x,p,k) = {y : ||y - x^+||_1 <= k} U {y : ||y - x^-||_1 <= k}
+with x^{+-} = x +- p (Eq. (7)); x itself is excluded during colouring.
 Sec. 3.1: the neighbourhood is stored once as a list of offsets ("stencil")
 that are added to the coordinates of any node (Algorithm 2 builds it; its body
 is not in the text, so this follows the set definition directly).

@@ -1,4 +1,4 @@
-// Displaced distance-k colouring: stencil (Eq. (9), Algorithm 2), the greedy
+// Displaced distance-k colouring: stencil (Eq. (8), Algorithm 2), the greedy
 // walk of Algorithm 1 and a validity count.
 //
 // The greedy walk is sequential by definition (Sec. 4: the visit of each node
@@ -255,7 +255,7 @@ static int prep(pt_ctx *c, const int dims[4], int mu, const int *p_list, int n_p
 // the colours of the two nodes before it (one not yet found, one being
 // written), so the search of node t skips those two colours itself when the
 // nodes are neighbours of t: the L1 distance to the nearer displaced image
-// (Eq. (9)), tested one node ahead by two threads and kept in shared memory.
+// (Eq. (8)), tested one node ahead by two threads and kept in shared memory.
 // Each thread holds its U offsets' deltas in registers for the whole walk
 // and issues all its loads of a gather before using any of them; both stamp
 // buffers live in shared memory, the colours come through L1.

@@ -60,7 +60,7 @@ __global__ void k_conflicts_noalloc(Geom g, int n_off, const int32_t *__restrict
     if (threadIdx.x == 0 && v[0] > 0.0) atomicAdd(&s->count, (unsigned long long)v[0]);
 }
 
-// Stencil of Eq. (9) written into the static staging table (sorted, unique).
+// Stencil of Eq. (8) written into the static staging table (sorted, unique).
 // Returns the number of offsets, or -1 if it exceeds PT_NOALLOC_MAX_OFFSETS.
 static int noalloc_stencil(int mu, const int *p_list, int n_p, int k) {
     int n = 0;

@@ -1,5 +1,5 @@
 """C-ABI library: it builds, loads without a GPU, exports every symbol that
-include/ptrace.h declares, and its host-side stencil (Eq. (9)) matches the
+include/ptrace.h declares, and its host-side stencil (Eq. (8)) matches the
 oracle.  No compute call is made (there may be no GPU)."""
 import os
 import re

@@ -70,7 +70,7 @@ def test_conflict_count_detects_invalid_colouring(pt, ctx):
     assert n == o_conflicts(col, dims, 2, [1], 1) and n > 0
 
 
-# ------------------------------------------------------------------ probes (Eqs. (3), (5))
+# ------------------------------------------------------------------ probes (Eqs. (4), (5))
 @pytest.mark.parametrize("noise,dof,comp", [("z2", 1, 0), ("z4", 12, 5), ("z2", 12, 0), ("z4", 12, -1)])
 def test_probes_bit_exact(pt, ctx, noise, dof, comp):
     dims = [6, 5, 7, 4]

@@ -1,4 +1,4 @@
-"""Pins for the lower bounds of Sec. 3.2 (Eq. (4), Thms 3.2-3.5, Table 1, Eq. (13), Table 4)."""
+"""Pins for the lower bounds of Sec. 3.2 (Eq. (9), Thms 3.2-3.5, Table 1, Eq. (13), Table 4)."""
 import itertools
 from fractions import Fraction as F
 
@@ -50,7 +50,7 @@ def test_theorems_3_2_3_3():
 
 
 def _in_N(x, y, p, k):
-    """x in N(y, p, k) on the infinite lattice (Eq. (9)), displacement along dim 0."""
+    """x in N(y, p, k) on the infinite lattice (Eq. (8)), displacement along dim 0."""
     up = sum(abs(x[i] - y[i] - (p if i == 0 else 0)) for i in range(len(x)))
     dn = sum(abs(x[i] - y[i] + (p if i == 0 else 0)) for i in range(len(x)))
     return up <= k or dn <= k

@@ -60,7 +60,7 @@ def test_shell_sizes_of_p0_are_l1_spheres():
 
 def test_shells_partition_the_union_of_balls():
     """The shells k = 1..K around the pair are disjoint and together make the
-    displaced neighbourhood N(x, p, K) minus x (Eq. (9))."""
+    displaced neighbourhood N(x, p, K) minus x (Eq. (8))."""
     from oracle.stencil import displaced_stencil
     dims = [20, 20, 20, 20]
     for p, K in [(0, 3), (2, 2), (3, 4)]:

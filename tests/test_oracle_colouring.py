@@ -238,7 +238,7 @@ def test_nested_with_one_parent_is_algorithm_1(order):
 
 def test_nested_probes_sum_to_parent_probe():
     """The point of nesting: the probes of the child classes of a parent class
-    sum to the parent's probe (Eq. (3) with shared noise), so solves at the
+    sum to the parent's probe (Eq. (4) with shared noise), so solves at the
     finer level give the coarser estimate by linearity."""
     from oracle.colouring import nested_colour
     from oracle.probes import probe

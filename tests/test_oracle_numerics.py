@@ -40,7 +40,7 @@ def test_noise_distribution():
 
 
 def test_probe_partition_of_unity():
-    """Sum over colours of the probes of one set is z0 (x) e_a (Eqs. (3), (5))."""
+    """Sum over colours of the probes of one set is z0 (x) e_a (Eqs. (4), (5))."""
     dims = [4, 4, 4, 4]
     col, m = greedy_colour(dims, 0, [1], 2, 0)
     for kind, dof, a in ((0, 1, 0), (1, 12, 5)):
@@ -218,7 +218,7 @@ def test_cg_and_bicgstab_match_dense():
 
 # ---------------------------------------------------------------- estimator and variance
 def test_all_distinct_colours_give_exact_trace():
-    """With every site its own colour the probed estimate is exact (Eq. (3))."""
+    """With every site its own colour the probed estimate is exact (Eq. (4))."""
     dims, m2 = [4, 4, 4, 4], 0.1
     lap = E.Laplacian(dims, m2)
     col = np.arange(256, dtype=np.int32)
@@ -325,7 +325,7 @@ def test_z4_variance_formula():
 
 
 def test_table6_speedup_arithmetic():
-    """Eq. (6) reproduces the printed speedups of Table 6 from its printed variances."""
+    """Eq. (15) reproduces the printed speedups of Table 6 from its printed variances."""
     for r in read_golden("table6_speedup.txt"):
         p, k = int(r[0]), int(r[1])
         s = E.speedup_over_hutchinson(float(r[3]), float(r[5]), int(r[4]))
