@@ -276,7 +276,22 @@ def run_ours(args):
            "gpu_launches": int(launches), "roofline": roofline, "clocks": clocks,
            "mean_inner_iters_per_rhs": stats[-1]["inner_iters"] / stats[-1]["n_rhs"],
            "mean_outer_iters_per_rhs": stats[-1]["outer_iters"] / stats[-1]["n_rhs"],
-           "solves_per_s": stats[-1]["n_rhs"] / step_s}
+           "solves_per_s": stats[-1]["n_rhs"] / step_s,
+           "max_true_relres": stats[-1]["max_relres"]}
+    if est is not None and W.n_sets > 1:
+        # Eq. (17): sqrt(v m / M) / |Tr(P_n A^-1)| for every colouring and displacement, v the sample
+        # variance of the colouring's estimator over the step's noise sets, M the largest colour count,
+        # the trace taken as the mean over every colouring and set
+        e = np.asarray(est)                                            # [n_col, n_sets, n_p]
+        var = (np.abs(e - e.mean(axis=1, keepdims=True)) ** 2).sum(axis=1) / (e.shape[1] - 1)
+        tr = np.abs(e.mean(axis=(0, 1)))
+        M = max(m)
+        nre = np.sqrt(var * np.asarray(m, dtype=float)[:, None] / M) / np.maximum(tr[None, :], 1e-300)
+        best = {("p=%d" % W.p_contract[n]): "(%d,%d)" % tuple(W.pk[int(np.argmin(nre[:, n]))])
+                for n in range(len(W.p_contract))}
+        out["normalised_relative_error"] = {
+            "rows": ["(%d,%d)" % tuple(pk) for pk in W.pk], "cols": ["p=%d" % q for q in W.p_contract],
+            "values": np.round(nre, 8).tolist(), "best_colouring_per_displacement": best}
 
     if W.kind == "lap" and rank == 0:
         # the hierarchical reading of "k = 1..4 grown at runtime": colourings nested level by level
