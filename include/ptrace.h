@@ -139,7 +139,7 @@ typedef struct pt_tune {
 /* Autotuner: solves the same trial right-hand sides (up to trial_rhs probes
  * of one noise set spread over the colours of col_dev) with candidate
  * parameters, by coordinate descent over delta (mixed precision), rhs_block
- * and group (Wilson) and graph_iters, keeps the fastest, and stores it in the context
+ * and group (Wilson) and graph_iters (overlap stays as set), keeps the fastest, and stores it in the context
  * for this operator's (kind, precision, lattice); later solves, traces and
  * gradients with that key use it.  *best (host) receives it.  Synchronises. */
 PT_API int pt_autotune(pt_ctx *ctx, const pt_op *op, const int32_t *col_dev, int n_colours, int mu, int noise,
