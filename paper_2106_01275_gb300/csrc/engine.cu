@@ -55,7 +55,6 @@ struct TaskStat {
 struct EP {
     Geom g;
     int kind, nsb, R, gs, vec4;
-    int shfl, qpr;             // Laplacian four-site apply: x and y neighbours by warp shuffles, qpr quads per row
     int rhs_block;             // Wilson applies: right-hand sides per item (1 or 2)
     int overlap;               // groups run as graph branches: the inner list holds PH_INNER slots only
     // nested trace mode (n_lev > 0): the tasks are the classes of the finest of
@@ -761,37 +760,12 @@ __global__ void __launch_bounds__(PT_BLOCK) k_cg_apply_v4(EP P) {
             };
             R pc[4], t[4];
             pquad(idx, pc);
-            R left, right, up[4], dn[4];
-            if (P.shfl) {
-                // a warp holds whole rows of qpr quads: the x neighbours are edge values of the
-                // adjacent quads of the row (periodic within it), the y neighbours the quads qpr
-                // lanes away unless the row is at the warp's edge or y wraps
-                const int lane = threadIdx.x & 31, qpr = P.qpr;
-                const int g0 = lane & ~(qpr - 1), lq = lane - g0;
-                left = __shfl_sync(0xffffffffu, pc[3], g0 + ((lq + qpr - 1) & (qpr - 1)));
-                right = __shfl_sync(0xffffffffu, pc[0], g0 + ((lq + 1) & (qpr - 1)));
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    up[c] = __shfl_down_sync(0xffffffffu, pc[c], qpr);
-                    dn[c] = __shfl_up_sync(0xffffffffu, pc[c], qpr);
-                }
-                const int lrow = lane / qpr, rows = 32 / qpr;
-                if (!(lrow + 1 < rows && xc[1] + 1 < P.g.D[1])) pquad(nb_fwd(P.g, idx, xc, 1), up);
-                if (!(lrow > 0 && xc[1] > 0)) pquad(nb_bwd(P.g, idx, xc, 1), dn);
-            } else {
-                left = pone(xc[0] == 0 ? idx + D0 - 1 : idx - 1);
-                right = pone(xc[0] + 4 == D0 ? idx + 4 - D0 : idx + 4);
-                pquad(nb_fwd(P.g, idx, xc, 1), up);
-                pquad(nb_bwd(P.g, idx, xc, 1), dn);
-            }
+            const R left = pone(xc[0] == 0 ? idx + D0 - 1 : idx - 1);
+            const R right = pone(xc[0] + 4 == D0 ? idx + 4 - D0 : idx + 4);
             // neighbours summed in the order of the one-site kernel: x+, x-, y+, y-, z+, z-, t+, t-
             R acc[4] = {pc[1] + left, pc[2] + pc[0], pc[3] + pc[1], right + pc[2]};
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[c] += up[c];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[c] += dn[c];
-#pragma unroll
-            for (int mu = 2; mu < 4; ++mu) {
+            for (int mu = 1; mu < 4; ++mu) {
                 pquad(nb_fwd(P.g, idx, xc, mu), t);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[c] += t[c];
@@ -1397,9 +1371,6 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     P.rhs_block = (KIND == 1 && !std::is_same<S, double>::value && tn.rhs_block == 2) ? 2 : 1;
     P.overlap = tn.overlap ? 1 : 0;
     P.vec4 = (KIND == 0 && g.D[0] % 4 == 0) ? 1 : 0;
-    // shuffles need whole rows per warp (D0 / 4 divides 32) and whole warps of sites (N % 128 == 0)
-    P.qpr = g.D[0] / 4;
-    P.shfl = (P.vec4 && P.qpr >= 1 && 32 % P.qpr == 0 && g.N % 128 == 0) ? 1 : 0;
     P.L = L;
     P.diag = 8.0 + op->m2;
     P.kappa = op->kappa;

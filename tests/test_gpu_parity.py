@@ -469,10 +469,9 @@ def test_overlapped_iterations_parity(pt, ctx):
 
 @pytest.mark.parametrize("dims", [[4, 3, 8, 4], [8, 3, 5, 3], [32, 2, 2, 4], [8, 5, 4, 4], [128, 1, 2, 1]])
 def test_laplacian_four_site_paths(pt, ctx, dims):
-    """The four-site Laplacian kernels with the x and y neighbours from warp
-    shuffles (whole rows per warp; rows whose y neighbour wraps or leaves the
-    warp load it) and without them (N not a multiple of 128): traces in FP64
-    and mixed precision against the oracle."""
+    """The four-site Laplacian kernels (D_0 a multiple of 4) on short rows,
+    long rows, sides of 1 to 3 and volumes that are not a multiple of the
+    block: traces in FP64, FP32 and BF16 storage against the oracle."""
     mu = 2
     col, m = greedy_colour(dims, mu, [1], 1, 0)
     op = pt.laplacian(ctx, dims, 0.3)
