@@ -17,7 +17,7 @@ Modules
 -------
 lattice      coordinates, storage index, displacement permutation P (Sec. 3)
 stencil      displaced neighbourhood N(x,p,k), Eq. (8), multi-p union (Sec. 3.4)
-colouring    greedy displaced distance-k colouring, Algorithm 1 (Sec. 3.1)
+colouring    greedy displaced distance-k colouring, Algorithm 1 (Sec. 3.1), nested variant
 bounds       lower bounds on the colour count, Eq. (9), Thms 3.2-3.5, Eq. (13)
 rng          SplitMix64 counter-based Z2 / Z4 noise (Sec. 1, Rademacher vectors)
 probes       probing vectors, Eq. (4), unbiased form Eq. (5), spin-colour dilution
@@ -26,6 +26,9 @@ solvers      textbook CG and BiCGStab in FP64, dense solve for tiny lattices
 estimator    Hutchinson / probed trace estimate, statistics, Eqs. (1), (15)-(17)
 variance     exact estimator variance, Eq. (2) generalised to non-symmetric B
 gradient     adjoint gradient of the probed estimate (extension, not in the paper)
+tiles        tile policy of Sec. 3.5 (Table 2)
+clearance    clearance of a colouring at other displacements (Thm 3.6, Table 5)
+deflation    deflation of the lowest singular triplets, Eq. (6) (Sec. 2.4)
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against a
 value printed in the paper, a closed form, brute force or an invariant, except
