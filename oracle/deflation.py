@@ -99,3 +99,47 @@ def deflated_probed_estimates(op, col, m, seed, n_sets, kind, mu, p_list, tol, U
                         corr = (vf.conj() @ PV) @ (M @ uv)
                     est[s, n] += np.vdot(v, displace(x, dims, mu, p)) - corr
     return est
+
+
+def lanczos_lowest(apply_h, n, n_ev, n_iter, seed=0, dtype=np.float64, block=8):
+    """Lowest n_ev eigenpairs of a Hermitian operator given by its action:
+    block Lanczos (a random block of `block` vectors, every new block
+    orthogonalised twice against the whole basis, n_iter blocks at most),
+    then Rayleigh-Ritz on the basis.  A block as large as the multiplicity of
+    the wanted eigenvalues resolves degenerate ones (a single start vector
+    sees one vector per distinct eigenvalue).  Returns (values ascending,
+    vectors as columns).  A matrix-free route to the triplets for lattices
+    where a dense decomposition is out of reach."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, block))
+    if dtype == np.complex128:
+        X = X + 1j * rng.standard_normal((n, block))
+    Q, _ = np.linalg.qr(X)
+    basis = [Q]
+    for _ in range(n_iter - 1):
+        W = np.stack([np.asarray(apply_h(Q[:, i])).reshape(-1) for i in range(Q.shape[1])], axis=1)
+        B = np.concatenate(basis, axis=1)
+        for _ in range(2):
+            W = W - B @ (B.conj().T @ W)
+        Q, R = np.linalg.qr(W)
+        keep = np.abs(np.diag(R)) > 1e-10 * max(1.0, np.abs(np.diag(R)).max(initial=0.0))
+        Q = Q[:, keep]
+        if Q.shape[1] == 0 or sum(b.shape[1] for b in basis) >= n:
+            break
+        basis.append(Q)
+    B = np.concatenate(basis, axis=1)
+    AB = np.stack([np.asarray(apply_h(B[:, i])).reshape(-1) for i in range(B.shape[1])], axis=1)
+    T = B.conj().T @ AB
+    th, S = np.linalg.eigh(0.5 * (T + T.conj().T))
+    return th[:n_ev], B @ S[:, :n_ev]
+
+
+def wilson_triplets_from_gamma5(apply_a, gamma5, n, n_ev, n_iter, seed=0):
+    """Singular triplets of a gamma5-Hermitian operator (A^H = g5 A g5): the
+    right singular vectors are eigenvectors of A^H A = (g5 A)^2, the lowest
+    from Lanczos; sigma = ||A v|| and u = A v / sigma.  Returns (U, s, V)."""
+    apply_aha = lambda x: gamma5(apply_a(gamma5(apply_a(x))))
+    th, V = lanczos_lowest(apply_aha, n, n_ev, n_iter, seed, np.complex128)
+    AV = np.stack([np.asarray(apply_a(V[:, i])).reshape(-1) for i in range(V.shape[1])], axis=1)
+    s = np.linalg.norm(AV, axis=0)
+    return AV / s[None, :], s, V

@@ -116,3 +116,35 @@ def test_wilson_triplets_and_split():
         P = D.displacement_matrix(dims, mu, p, dof=12)
         part = D.deflated_part(U, V, M, dims, mu, [p], dof=12)[0]
         assert np.isclose(part + np.trace(P @ Ainv @ (np.eye(A.shape[0]) - Q)), np.trace(P @ Ainv), rtol=1e-10)
+
+
+def test_lanczos_matches_the_dense_spectrum_of_the_laplacian():
+    """Matrix-free Lanczos (full reorthogonalisation) finds the same lowest
+    eigenvalues as the dense decomposition, and its vectors are eigenvectors."""
+    dims, m2 = [6, 6, 6, 6], 0.05
+    op = _lap(dims, m2)
+    n = int(np.prod(dims))
+    A = D.dense_matrix(op)
+    want = np.linalg.eigvalsh(A)[:6]
+    th, V = D.lanczos_lowest(lambda x: op.apply(x), n, 6, 15, block=12)     # 180 of 1296 dimensions
+    assert np.allclose(th, want, rtol=1e-7, atol=1e-9)
+    assert np.allclose(A @ V, V * th[None, :], atol=1e-5)
+
+
+def test_gamma5_triplets_match_the_dense_svd_of_wilson():
+    """gamma5-hermiticity: the lowest singular values of the Wilson operator
+    from Lanczos on A^H A = (g5 A)^2 equal those of the dense SVD, and the
+    triplets satisfy A V = U diag(s)."""
+    from oracle import operators as OO
+    from paper_2106_01275_gb300 import inputs
+    dims, kappa = [2, 2, 2, 2], 0.12
+    Uf = inputs.gauge_links(dims, 7)
+    op = OE.Wilson(dims, Uf, kappa)
+    N = int(np.prod(dims))
+    A = D.dense_matrix(op)
+    g5 = lambda x: OO.gamma5_apply(np.asarray(x).reshape(N, 4, 3)).reshape(-1)
+    ap = lambda x: np.asarray(op.apply(np.asarray(x).reshape(N, 12))).reshape(-1)
+    U, s, V = D.wilson_triplets_from_gamma5(ap, g5, 12 * N, 4, 24)     # the whole space: tests the construction
+    _, s_ref, _ = D.lowest_singular_triplets(A, 4)
+    assert np.allclose(s, s_ref, rtol=1e-8)
+    assert np.allclose(A @ V, U * s[None, :], atol=1e-8)
