@@ -364,6 +364,29 @@ PT_API int pt_trace_PAinv_multi(pt_ctx *ctx, const pt_op *op, int n_col, const i
  * level's solves.  n_lev * n_p <= 32.  A temporary stream-ordered
  * allocation holds the ancestor table.  Other arguments as pt_trace_PAinv.
  * Synchronises. */
+/* Deflation of given triplets (Sec. 2.4, Eq. (6)) for the displaced trace.
+ * With U, V (n_ev columns each) and M = (U^H A V)^{-1} (the caller's small
+ * matrix; for singular triplets, diag(1 / sigma)):
+ *   Tr(P A^{-1}) = Tr(M U^H P V) + Tr(P A^{-1} (I - Q)),  Q = A V M U^H,
+ * and a probe v contributes v^H P A^{-1} v - (v^H P V) M (U^H v) to the
+ * second part.  This call computes the pieces that need no solve, for the
+ * diluted probes of pt_trace_PAinv (same col_dev, colours, noise, seed and
+ * sets; every component diluted):
+ *   exact_out[n] = Tr(M U^H P_{p_n} V)                   (host complex128 [n_p])
+ *   corr_out[s][n] = sum_{c,a} (v^H P_{p_n} V) M (U^H v)  (host complex128 [n_sets][n_p]),
+ * so that est[s][n] - corr_out[s][n] (est from pt_trace_PAinv or
+ * pt_trace_PAinv_multi) estimates the second part and exact_out + the mean
+ * of that the whole trace.  U_dev, V_dev: complex128 [n_ev][N][dof] (device,
+ * read; dof = 1 or 12, site-major as the user layout); M_host: complex128
+ * [n_ev][n_ev] row-major (host).  1 <= n_p <= 16, 1 <= n_ev <= 4096.  The
+ * per-probe and Gram dot products run on the device (temporary stream-ordered
+ * allocations); the n_ev x n_ev contractions with M on the host.
+ * Synchronises. */
+PT_API int pt_deflation_terms(pt_ctx *ctx, const pt_op *op, const int32_t *col_dev, int n_colours, int mu,
+                              const int *p_list, int n_p, int noise, uint64_t seed, int set0, int n_sets,
+                              int n_ev, const double *U_dev, const double *V_dev, const double *M_host,
+                              double *corr_out, double *exact_out);
+
 PT_API int pt_trace_PAinv_nested(pt_ctx *ctx, const pt_op *op, int n_lev, const int32_t *cols_dev,
                                  const int *n_colours, int mu, const int *p_list, int n_p, int noise,
                                  uint64_t seed, int set0, int n_sets, int dilute, int prec, double tol,

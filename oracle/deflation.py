@@ -143,3 +143,23 @@ def wilson_triplets_from_gamma5(apply_a, gamma5, n, n_ev, n_iter, seed=0):
     AV = np.stack([np.asarray(apply_a(V[:, i])).reshape(-1) for i in range(V.shape[1])], axis=1)
     s = np.linalg.norm(AV, axis=0)
     return AV / s[None, :], s, V
+
+
+def deflation_corrections(col, m, seed, n_sets, kind, dims, mu, p_list, U, V, M, dof=1, set0=0):
+    """corr[s, n] = sum_{c, a} (v^H P_n V) M (U^H v) over the diluted probes
+    v = v_{s,c,a}: the part of the deflated estimate that needs no solve."""
+    N = int(np.prod(dims))
+    corr = np.zeros((n_sets, len(p_list)), dtype=np.complex128)
+    for s in range(n_sets):
+        for c in range(m):
+            for a in range(dof):
+                v = probe(col, c, seed, set0 + s, kind, dof, a)
+                if not np.any(v):
+                    continue
+                vf = np.asarray(v).reshape(-1)
+                uv = U.conj().T @ vf
+                for n, p in enumerate(p_list):
+                    PV = np.stack([displace(V[:, i].reshape(N, dof) if dof > 1 else V[:, i], dims, mu, p)
+                                   .reshape(-1) for i in range(V.shape[1])], axis=1)
+                    corr[s, n] += (vf.conj() @ PV) @ (M @ uv)
+    return corr

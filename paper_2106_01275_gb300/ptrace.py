@@ -95,6 +95,8 @@ _SIGS = {
                               _I, _I, _I, _I, _D, _I, _P, ctypes.POINTER(Stats)], _I),
     "pt_trace_PAinv_nested": ([_P, _P, _I, _P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _I, _I, ctypes.c_uint64,
                                _I, _I, _I, _I, _D, _I, _P, ctypes.POINTER(Stats)], _I),
+    "pt_deflation_terms": ([_P, _P, _P, _I, _I, ctypes.POINTER(_I), _I, _I, ctypes.c_uint64, _I, _I, _I, _P, _P, _P,
+                            _P, _P], _I),
     "pt_grad": ([_P, _P, _P, _I, _I, _I, _I, ctypes.c_uint64, _I, _I, _I, _I, _D, _I, _P, _P, _P, _P,
                  ctypes.POINTER(Stats)], _I),
 }
@@ -474,6 +476,23 @@ def trace_nested(op, cols, n_colours, mu, p_list, noise="z2", seed=0, set0=0, n_
                                      int(maxit), _np_ptr(est), ctypes.byref(st))
     _check(rc)
     return est, st.as_dict()
+
+
+def deflation_terms(op, col, n_colours, mu, p_list, noise, seed, set0, n_sets, U, V, M):
+    """pt_deflation_terms: (corr[n_sets, n_p], exact[n_p]) complex; U, V:
+    torch complex128 [n_ev, N, dof] on the device, M: numpy [n_ev, n_ev]."""
+    import torch
+    n_p = len(p_list)
+    U = torch.view_as_real(U.contiguous()).contiguous()
+    V = torch.view_as_real(V.contiguous()).contiguous()
+    Mh = np.ascontiguousarray(np.asarray(M, dtype=np.complex128))
+    corr = np.zeros((n_sets, n_p), dtype=np.complex128)
+    exact = np.zeros(n_p, dtype=np.complex128)
+    _check(lib().pt_deflation_terms(op.ctx.handle, op._h, _ptr(col), int(n_colours), int(mu), _ints(p_list), n_p,
+                                    NOISE[noise] if isinstance(noise, str) else int(noise), int(seed), int(set0),
+                                    int(n_sets), int(Mh.shape[0]), _ptr(U), _ptr(V), _np_ptr(Mh), _np_ptr(corr),
+                                    _np_ptr(exact)))
+    return corr, exact
 
 
 def grad(op, col, n_colours, mu, p, noise="z2", seed=0, set0=0, n_sets=1, dilute=True, prec="mixed_fp32",

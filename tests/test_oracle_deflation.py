@@ -148,3 +148,17 @@ def test_gamma5_triplets_match_the_dense_svd_of_wilson():
     _, s_ref, _ = D.lowest_singular_triplets(A, 4)
     assert np.allclose(s, s_ref, rtol=1e-8)
     assert np.allclose(A @ V, U * s[None, :], atol=1e-8)
+
+
+def test_corrections_equal_the_plain_estimate_under_full_deflation():
+    """With every triplet deflated the corrected contraction of each probe is
+    zero, so the corrections equal the plain probed estimates."""
+    dims, mu, m2 = [4, 2, 2, 2], 0, 0.3
+    op = _lap(dims, m2)
+    A = D.dense_matrix(op)
+    U, s, V = D.lowest_singular_triplets(A, A.shape[0])
+    M = D.small_matrix(A @ V, U)
+    col, m = greedy_colour(dims, mu, [1], 1, 0)
+    corr = D.deflation_corrections(col, m, 5, 2, 0, dims, mu, [0, 1], U, V, M)
+    plain = OE.probed_estimates(op, col, m, 5, 2, 0, mu, [0, 1], 1e-13)
+    assert np.allclose(corr, plain, rtol=1e-9, atol=1e-10)
