@@ -56,7 +56,7 @@ extern "C" {
 #define PT_ERR_NUMERIC  (-5)  /* NaN/Inf or a Krylov breakdown (zero denominator)  */
 #define PT_ERR_OOM      (-6)  /* device allocation of the work space failed        */
 
-/* ---- precision modes of the solver (BASELINE precision form) ---- */
+/* ---- precision modes of the solver ---- */
 #define PT_PREC_FP64        0 /* all vectors and arithmetic FP64                     */
 #define PT_PREC_MIXED_FP32  1 /* FP32 inner Krylov inside FP64 defect correction      */
 #define PT_PREC_MIXED_BF16  2 /* as MIXED_FP32, inner vectors stored in BF16          */
