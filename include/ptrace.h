@@ -364,6 +364,11 @@ PT_API int pt_trace_PAinv_multi(pt_ctx *ctx, const pt_op *op, int n_col, const i
  * level's solves.  n_lev * n_p <= 32.  A temporary stream-ordered
  * allocation holds the ancestor table.  Other arguments as pt_trace_PAinv.
  * Synchronises. */
+PT_API int pt_trace_PAinv_nested(pt_ctx *ctx, const pt_op *op, int n_lev, const int32_t *cols_dev,
+                                 const int *n_colours, int mu, const int *p_list, int n_p, int noise,
+                                 uint64_t seed, int set0, int n_sets, int dilute, int prec, double tol,
+                                 int maxit, double *est_out, pt_stats *stats);
+
 /* Deflation of given triplets (Sec. 2.4, Eq. (6)) for the displaced trace.
  * With U, V (n_ev columns each) and M = (U^H A V)^{-1} (the caller's small
  * matrix; for singular triplets, diag(1 / sigma)):
@@ -387,10 +392,39 @@ PT_API int pt_deflation_terms(pt_ctx *ctx, const pt_op *op, const int32_t *col_d
                               int n_ev, const double *U_dev, const double *V_dev, const double *M_host,
                               double *corr_out, double *exact_out);
 
-PT_API int pt_trace_PAinv_nested(pt_ctx *ctx, const pt_op *op, int n_lev, const int32_t *cols_dev,
-                                 const int *n_colours, int mu, const int *p_list, int n_p, int noise,
-                                 uint64_t seed, int set0, int n_sets, int dilute, int prec, double tol,
-                                 int maxit, double *est_out, pt_stats *stats);
+/* Eigenpairs of a small dense Hermitian matrix on the host: the Rayleigh-Ritz
+ * step of pt_singular_triplets, exported for its own tests (no paper
+ * counterpart; a textbook routine: Householder tridiagonalisation, a diagonal
+ * phase that makes the tridiagonal real, the symmetric QR algorithm with
+ * implicit Wilkinson shifts).  T_host: complex128 [m][m] row-major (host,
+ * read; its Hermitian part (T + T^H) / 2 is used); w_out: float64 [m] (host),
+ * every eigenvalue ascending; X_out: complex128 [n_vec][m] (host), the
+ * eigenvectors of the lowest n_vec, orthonormal.  1 <= m <= 4096,
+ * 0 <= n_vec <= m.  PT_ERR_NUMERIC on a non-finite entry.  No device work. */
+PT_API int pt_hermitian_eig(int m, const double *T_host, int n_vec, double *w_out, double *X_out);
+
+/* The lowest singular triplets that deflation uses (Sec. 2.4): n_ev smallest
+ * singular values of A with left / right singular vectors, A V = U diag(s).
+ * Block Lanczos with full reorthogonalisation on the Hermitian operator
+ * H = A (the Laplacian: symmetric positive definite, so U = V and s are its
+ * eigenvalues) or H = A^H A = (g5 A)^2 (Wilson-Dirac, g5-Hermitian: V are
+ * eigenvectors of H, s = ||A v||, U = A V diag(1/s)), then Rayleigh-Ritz on
+ * the basis.  Each candidate vector is orthogonalised twice against the basis
+ * (classical Gram-Schmidt) and dropped when less than 1e-8 of its norm is
+ * left, so a block at least as large as the multiplicity of the wanted values
+ * resolves degenerate ones.  The operator runs in FP64 (pt_apply); the Gram
+ * and combination kernels accumulate in FP64; the Rayleigh-Ritz
+ * eigendecomposition (basis size, at most block * n_iter) runs on the host.
+ *   start_dev: complex128 [block][N][dof] (device, read): the start block (the
+ *              Laplacian uses its real part);
+ *   U_dev, V_dev: complex128 [n_ev][N][dof] (device, written);
+ *   s_out: float64 [n_ev] (host, written), ascending.
+ * 1 <= block <= 64, n_iter >= 1, block * n_iter <= 1024, n_ev <= block * n_iter.
+ * PT_ERR_NUMERIC if the Krylov space closes with fewer than n_ev vectors.
+ * Temporary stream-ordered allocations: (2 block n_iter + 3 block) vectors.
+ * Synchronises. */
+PT_API int pt_singular_triplets(pt_ctx *ctx, const pt_op *op, int n_ev, int block, int n_iter,
+                                const double *start_dev, double *U_dev, double *V_dev, double *s_out);
 
 /* Adjoint gradient of the probed estimate T = sum_s est[s] for one
  * displacement p (not in the paper): with x = A^{-1} v, y = A^{-+} P^T v,

@@ -97,6 +97,8 @@ _SIGS = {
                                _I, _I, _I, _I, _D, _I, _P, ctypes.POINTER(Stats)], _I),
     "pt_deflation_terms": ([_P, _P, _P, _I, _I, ctypes.POINTER(_I), _I, _I, ctypes.c_uint64, _I, _I, _I, _P, _P, _P,
                             _P, _P], _I),
+    "pt_hermitian_eig": ([_I, _P, _I, _P, _P], _I),
+    "pt_singular_triplets": ([_P, _P, _I, _I, _I, _P, _P, _P, _P], _I),
     "pt_grad": ([_P, _P, _P, _I, _I, _I, _I, ctypes.c_uint64, _I, _I, _I, _I, _D, _I, _P, _P, _P, _P,
                  ctypes.POINTER(Stats)], _I),
 }
@@ -493,6 +495,33 @@ def deflation_terms(op, col, n_colours, mu, p_list, noise, seed, set0, n_sets, U
                                     int(n_sets), int(Mh.shape[0]), _ptr(U), _ptr(V), _np_ptr(Mh), _np_ptr(corr),
                                     _np_ptr(exact)))
     return corr, exact
+
+
+def hermitian_eig(T, n_vec):
+    """pt_hermitian_eig (host only): (w[m] ascending, X[m, n_vec]) for a
+    Hermitian numpy matrix T; the columns of X are the lowest eigenvectors."""
+    T = np.ascontiguousarray(np.asarray(T, dtype=np.complex128))
+    m = T.shape[0]
+    w = np.zeros(m, dtype=np.float64)
+    X = np.zeros((max(n_vec, 1), m), dtype=np.complex128)
+    _check(lib().pt_hermitian_eig(int(m), _np_ptr(T), int(n_vec), _np_ptr(w), _np_ptr(X)))
+    return w, X[:n_vec].T
+
+
+def singular_triplets(op, n_ev, block, n_iter, start):
+    """pt_singular_triplets: (U, s, V) with U, V torch complex128 [n_ev, N, dof]
+    on the device and s numpy float64 [n_ev] ascending; start: torch
+    complex128 [block, N, dof] on the device."""
+    import torch
+    if start.dtype != torch.complex128 or not start.is_cuda or start.numel() < int(block) * op.N * op.dof:
+        raise ValueError("start: torch complex128 [block, N, dof] on the device")
+    S = torch.view_as_real(start.contiguous()).contiguous()
+    U = torch.empty((n_ev, op.N, op.dof), dtype=torch.complex128, device=start.device)
+    V = torch.empty_like(U)
+    s = np.zeros(n_ev, dtype=np.float64)
+    _check(lib().pt_singular_triplets(op.ctx.handle, op._h, int(n_ev), int(block), int(n_iter), _ptr(S),
+                                      _ptr(torch.view_as_real(U)), _ptr(torch.view_as_real(V)), _np_ptr(s)))
+    return U, s, V
 
 
 def grad(op, col, n_colours, mu, p, noise="z2", seed=0, set0=0, n_sets=1, dilute=True, prec="mixed_fp32",
