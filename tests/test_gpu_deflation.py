@@ -100,7 +100,7 @@ def test_singular_triplets_laplacian_closed_form(pt, ctx):
     assert np.allclose(s, want, rtol=1e-10, atol=0)
     Vh = V.cpu().numpy().reshape(10, N).T
     assert np.abs(Vh.imag).max() == 0.0                       # a real start keeps the basis real
-    AV = np.stack([OE.Laplacian(dims, m2).apply(Vh[:, j].real) for j in range(10)], axis=1)
+    AV = np.stack([np.asarray(OE.Laplacian(dims, m2).apply(Vh[:, j].real)).reshape(-1) for j in range(10)], axis=1)
     assert np.abs(AV - Vh * s[None, :]).max() < 1e-8
     assert np.abs(Vh.conj().T @ Vh - np.eye(10)).max() < 1e-12
     assert np.array_equal(U.cpu().numpy(), V.cpu().numpy())
