@@ -19,50 +19,108 @@
 
 typedef std::complex<double> zc;
 
-// G[i][j] = sum_r conj(X_i[r]) Y_j[r], one CTA per entry (fixed summation order)
-__global__ void __launch_bounds__(256) k_eig_gram(long n, const double2 *__restrict__ X, int a,
-                                                  const double2 *__restrict__ Y, int b, double2 *G) {
-    __shared__ double sh[2 * 32];
-    for (long e = blockIdx.x; e < (long)a * b; e += gridDim.x) {
-        const int i = (int)(e / b), j = (int)(e % b);
-        const double2 *x = X + (size_t)i * n, *y = Y + (size_t)j * n;
-        double re = 0.0, im = 0.0;
-        for (long r = threadIdx.x; r < n; r += blockDim.x) {
-            const double2 u = x[r], v = y[r];
-            re += u.x * v.x + u.y * v.y;
-            im += u.x * v.y - u.y * v.x;
+// G[i][j] = sum_r conj(X_i[r]) Y_j[r] (G row-major a x b).  One CTA per
+// EIG_TI x EIG_TJ tile of G: each thread accumulates the tile over its rows
+// (registers), then warp shuffles and a shared-memory pass over the warps,
+// in a fixed order.  Each X vector is read ceil(b / EIG_TJ) times, each Y
+// vector ceil(a / EIG_TI) times.
+#define EIG_TI 4
+#define EIG_TJ 8
+#define EIG_NT 256
+__global__ void __launch_bounds__(EIG_NT) k_eig_gram(long n, const double2 *__restrict__ X, int a,
+                                                     const double2 *__restrict__ Y, int b, double2 *G) {
+    __shared__ double sh[EIG_NT / 32][2 * EIG_TI * EIG_TJ];
+    const int i0 = blockIdx.x * EIG_TI, j0 = blockIdx.y * EIG_TJ;
+    const int ni = min(EIG_TI, a - i0), nj = min(EIG_TJ, b - j0);
+    double re[EIG_TI][EIG_TJ], im[EIG_TI][EIG_TJ];
+#pragma unroll
+    for (int ii = 0; ii < EIG_TI; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < EIG_TJ; ++jj) re[ii][jj] = im[ii][jj] = 0.0;
+    for (long r = threadIdx.x; r < n; r += EIG_NT) {
+        double2 x[EIG_TI], y[EIG_TJ];
+#pragma unroll
+        for (int ii = 0; ii < EIG_TI; ++ii) x[ii] = ii < ni ? X[(size_t)(i0 + ii) * n + r] : make_double2(0.0, 0.0);
+#pragma unroll
+        for (int jj = 0; jj < EIG_TJ; ++jj) y[jj] = jj < nj ? Y[(size_t)(j0 + jj) * n + r] : make_double2(0.0, 0.0);
+#pragma unroll
+        for (int ii = 0; ii < EIG_TI; ++ii)
+#pragma unroll
+            for (int jj = 0; jj < EIG_TJ; ++jj) {
+                re[ii][jj] += x[ii].x * y[jj].x + x[ii].y * y[jj].y;
+                im[ii][jj] += x[ii].x * y[jj].y - x[ii].y * y[jj].x;
+            }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int ii = 0; ii < EIG_TI; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < EIG_TJ; ++jj) {
+            double u = re[ii][jj], v = im[ii][jj];
+            for (int o = 16; o > 0; o >>= 1) {
+                u += __shfl_down_sync(0xffffffffu, u, o);
+                v += __shfl_down_sync(0xffffffffu, v, o);
+            }
+            if (lane == 0) {
+                sh[warp][2 * (ii * EIG_TJ + jj)] = u;
+                sh[warp][2 * (ii * EIG_TJ + jj) + 1] = v;
+            }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            re += __shfl_down_sync(0xffffffffu, re, o);
-            im += __shfl_down_sync(0xffffffffu, im, o);
-        }
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-        __syncthreads();
-        if (lane == 0) { sh[2 * warp] = re; sh[2 * warp + 1] = im; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double sr = 0.0, si = 0.0;
-            for (int w = 0; w < nw; ++w) { sr += sh[2 * w]; si += sh[2 * w + 1]; }
-            G[e] = make_double2(sr, si);
-        }
-        __syncthreads();
+    __syncthreads();
+    for (int t = threadIdx.x; t < EIG_TI * EIG_TJ; t += EIG_NT) {
+        const int ii = t / EIG_TJ, jj = t % EIG_TJ;
+        if (ii >= ni || jj >= nj) continue;
+        double u = 0.0, v = 0.0;
+        for (int w = 0; w < EIG_NT / 32; ++w) { u += sh[w][2 * t]; v += sh[w][2 * t + 1]; }
+        G[(size_t)(i0 + ii) * b + j0 + jj] = make_double2(u, v);
     }
 }
 
-// Y_j = alpha Y_j + sum_i X_i C[i][j]  (Y must not overlap X)
-__global__ void k_eig_combine(long n, const double2 *__restrict__ X, int a, const double2 *__restrict__ C, int b,
-                              double alpha, double2 *Y) {
-    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n * b; t += (long)gridDim.x * blockDim.x) {
-        const int j = (int)(t / n);
-        const long r = t % n;
-        double re = 0.0, im = 0.0;
-        if (alpha != 0.0) { re = alpha * Y[(size_t)j * n + r].x; im = alpha * Y[(size_t)j * n + r].y; }
-        for (int i = 0; i < a; ++i) {
-            const double2 x = X[(size_t)i * n + r], c = C[(size_t)i * b + j];
-            re += x.x * c.x - x.y * c.y;
-            im += x.x * c.y + x.y * c.x;
+// Y_j = alpha Y_j + sum_i X_i C[i][j] (C row-major a x b; Y must not overlap
+// X).  A thread owns one row r and EIG_TJ columns (blockIdx.y); C is staged in
+// shared memory EIG_CI rows at a time, so each X vector is read
+// ceil(b / EIG_TJ) times.  The row loop is uniform over the CTA (barriers).
+#define EIG_CI 64
+__global__ void __launch_bounds__(EIG_NT) k_eig_combine(long n, const double2 *__restrict__ X, int a,
+                                                        const double2 *__restrict__ C, int b, double alpha,
+                                                        double2 *Y) {
+    __shared__ double2 sc[EIG_CI][EIG_TJ];
+    const int j0 = blockIdx.y * EIG_TJ, nj = min(EIG_TJ, b - j0);
+    for (long r0 = (long)blockIdx.x * EIG_NT; r0 < n; r0 += (long)gridDim.x * EIG_NT) {
+        const long r = r0 + threadIdx.x;
+        const bool on = r < n;
+        double2 acc[EIG_TJ];
+#pragma unroll
+        for (int jj = 0; jj < EIG_TJ; ++jj) {
+            acc[jj] = make_double2(0.0, 0.0);
+            if (on && jj < nj && alpha != 0.0) {
+                const double2 yv = Y[(size_t)(j0 + jj) * n + r];
+                acc[jj] = make_double2(alpha * yv.x, alpha * yv.y);
+            }
         }
-        Y[(size_t)j * n + r] = make_double2(re, im);
+        for (int c0 = 0; c0 < a; c0 += EIG_CI) {
+            const int nc = min(EIG_CI, a - c0);
+            __syncthreads();
+            for (int t = threadIdx.x; t < EIG_CI * EIG_TJ; t += EIG_NT) {
+                const int ci = t / EIG_TJ, jj = t % EIG_TJ;
+                sc[ci][jj] = (ci < nc && jj < nj) ? C[(size_t)(c0 + ci) * b + j0 + jj] : make_double2(0.0, 0.0);
+            }
+            __syncthreads();
+            if (on)
+                for (int ci = 0; ci < nc; ++ci) {
+                    const double2 x = X[(size_t)(c0 + ci) * n + r];
+#pragma unroll
+                    for (int jj = 0; jj < EIG_TJ; ++jj) {
+                        const double2 c = sc[ci][jj];
+                        acc[jj].x += x.x * c.x - x.y * c.y;
+                        acc[jj].y += x.x * c.y + x.y * c.x;
+                    }
+                }
+        }
+        if (on)
+#pragma unroll
+            for (int jj = 0; jj < EIG_TJ; ++jj)
+                if (jj < nj) Y[(size_t)(j0 + jj) * n + r] = acc[jj];
     }
 }
 
@@ -100,7 +158,8 @@ static inline zc zcmul(zc a, zc b) {    // conj(a) b
 //  2. the diagonal unitary D (d_0 = 1, d_{j+1} = d_j beta_j / |beta_j|) makes
 //     the sub-diagonal real: Tr = D^H Tc D has sub-diagonal |beta_j|;
 //  3. the symmetric QR algorithm with implicit Wilkinson shifts on Tr,
-//     Tr = Z diag(w) Z^T, the rotations accumulated in Z;
+//     Tr = Z diag(w) Z^T, Z the product of the rotations (kept, and applied
+//     only for the wanted vectors);
 // so eigenvector j of A is Q D z_j.  PT_ERR_NUMERIC if the QR iteration has
 // not converged after 60 m steps (NaN input).
 static int herm_eig(const std::vector<zc> &T, int m, int n_vec, std::vector<double> &w, std::vector<zc> &X) {
@@ -125,20 +184,26 @@ static int herm_eig(const std::vector<zc> &T, int m, int n_vec, std::vector<doub
         for (int i = k + 1; i < m; ++i) vn += std::norm(v[i]);
         vn = sqrt(vn);
         for (int i = k + 1; i < m; ++i) v[i] /= vn;
-        // trailing block S <- H S H = S - 2 v q^H - 2 q v^H, p = S v, q = p - (v^H p) v
-        double K = 0.0;
+        // trailing block S <- H S H = S - 2 v q^H - 2 q v^H, p = S v, q = p - (v^H p) v;
+        // S is kept in its lower triangle (row-major rows: p from rows and their mirror)
+        for (int i = k + 1; i < m; ++i) p[i] = zc(0.0, 0.0);
         for (int i = k + 1; i < m; ++i) {
-            zc acc(0.0, 0.0);
             const zc *row = &a[(size_t)i * m];
-            for (int j = k + 1; j < m; ++j) acc += zmul(row[j], v[j]);
-            p[i] = acc;
-            K += zcmul(v[i], acc).real();
+            const zc vi = v[i];
+            zc acc = zmul(row[i], vi);
+            for (int j = k + 1; j < i; ++j) {
+                acc += zmul(row[j], v[j]);
+                p[j] += zcmul(row[j], vi);             // S_ji = conj(S_ij)
+            }
+            p[i] += acc;
         }
+        double K = 0.0;
+        for (int i = k + 1; i < m; ++i) K += zcmul(v[i], p[i]).real();
         for (int i = k + 1; i < m; ++i) q[i] = p[i] - K * v[i];
         for (int i = k + 1; i < m; ++i) {
             zc *row = &a[(size_t)i * m];
             const zc vi = v[i], qi = q[i];
-            for (int j = k + 1; j < m; ++j) row[j] -= 2.0 * (zmul(vi, std::conj(q[j])) + zmul(qi, std::conj(v[j])));
+            for (int j = k + 1; j <= i; ++j) row[j] -= 2.0 * (zmul(vi, std::conj(q[j])) + zmul(qi, std::conj(v[j])));
         }
         for (int i = k + 1; i < m; ++i) a[(size_t)i * m + k] = a[(size_t)k * m + i] = zc(0.0, 0.0);
         a[(size_t)(k + 1) * m + k] = alpha;
@@ -156,9 +221,12 @@ static int herm_eig(const std::vector<zc> &T, int m, int n_vec, std::vector<doub
         e[j] = r;
         ph[j + 1] = r > 0.0 ? zmul(ph[j], zc(beta[j].real() / r, beta[j].imag() / r)) : ph[j];
     }
-    // 3. implicit symmetric QR; Zt[k m + i] = Z[i][k] (rotations act on rows of Zt)
-    std::vector<double> Zt((size_t)m * m, 0.0);
-    for (int i = 0; i < m; ++i) Zt[(size_t)i * m + i] = 1.0;
+    // 3. implicit symmetric QR.  Each rotation R_t (plane (k, k+1)) is kept:
+    // with Z^T = R_T ... R_1, eigenvector j is row j of Z^T, which the
+    // rotations give in reverse order, for the wanted vectors only.
+    struct Rot { int k; double c, s; };
+    std::vector<Rot> rots;
+    rots.reserve((size_t)8 * m);
     const double eps = 2.220446049250313e-16;
     long steps = 0;
     for (;;) {
@@ -187,12 +255,7 @@ static int herm_eig(const std::vector<zc> &T, int m, int n_vec, std::vector<doub
                 e[k + 1] *= c;
                 x = e[k];
             }
-            double *r0 = &Zt[(size_t)k * m], *r1 = &Zt[(size_t)(k + 1) * m];
-            for (int i = 0; i < m; ++i) {
-                const double u0 = r0[i], u1 = r1[i];
-                r0[i] = c * u0 + sn * u1;
-                r1[i] = -sn * u0 + c * u1;
-            }
+            rots.push_back({k, c, sn});
         }
     }
     std::vector<int> ord(m);
@@ -201,10 +264,22 @@ static int herm_eig(const std::vector<zc> &T, int m, int n_vec, std::vector<doub
     w.resize(m);
     for (int j = 0; j < m; ++j) w[j] = d[ord[j]];
     X.assign((size_t)n_vec * m, zc(0.0, 0.0));
+    // z_j^T = e_{ord[j]}^T R_T ... R_1 for all wanted j at once: Zw[i n_vec + j]
+    // = component i of z_j, so a rotation updates two contiguous rows
+    std::vector<double> Zw((size_t)m * std::max(n_vec, 1), 0.0);
+    for (int j = 0; j < n_vec; ++j) Zw[(size_t)ord[j] * n_vec + j] = 1.0;
+    for (size_t t = rots.size(); t-- > 0 && n_vec > 0;) {
+        const Rot &R = rots[t];
+        double *r0 = &Zw[(size_t)R.k * n_vec], *r1 = &Zw[(size_t)(R.k + 1) * n_vec];
+        for (int j = 0; j < n_vec; ++j) {
+            const double u0 = r0[j], u1 = r1[j];
+            r0[j] = R.c * u0 - R.s * u1;
+            r1[j] = R.s * u0 + R.c * u1;
+        }
+    }
     for (int j = 0; j < n_vec; ++j) {
         zc *y = &X[(size_t)j * m];
-        const double *z = &Zt[(size_t)ord[j] * m];
-        for (int i = 0; i < m; ++i) y[i] = z[i] * ph[i];
+        for (int i = 0; i < m; ++i) y[i] = Zw[(size_t)i * n_vec + j] * ph[i];
         for (int k = m - 3; k >= 0; --k) {      // y <- H_k y, last reflector first
             if (!refl[k]) continue;
             const zc *v = &V[(size_t)k * m];
@@ -253,7 +328,8 @@ struct EigRun {
 
 static int eig_gram(const EigRun &E, const double2 *X, int a, const double2 *Y, int b, double2 *d_G,
                     std::vector<zc> &G) {
-    k_eig_gram<<<E.grid, 256, 0, E.c->stream>>>(E.n, X, a, Y, b, d_G);
+    const dim3 g((a + EIG_TI - 1) / EIG_TI, (b + EIG_TJ - 1) / EIG_TJ);
+    k_eig_gram<<<g, EIG_NT, 0, E.c->stream>>>(E.n, X, a, Y, b, d_G);
     ++pt_kernel_launch_count;
     PT_CUDA(cudaGetLastError());
     G.resize((size_t)a * b);
@@ -265,7 +341,8 @@ static int eig_gram(const EigRun &E, const double2 *X, int a, const double2 *Y, 
 static int eig_combine(const EigRun &E, const double2 *X, int a, const std::vector<zc> &C, int b, double alpha,
                        double2 *Y, double2 *d_C) {
     PT_CUDA(cudaMemcpyAsync(d_C, C.data(), (size_t)a * b * sizeof(double2), cudaMemcpyHostToDevice, E.c->stream));
-    k_eig_combine<<<E.grid, 256, 0, E.c->stream>>>(E.n, X, a, d_C, b, alpha, Y);
+    const dim3 g((unsigned)std::min<long>((E.n + EIG_NT - 1) / EIG_NT, E.grid), (b + EIG_TJ - 1) / EIG_TJ);
+    k_eig_combine<<<g, EIG_NT, 0, E.c->stream>>>(E.n, X, a, d_C, b, alpha, Y);
     ++pt_kernel_launch_count;
     PT_CUDA(cudaGetLastError());
     PT_CUDA(cudaStreamSynchronize(E.c->stream));   // C (host) is reused by the caller
@@ -295,25 +372,35 @@ static int eig_apply_h(const EigRun &E, const double2 *X, int b, double2 *Y) {
     return PT_OK;
 }
 
-// Append the columns of W (b vectors) to the basis B (k vectors), each
-// orthogonalised twice against the basis so far and normalised, unless less
-// than 1e-8 of its norm remains.  *k grows by the columns kept.
+// Append the columns of W (b vectors, overwritten) to the basis B (k
+// vectors): the whole block is orthogonalised twice against the basis so far
+// (block classical Gram-Schmidt: G = B^H W, W <- W - B G), then each column
+// twice against the columns of this block already kept, and normalised,
+// unless less than 1e-8 of its norm before the projections remains.  *k grows
+// by the columns kept.
 static int eig_add_columns(const EigRun &E, double2 *W, int b, double2 *B, int *k, int kmax, double2 *d_G,
                            double2 *d_C) {
     std::vector<zc> G, C(1);
+    const int k0 = *k;
+    int rc = eig_gram(E, W, b, W, b, d_G, G);
+    if (rc) return rc;
+    std::vector<double> before(b);
+    for (int j = 0; j < b; ++j) before[j] = sqrt(std::max(G[(size_t)j * b + j].real(), 0.0));
+    for (int rep = 0; rep < 2 && k0 > 0; ++rep) {
+        if ((rc = eig_gram(E, B, k0, W, b, d_G, G))) return rc;
+        for (auto &g : G) g = -g;
+        if ((rc = eig_combine(E, B, k0, G, b, 1.0, W, d_C))) return rc;
+    }
     for (int j = 0; j < b && *k < kmax; ++j) {
         double2 *w = W + (size_t)j * E.n;
-        int rc = eig_gram(E, w, 1, w, 1, d_G, G);
-        if (rc) return rc;
-        const double before = sqrt(std::max(G[0].real(), 0.0));
-        for (int rep = 0; rep < 2 && *k > 0; ++rep) {
-            if ((rc = eig_gram(E, B, *k, w, 1, d_G, G))) return rc;
+        for (int rep = 0; rep < 2 && *k > k0; ++rep) {
+            if ((rc = eig_gram(E, B + (size_t)k0 * E.n, *k - k0, w, 1, d_G, G))) return rc;
             for (auto &g : G) g = -g;
-            if ((rc = eig_combine(E, B, *k, G, 1, 1.0, w, d_C))) return rc;
+            if ((rc = eig_combine(E, B + (size_t)k0 * E.n, *k - k0, G, 1, 1.0, w, d_C))) return rc;
         }
         if ((rc = eig_gram(E, w, 1, w, 1, d_G, G))) return rc;
         const double after = sqrt(std::max(G[0].real(), 0.0));
-        if (!(after > 1e-8 * before) || !(after > 0.0)) continue;
+        if (!(after > 1e-8 * before[j]) || !(after > 0.0)) continue;
         C[0] = 1.0 / after;
         if ((rc = eig_combine(E, w, 1, C, 1, 0.0, B + (size_t)(*k) * E.n, d_C))) return rc;
         ++*k;
