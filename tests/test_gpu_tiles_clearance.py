@@ -199,3 +199,20 @@ def test_nested_trace_wilson_diluted(pt, ctx):
     for l, (c, m) in enumerate([(c1, m1), (c2, m2)]):
         want = OE.probed_estimates(W, c, m, 3, 1, 1, mu, [0, 1], 1e-12)
         assert np.allclose(est[l], want, rtol=1e-8, atol=1e-7), l
+
+
+def test_colour_store_matches_tiled_colouring(pt, ctx, tmp_path):
+    """The tile store (Sec. 3.5): a miss colours the tile on the GPU and stores
+    it, a hit reads it back; both equal pt_colour_tiled bit for bit."""
+    from paper_2106_01275_gb300 import colour_db
+    db = colour_db.ColourDB(tmp_path)
+    dims, mu, ps, k = [8, 8, 16, 8], 2, [3], 2
+    want, m_want, tile = pt.colour_tiled(ctx, dims, mu, ps, k, "natural")
+    col, m, tile1, hit = db.colour(ctx, dims, mu, ps, k, "natural")
+    assert not hit and tile1 == tile and m == m_want
+    assert np.array_equal(col.cpu().numpy(), want.cpu().numpy())
+    col2, m2, _, hit2 = db.colour(ctx, dims, mu, [-3], k, "natural")
+    assert hit2 and m2 == m and np.array_equal(col2.cpu().numpy(), want.cpu().numpy())
+    stored, m3 = db.get(tile, mu, ps, k, "natural")
+    o_col, o_m = greedy_colour(tile, mu, ps, k, 0)
+    assert m3 == o_m and np.array_equal(stored, o_col)
