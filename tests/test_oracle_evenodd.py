@@ -70,3 +70,28 @@ def test_wilson_schur_solves_the_system():
 def test_odd_sides_are_refused():
     with pytest.raises(ValueError):
         EO.LaplacianEO([4, 3, 4, 4], 0.1)
+
+
+def test_clover_schur_is_the_block_formula_and_solves_the_system():
+    """With the clover term the diagonal blocks are site matrices: the
+    matrix-free S equals the dense block formula, the even solve plus
+    reconstruction is A^{-1} b, and c_sw = 0 gives the Wilson complement."""
+    from oracle import clover as CL
+    dims, kappa, csw = [2, 2, 2, 4], 0.12, 1.8
+    U = inputs.gauge_links(dims, 24, eps=0.8)
+    eo = EO.WilsonCloverEO(dims, U, kappa, csw)
+    A = D.dense_matrix(CL.WilsonClover(dims, U, kappa, csw))
+    n_e = eo.ev.size * 12
+    S = _dense(lambda v: eo.schur(v.reshape(-1, 12)), n_e, np.complex128)
+    idx_e = (eo.ev[:, None] * 12 + np.arange(12)).reshape(-1)
+    idx_o = (eo.od[:, None] * 12 + np.arange(12)).reshape(-1)
+    S_block = A[np.ix_(idx_e, idx_e)] - A[np.ix_(idx_e, idx_o)] @ np.linalg.inv(A[np.ix_(idx_o, idx_o)]) @ A[np.ix_(idx_o, idx_e)]
+    assert np.allclose(S, S_block, atol=1e-12)
+    assert not np.allclose(A[np.ix_(idx_o, idx_o)], np.eye(idx_o.size))          # the blocks are not trivial
+    rng = np.random.default_rng(6)
+    b = rng.standard_normal((eo.N, 12)) + 1j * rng.standard_normal((eo.N, 12))
+    x_e = np.linalg.solve(S, eo.rhs(b).reshape(-1))
+    assert np.allclose(eo.reconstruct(x_e, b).reshape(-1), np.linalg.solve(A, b.reshape(-1)), atol=1e-11)
+    eo0, eow = EO.WilsonCloverEO(dims, U, kappa, 0.0), EO.WilsonEO(dims, U, kappa)
+    v = rng.standard_normal((eo.ev.size, 12)) + 1j * rng.standard_normal((eo.ev.size, 12))
+    assert np.allclose(eo0.schur(v), eow.schur(v), atol=1e-14)
