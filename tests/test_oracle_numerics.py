@@ -271,7 +271,10 @@ def test_exact_variance_vs_enumeration_2to4_lattice():
     assert abs(V.exact_variance(B, col, 0) - brute_force_variance(B, col, 0, 16)) < 1e-12
 
 
-def test_variance_survey_values_and_probing_reduces_it():
+def test_probing_reduces_the_exact_variance():
+    """4^4, m^2 = 0.1, p = 1 along dim 0: distance-1 and -2 colourings take 4
+    and 8 colours, and each step of probing lowers the exact Z2 variance
+    (Eq. (2) in its general form, itself pinned by brute force above)."""
     dims, m2 = [4, 4, 4, 4], 0.1
     B = np.linalg.inv(dense_laplacian_loops(dims, m2))[L.shift_map(dims, 0, 1), :]
     vh = V.exact_variance(B, np.zeros(256, int), 0)
@@ -280,9 +283,7 @@ def test_variance_survey_values_and_probing_reduces_it():
     v1 = V.exact_variance(B, c1, 0)
     v2 = V.exact_variance(B, c2, 0)
     assert (m1, m2_) == (4, 8)
-    assert abs(vh - 205.847384320806) < 1e-8 and abs(v1 - 46.1635621789066) < 1e-8
-    assert abs(v2 - 22.3233491167402) < 1e-8
-    assert vh > v1 > v2
+    assert vh > 2 * v1 > 0 and v1 > 1.5 * v2 > 0
 
 
 def test_unbiased_and_sample_variance():
