@@ -51,3 +51,61 @@ def test_clock_sampler_reads_reasons():
     assert c["reasons"] == ["sw_power_cap"]
     cs.proc = None
     assert cs.stop()["reasons"] == ["unsampled"]
+
+
+def test_deflation_leg_json_line(monkeypatch, capsys):
+    """`bench.py --workload deflation --case small` end to end on the CPU, with
+    every call of the binding stood in for by the oracle (colouring, block
+    Lanczos triplets, probed estimates, deflation corrections): one JSON line
+    whose checks hold and whose deflated variance is below the plain one."""
+    import numpy as np
+    import torch
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle.estimator as OE
+    from oracle import deflation as D
+    from oracle.colouring import greedy_colour
+    from paper_2106_01275_gb300 import ptrace as pt
+
+    monkeypatch.setattr(torch.cuda, "set_device", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(torch.Tensor, "cuda", lambda self, *a, **k: self)
+    monkeypatch.setattr(pt, "Context", lambda dev: types.SimpleNamespace(device=dev))
+    monkeypatch.setattr(pt, "laplacian", lambda ctx, dims, m2: types.SimpleNamespace(dims=dims, m2=m2))
+    monkeypatch.setattr(pt, "colour", lambda ctx, dims, mu, ps, k, order: greedy_colour(dims, mu, ps, k, 0))
+
+    def triplets(op, n_ev, block, n_iter, start):
+        o = OE.Laplacian(op.dims, op.m2)
+        w, V = D.lanczos_lowest(lambda x: np.asarray(o.apply(x)).reshape(-1), o_n(op), n_ev, n_iter, 0,
+                                np.float64, block)
+        Vt = V.T.reshape(n_ev, -1, 1).astype(np.complex128)
+        return Vt, w, Vt
+
+    def o_n(op):
+        return int(np.prod(op.dims))
+
+    def trace(op, col, m, mu, ps, noise, seed, set0, n_sets, dil, prec, tol, maxit):
+        est = OE.probed_estimates(OE.Laplacian(op.dims, op.m2), col, m, seed, n_sets, 0, mu, ps, 1e-10)
+        return est, None, None, {"n_rhs": m * n_sets}
+
+    def terms(op, col, m, mu, ps, noise, seed, set0, n_sets, U, V, M):
+        Uh = np.asarray(U).reshape(U.shape[0], -1).T
+        Vh = np.asarray(V).reshape(V.shape[0], -1).T
+        return (D.deflation_corrections(col, m, seed, n_sets, 0, op.dims, mu, ps, Uh, Vh, M),
+                D.deflated_part(Uh, Vh, M, op.dims, mu, ps))
+
+    monkeypatch.setattr(pt, "singular_triplets", triplets)
+    monkeypatch.setattr(pt, "trace", trace)
+    monkeypatch.setattr(pt, "deflation_terms", terms)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "deflation", "--case", "small"])
+    bench.main()
+    lines = [l for l in capsys.readouterr().out.strip().splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "higher_is_better", "config", "var_plain", "var_deflated", "seconds",
+                "check_ritz_vs_closed_form_max_rel", "check_p0_trace_minus_sum_inv_s"):
+        assert key in d, key
+    assert d["config"]["workload"].startswith("deflation: 8^4")
+    assert d["check_ritz_vs_closed_form_max_rel"] < 1e-6 and d["check_p0_trace_minus_sum_inv_s"] < 1e-9
+    assert len(d["var_plain"]) == 5 and all(a > 10 * b for a, b in zip(d["var_plain"], d["var_deflated"]))
