@@ -426,6 +426,40 @@ PT_API int pt_hermitian_eig(int m, const double *T_host, int n_vec, double *w_ou
 PT_API int pt_singular_triplets(pt_ctx *ctx, const pt_op *op, int n_ev, int block, int n_iter,
                                 const double *start_dev, double *U_dev, double *V_dev, double *s_out);
 
+/* ---------------------------------------------------------------- even-odd */
+
+/* Even-odd (red-black) preconditioning of both operators (the standard first
+ * step towards the paper's production solver, Sec. 4.2; no equation of the
+ * paper).  Every lattice side must be even (PT_ERR_ARG otherwise).  With the
+ * even sites first, A = [[A_ee, A_eo], [A_oe, A_oo]] and A x = b becomes
+ *   S x_e = b'_e,  S = A_ee - A_eo A_oo^{-1} A_oe,
+ *   b'_e = b_e - A_eo A_oo^{-1} b_o,  x_o = A_oo^{-1} (b_o - A_oe x_e);
+ * Laplacian (d = 8 + m2): S = d - H_eo H_oe / d, b'_e = b_e + H_eo b_o / d,
+ * x_o = (b_o + H_oe x_e) / d; Wilson: S = 1 - kappa^2 D_eo D_oe,
+ * b'_e = b_e + kappa D_eo b_o, x_o = b_o + kappa D_oe x_e.
+ * A half field holds the sites of one parity in storage order: site i is
+ * entry i >> 1 of its parity's half field.  Fields are in the user layout
+ * (float64 [nrhs][sites] or complex128 [nrhs][sites][4][3], device), FP64
+ * throughout; calls are enqueued on the context stream.
+ *
+ * pt_eo_layout (host only): site_out[h] (int32 [N/2]) = storage index of
+ * entry h of the half field of `parity`; nbr_out[8 h + 2 mu + 0/1] (int32
+ * [N/2][8]) = half-field index (in the other parity) of x + mu / x - mu. */
+PT_API int pt_eo_layout(const int dims[4], int parity, int32_t *site_out, int32_t *nbr_out);
+
+/* ye = S xe for nrhs even half fields (xe, ye must not overlap; a temporary
+ * stream-ordered odd half field per right-hand side). */
+PT_API int pt_eo_schur(pt_ctx *ctx, const pt_op *op, const double *xe_dev, double *ye_dev, int nrhs);
+
+/* be = b'_e (even half fields) from full fields b. */
+PT_API int pt_eo_prepare(pt_ctx *ctx, const pt_op *op, const double *b_dev, double *be_dev, int nrhs);
+
+/* x (full fields) = x_e on the even sites and x_o = A_oo^{-1}(b_o - A_oe x_e)
+ * on the odd ones, from even half fields xe and full fields b (a temporary
+ * stream-ordered odd half field per right-hand side). */
+PT_API int pt_eo_reconstruct(pt_ctx *ctx, const pt_op *op, const double *xe_dev, const double *b_dev,
+                             double *x_dev, int nrhs);
+
 /* Adjoint gradient of the probed estimate T = sum_s est[s] for one
  * displacement p (not in the paper): with x = A^{-1} v, y = A^{-+} P^T v,
  *   dT/dtheta = - sum_v y^H (dA/dtheta) x.

@@ -99,6 +99,10 @@ _SIGS = {
                             _P, _P], _I),
     "pt_hermitian_eig": ([_I, _P, _I, _P, _P], _I),
     "pt_singular_triplets": ([_P, _P, _I, _I, _I, _P, _P, _P, _P], _I),
+    "pt_eo_layout": ([ctypes.POINTER(_I), _I, _P, _P], _I),
+    "pt_eo_schur": ([_P, _P, _P, _P, _I], _I),
+    "pt_eo_prepare": ([_P, _P, _P, _P, _I], _I),
+    "pt_eo_reconstruct": ([_P, _P, _P, _P, _P, _I], _I),
     "pt_grad": ([_P, _P, _P, _I, _I, _I, _I, ctypes.c_uint64, _I, _I, _I, _I, _D, _I, _P, _P, _P, _P,
                  ctypes.POINTER(Stats)], _I),
 }
@@ -522,6 +526,59 @@ def singular_triplets(op, n_ev, block, n_iter, start):
     _check(lib().pt_singular_triplets(op.ctx.handle, op._h, int(n_ev), int(block), int(n_iter), _ptr(S),
                                       _ptr(torch.view_as_real(U)), _ptr(torch.view_as_real(V)), _np_ptr(s)))
     return U, s, V
+
+
+def eo_layout(dims, parity):
+    """pt_eo_layout (host only): (site[N/2], nbr[N/2, 8]) int32."""
+    Nh = int(np.prod(dims)) // 2
+    site = np.zeros(Nh, dtype=np.int32)
+    nbr = np.zeros((Nh, 8), dtype=np.int32)
+    _check(lib().pt_eo_layout(_ints(dims), int(parity), _np_ptr(site), _np_ptr(nbr)))
+    return site, nbr
+
+
+def _eo_field(op, x, sites, name):
+    import torch
+    want = (sites,) if op.dof == 1 else (sites, 4, 3)
+    dt = torch.float64 if op.dof == 1 else torch.complex128
+    if x.dtype != dt or not x.is_cuda or tuple(x.shape[1:]) != want:
+        raise ValueError("%s: %s [nrhs, %s] on the device" % (name, dt, ", ".join(map(str, want))))
+    return x.contiguous()
+
+
+def _eo_ptr(t):
+    import torch
+    return _ptr(torch.view_as_real(t) if t.is_complex() else t)
+
+
+def eo_schur(op, xe):
+    """pt_eo_schur: S xe for even half fields xe [nrhs, N/2(, 4, 3)]."""
+    import torch
+    xe = _eo_field(op, xe, op.N // 2, "xe")
+    ye = torch.empty_like(xe)
+    _check(lib().pt_eo_schur(op.ctx.handle, op._h, _eo_ptr(xe), _eo_ptr(ye), int(xe.shape[0])))
+    return ye
+
+
+def eo_prepare(op, b):
+    """pt_eo_prepare: b'_e [nrhs, N/2(, 4, 3)] from full fields b [nrhs, N(, 4, 3)]."""
+    import torch
+    b = _eo_field(op, b, op.N, "b")
+    be = torch.empty((b.shape[0], op.N // 2) + tuple(b.shape[2:]), dtype=b.dtype, device=b.device)
+    _check(lib().pt_eo_prepare(op.ctx.handle, op._h, _eo_ptr(b), _eo_ptr(be), int(b.shape[0])))
+    return be
+
+
+def eo_reconstruct(op, xe, b):
+    """pt_eo_reconstruct: full solutions x [nrhs, N(, 4, 3)] from xe and b."""
+    import torch
+    xe = _eo_field(op, xe, op.N // 2, "xe")
+    b = _eo_field(op, b, op.N, "b")
+    if xe.shape[0] != b.shape[0]:
+        raise ValueError("xe and b hold different numbers of right-hand sides")
+    x = torch.empty_like(b)
+    _check(lib().pt_eo_reconstruct(op.ctx.handle, op._h, _eo_ptr(xe), _eo_ptr(b), _eo_ptr(x), int(b.shape[0])))
+    return x
 
 
 def grad(op, col, n_colours, mu, p, noise="z2", seed=0, set0=0, n_sets=1, dilute=True, prec="mixed_fp32",
