@@ -460,6 +460,39 @@ PT_API int pt_eo_prepare(pt_ctx *ctx, const pt_op *op, const double *b_dev, doub
 PT_API int pt_eo_reconstruct(pt_ctx *ctx, const pt_op *op, const double *xe_dev, const double *b_dev,
                              double *x_dev, int nrhs);
 
+/* ---------------------------------------------------------------- clover */
+
+/* Clover (Sheikholeslami-Wohlert) site blocks of the Wilson-Dirac operator
+ * (Sec. 4.2 names a clover Wilson operator and leaves its definition to the
+ * literature; the textbook form with this library's gamma basis and hopping
+ * sign):
+ *   C(x) = -kappa c_sw sum_{mu<nu} sigma_{mu nu} (x) F_{mu nu}(x),
+ *   sigma_{mu nu} = (i/2)[g_mu, g_nu],  F_{mu nu} = (Q_{mu nu} - Q_{mu nu}^H)/(8 i),
+ * Q_{mu nu}(x) the four plaquettes of the (mu, nu) plane at x, so that the
+ * clover operator is A_c = A_W + C.  Blocks: complex128 [N][12][12],
+ * row-major, component = 3 spin + colour.  The per-site arithmetic is shared
+ * by the device kernels and the host-only entries (which need no GPU).
+ *
+ * pt_clover_blocks_host: from links in the user layout (host, complex128
+ * [N][4][3][3]); blocks_out on the host.  pt_clover_blocks: from the links of
+ * a Wilson operator; blocks_dev on the device (enqueued on the stream). */
+PT_API int pt_clover_blocks_host(const int dims[4], const double *U_host, double kappa, double csw,
+                                 double *blocks_out);
+PT_API int pt_clover_blocks(pt_ctx *ctx, const pt_op *op, double csw, double *blocks_dev);
+
+/* y[r][x] = beta y[r][x] + B(x) x[r][x] for nrhs spinor fields (user layout,
+ * device; x and y must not overlap) and blocks B [N][12][12] (device).  With
+ * beta = 1 and y = A_W x (pt_apply) this is the clover operator. */
+PT_API int pt_site_blocks_apply(pt_ctx *ctx, int N, const double *blocks_dev, const double *x_dev, double beta,
+                                double *y_dev, int nrhs);
+
+/* inv = (shift 1 + B(x))^{-1} per site by Gauss-Jordan elimination with
+ * partial pivoting (shift = 1 gives the clover diagonal block A_xx);
+ * PT_ERR_NUMERIC if a block is singular.  _host: n blocks on the host; the
+ * device form synchronises the stream. */
+PT_API int pt_site_blocks_invert_host(int n, const double *blocks, double shift, double *inv_out);
+PT_API int pt_site_blocks_invert(pt_ctx *ctx, int N, const double *blocks_dev, double shift, double *inv_dev);
+
 /* Adjoint gradient of the probed estimate T = sum_s est[s] for one
  * displacement p (not in the paper): with x = A^{-1} v, y = A^{-+} P^T v,
  *   dT/dtheta = - sum_v y^H (dA/dtheta) x.

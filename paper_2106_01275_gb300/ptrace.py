@@ -103,6 +103,11 @@ _SIGS = {
     "pt_eo_schur": ([_P, _P, _P, _P, _I], _I),
     "pt_eo_prepare": ([_P, _P, _P, _P, _I], _I),
     "pt_eo_reconstruct": ([_P, _P, _P, _P, _P, _I], _I),
+    "pt_clover_blocks_host": ([ctypes.POINTER(_I), _P, _D, _D, _P], _I),
+    "pt_clover_blocks": ([_P, _P, _D, _P], _I),
+    "pt_site_blocks_apply": ([_P, _I, _P, _P, _D, _P, _I], _I),
+    "pt_site_blocks_invert_host": ([_I, _P, _D, _P], _I),
+    "pt_site_blocks_invert": ([_P, _I, _P, _D, _P], _I),
     "pt_grad": ([_P, _P, _P, _I, _I, _I, _I, ctypes.c_uint64, _I, _I, _I, _I, _D, _I, _P, _P, _P, _P,
                  ctypes.POINTER(Stats)], _I),
 }
@@ -579,6 +584,66 @@ def eo_reconstruct(op, xe, b):
     x = torch.empty_like(b)
     _check(lib().pt_eo_reconstruct(op.ctx.handle, op._h, _eo_ptr(xe), _eo_ptr(b), _eo_ptr(x), int(b.shape[0])))
     return x
+
+
+def clover_blocks_host(dims, U, kappa, csw):
+    """pt_clover_blocks_host: C(x) as numpy complex128 [N, 12, 12] from numpy
+    links [N, 4, 3, 3] (host only)."""
+    U = np.ascontiguousarray(np.asarray(U, dtype=np.complex128))
+    N = int(np.prod(dims))
+    if U.shape != (N, 4, 3, 3):
+        raise ValueError("links: complex128 [N, 4, 3, 3]")
+    out = np.zeros((N, 12, 12), dtype=np.complex128)
+    _check(lib().pt_clover_blocks_host(_ints(dims), _np_ptr(U), float(kappa), float(csw), _np_ptr(out)))
+    return out
+
+
+def site_blocks_invert_host(B, shift=1.0):
+    """pt_site_blocks_invert_host: (shift 1 + B)^{-1} per block, numpy [n, 12, 12]."""
+    B = np.ascontiguousarray(np.asarray(B, dtype=np.complex128))
+    if B.ndim != 3 or B.shape[1:] != (12, 12):
+        raise ValueError("blocks: complex128 [n, 12, 12]")
+    out = np.zeros_like(B)
+    _check(lib().pt_site_blocks_invert_host(int(B.shape[0]), _np_ptr(B), float(shift), _np_ptr(out)))
+    return out
+
+
+def clover_blocks(op, csw):
+    """pt_clover_blocks: C(x) as torch complex128 [N, 12, 12] on the device."""
+    import torch
+    if op.dof != 12:
+        raise ValueError("a Wilson-Dirac operator is required")
+    out = torch.empty((op.N, 12, 12), dtype=torch.complex128, device="cuda:%d" % op.ctx.device)
+    _check(lib().pt_clover_blocks(op.ctx.handle, op._h, float(csw), _ptr(torch.view_as_real(out))))
+    return out
+
+
+def site_blocks_apply(ctx, B, x, y=None, beta=0.0):
+    """pt_site_blocks_apply: beta y + B x per site; B [N, 12, 12], x [nrhs, N, 4, 3]
+    (torch complex128 on the device)."""
+    import torch
+    N = B.shape[0]
+    if B.shape != (N, 12, 12) or x.dim() != 4 or tuple(x.shape[1:]) != (N, 4, 3) or \
+            B.dtype != torch.complex128 or x.dtype != torch.complex128:
+        raise ValueError("B: complex128 [N, 12, 12], x: complex128 [nrhs, N, 4, 3]")
+    B, x = B.contiguous(), x.contiguous()
+    if y is None:
+        y, beta = torch.zeros_like(x), 0.0
+    elif y.shape != x.shape or y.dtype != x.dtype or not y.is_contiguous():
+        raise ValueError("y: contiguous, the shape and type of x")
+    _check(lib().pt_site_blocks_apply(ctx.handle, int(N), _ptr(torch.view_as_real(B)), _ptr(torch.view_as_real(x)),
+                                      float(beta), _ptr(torch.view_as_real(y)), int(x.shape[0])))
+    return y
+
+
+def site_blocks_invert(ctx, B, shift=1.0):
+    """pt_site_blocks_invert: (shift 1 + B)^{-1} per site, torch [N, 12, 12] on the device."""
+    import torch
+    B = B.contiguous()
+    out = torch.empty_like(B)
+    _check(lib().pt_site_blocks_invert(ctx.handle, int(B.shape[0]), _ptr(torch.view_as_real(B)), float(shift),
+                                       _ptr(torch.view_as_real(out))))
+    return out
 
 
 def grad(op, col, n_colours, mu, p, noise="z2", seed=0, set0=0, n_sets=1, dilute=True, prec="mixed_fp32",
