@@ -460,6 +460,14 @@ PT_API int pt_eo_prepare(pt_ctx *ctx, const pt_op *op, const double *b_dev, doub
 PT_API int pt_eo_reconstruct(pt_ctx *ctx, const pt_op *op, const double *xe_dev, const double *b_dev,
                              double *x_dev, int nrhs);
 
+/* The same three steps on the host, with the device entries' site arithmetic
+ * and sequence of steps (no GPU needed): kind 0 (Laplacian, m2) or 1 (Wilson,
+ * kappa, links U_host in the user layout, antip); step 0: out = S in1 (even
+ * half fields), 1: out = b'_e from full fields in1, 2: out = full x from
+ * even half fields in1 and full fields in2.  Host buffers. */
+PT_API int pt_eo_host(int kind, const int dims[4], double m2, double kappa, const double *U_host, int antip,
+                      int step, const double *in1, const double *in2, double *out, int nrhs);
+
 /* ---------------------------------------------------------------- clover */
 
 /* Clover (Sheikholeslami-Wohlert) site blocks of the Wilson-Dirac operator

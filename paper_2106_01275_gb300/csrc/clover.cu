@@ -15,39 +15,13 @@
 // the same code.
 #include <algorithm>
 
+#include "hd_complex.cuh"
 #include "pt_common.cuh"
-
-struct zd {
-    double re, im;
-};
-__host__ __device__ __forceinline__ zd zadd(zd a, zd b) { return {a.re + b.re, a.im + b.im}; }
-__host__ __device__ __forceinline__ zd zsub(zd a, zd b) { return {a.re - b.re, a.im - b.im}; }
-__host__ __device__ __forceinline__ zd zmulc(zd a, zd b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
-__host__ __device__ __forceinline__ zd zconj(zd a) { return {a.re, -a.im}; }
-__host__ __device__ __forceinline__ zd zscal(zd a, double s) { return {a.re * s, a.im * s}; }
 
 // sigma_{mu nu} for the six planes mu < nu, in the order (0,1) (0,2) (0,3) (1,2) (1,3) (2,3)
 struct SigmaTab {
     zd s[6][16];
 };
-
-static void gamma_chiral(int mu, zd g[16]) {
-    for (int i = 0; i < 16; ++i) g[i] = {0.0, 0.0};
-    // Pauli matrices
-    const zd P[3][4] = {{{0, 0}, {1, 0}, {1, 0}, {0, 0}},
-                        {{0, 0}, {0, -1}, {0, 1}, {0, 0}},
-                        {{1, 0}, {0, 0}, {0, 0}, {-1, 0}}};
-    if (mu < 3) {   // [[0, -i s_k], [i s_k, 0]]
-        for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 2; ++b) {
-                const zd s = P[mu][2 * a + b];
-                g[a * 4 + (b + 2)] = {s.im, -s.re};           // -i s
-                g[(a + 2) * 4 + b] = {-s.im, s.re};           //  i s
-            }
-    } else {        // [[0, I], [I, 0]]
-        g[0 * 4 + 2] = g[1 * 4 + 3] = g[2 * 4 + 0] = g[3 * 4 + 1] = {1.0, 0.0};
-    }
-}
 
 static SigmaTab make_sigma() {
     SigmaTab T;
@@ -79,24 +53,6 @@ __host__ __device__ __forceinline__ int cl_step(const CloverGeom &g, int i, int 
     if (s > 0) return (x == g.D[mu] - 1) ? i - (g.D[mu] - 1) * g.stride[mu] : i + g.stride[mu];
     return (x == 0) ? i + (g.D[mu] - 1) * g.stride[mu] : i - g.stride[mu];
 }
-
-// link accessors: the library's packed FP64 links [4][9][N] (device) or the
-// user layout [N][4][3][3] (host)
-struct PackedLinks {
-    const double *U;
-    int N;
-    __host__ __device__ __forceinline__ zd operator()(int site, int mu, int e) const {
-        const size_t k = ((size_t)(mu * 9 + e) * N + site) * 2;
-        return {U[k], U[k + 1]};
-    }
-};
-struct UserLinks {
-    const double *U;
-    __host__ __device__ __forceinline__ zd operator()(int site, int mu, int e) const {
-        const size_t k = (((size_t)site * 4 + mu) * 9 + e) * 2;
-        return {U[k], U[k + 1]};
-    }
-};
 
 // 3 x 3 products of links taken forward (U) or backward (U^H)
 template <class L>

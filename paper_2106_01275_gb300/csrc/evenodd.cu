@@ -16,10 +16,15 @@
 // D_0 even, the sites i and i ^ 1 have opposite parities, so site i is entry
 // i >> 1 of its parity's half field.  All fields here are in the user layout
 // (float64 [nrhs][sites] for the Laplacian, complex128 [nrhs][sites][4][3]
-// for Wilson) and all arithmetic is FP64; the hop reproduces the library's
-// site operator (same spin projection, links and boundary signs).
+// for Wilson) and all arithmetic is FP64.
+//
+// The site arithmetic and the sequence of steps are shared by the device
+// entry points and host-only ones (which tests run without a GPU): only the
+// loop over sites differs (a kernel launch or a host loop).
 #include <algorithm>
+#include <vector>
 
+#include "hd_complex.cuh"
 #include "pt_common.cuh"
 
 struct EoGeom {
@@ -63,141 +68,279 @@ struct UserField {
     const double *f;
     int half;
     int sites;      // N or N / 2
-    __device__ __forceinline__ size_t at(int y) const { return (size_t)(half ? (y >> 1) : y); }
+    __host__ __device__ __forceinline__ size_t at(int y) const { return (size_t)(half ? (y >> 1) : y); }
 };
 
-// (H psi)(x) for the Wilson hopping term at storage index i, psi read from
-// field F of right-hand side r: the library's site operator with the
-// neighbour spinors taken from a user-layout full or half field
-__device__ __forceinline__ void eo_wilson_hop(const EoGeom &g, const double *U64, int antip, const UserField &F,
-                                              int r, int i, const int x[4], Cx<double> acc[4][3]) {
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) acc[s][a] = Cx<double>{0.0, 0.0};
+struct EoOp {
+    int kind;       // 0 Laplacian, 1 Wilson
+    int antip;      // antiperiodic in dim 3 (Wilson)
+    GammaTab G;
+};
+
+// (H psi)(x) of the Wilson hopping term at storage index i, from its
+// definition: sum over mu of (1 - g_mu) U_mu(x) psi(x + mu) and
+// (1 + g_mu) U_mu(x - mu)^H psi(x - mu), times -1 on the hops that cross the
+// time boundary when time is antiperiodic; psi is right-hand side r of F
+template <class L>
+__host__ __device__ void eo_wilson_hop(const EoGeom &g, const L &U, const EoOp &o, const UserField &F, int r, int i,
+                                       const int x[4], zd acc[12]) {
+    for (int c = 0; c < 12; ++c) acc[c] = {0.0, 0.0};
     const double *base = F.f + (size_t)r * F.sites * 24;
-#pragma unroll 1
-    for (int mu = 0; mu < 4; ++mu) {
-#pragma unroll
+    for (int mu = 0; mu < 4; ++mu)
         for (int dir = 0; dir < 2; ++dir) {
-            const int s = dir == 0 ? 1 : -1;
-            const int y = eo_neighbour(g, i, x, mu, s);
-            const double sg = dir == 0 ? -1.0 : 1.0;          // (1 - g_mu) forward, (1 + g_mu) backward
-            const bool cross = antip && mu == 3 && (dir == 0 ? x[3] == g.D[3] - 1 : x[3] == 0);
+            const int y = eo_neighbour(g, i, x, mu, dir == 0 ? 1 : -1);
+            const bool cross = o.antip && mu == 3 && (dir == 0 ? x[3] == g.D[3] - 1 : x[3] == 0);
             const double eta = cross ? -1.0 : 1.0;
-            Cx<double> ps[4][3], h[2][3], uh[2][3], u[3][3];
+            const double sgn = dir == 0 ? -1.0 : 1.0;         // (1 - g_mu) forward, (1 + g_mu) backward
             const double *p = base + F.at(y) * 24;
-#pragma unroll
-            for (int c = 0; c < 12; ++c) ps[c / 3][c % 3] = Cx<double>{p[2 * c], p[2 * c + 1]};
-            spin_project<double>(mu, sg, ps, h);
-            load_link<double, double>(U64, g.N, mu, dir == 0 ? i : y, u);
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-#pragma unroll
+            zd chi[12];                                        // colour-rotated neighbour
+            for (int s = 0; s < 4; ++s)
                 for (int a = 0; a < 3; ++a) {
-                    Cx<double> t;
-                    if (dir == 0) {                             // U_mu(x) h
-                        t = cmul(u[a][0], h[k][0]);
-                        t = cadd(t, cmul(u[a][1], h[k][1]));
-                        t = cadd(t, cmul(u[a][2], h[k][2]));
-                    } else {                                    // U_mu(x - mu)^H h
-                        t = cconjmul(u[0][a], h[k][0]);
-                        t = cadd(t, cconjmul(u[1][a], h[k][1]));
-                        t = cadd(t, cconjmul(u[2][a], h[k][2]));
+                    zd t = {0.0, 0.0};
+                    for (int b = 0; b < 3; ++b) {
+                        const zd w = dir == 0 ? U(i, mu, a * 3 + b) : zconj(U(y, mu, b * 3 + a));
+                        t = zadd(t, zmulc(w, zd{p[2 * (s * 3 + b)], p[2 * (s * 3 + b) + 1]}));
                     }
-                    uh[k][a] = t;
+                    chi[s * 3 + a] = t;
                 }
-            spin_accumulate<double>(mu, sg, eta, uh, acc);
+            for (int s = 0; s < 4; ++s)
+                for (int a = 0; a < 3; ++a) {
+                    zd gchi = {0.0, 0.0};
+                    for (int t = 0; t < 4; ++t) gchi = zadd(gchi, zmulc(o.G.g[mu][s * 4 + t], chi[t * 3 + a]));
+                    acc[s * 3 + a] = zadd(acc[s * 3 + a], zscal(zadd(chi[s * 3 + a], zscal(gchi, sgn)), eta));
+                }
+        }
+}
+
+// one output entry: out[r][h] = alpha self[r][site] + beta (hop src)[r][site]
+// at the site of parity par_out (out is a half field; self may be NULL)
+template <class L>
+__host__ __device__ void eo_axpby_site(const EoGeom &g, const L &U, const EoOp &o, int par_out,
+                                       const UserField &self, double alpha, const UserField &src, double beta, int r,
+                                       int h, double *out) {
+    int x[4];
+    const int i = eo_full_site(g, par_out, h, x);
+    if (o.kind == 0) {
+        const double *sb = src.f + (size_t)r * src.sites;
+        double hop = 0.0;
+        for (int mu = 0; mu < 4; ++mu) {
+            hop += sb[src.at(eo_neighbour(g, i, x, mu, 1))];
+            hop += sb[src.at(eo_neighbour(g, i, x, mu, -1))];
+        }
+        double v = beta * hop;
+        if (self.f) v += alpha * self.f[(size_t)r * self.sites + self.at(i)];
+        out[(size_t)r * g.Nh + h] = v;
+    } else {
+        zd acc[12];
+        eo_wilson_hop(g, U, o, src, r, i, x, acc);
+        double *ov = out + ((size_t)r * g.Nh + h) * 24;
+        const double *sp = self.f ? self.f + ((size_t)r * self.sites + self.at(i)) * 24 : nullptr;
+        for (int c = 0; c < 12; ++c) {
+            double re = beta * acc[c].re, im = beta * acc[c].im;
+            if (sp) { re += alpha * sp[2 * c]; im += alpha * sp[2 * c + 1]; }
+            ov[2 * c] = re;
+            ov[2 * c + 1] = im;
         }
     }
 }
 
-// out[r][h] = alpha self[r][site] + beta (hop src)[r][site] at the sites of
-// parity par_out (out is a half field); self may be NULL (alpha ignored)
-template <int KIND>
-__global__ void __launch_bounds__(128) k_eo_axpby_hop(EoGeom g, const double *U64, int antip, int par_out,
-                                                      UserField self, double alpha, UserField src, double beta,
-                                                      int nrhs, double *out) {
+// x[r][i] = x_e[r][i >> 1] (even i) or x_o[r][i >> 1] (odd i); w reals per site
+__host__ __device__ __forceinline__ void eo_merge_site(const EoGeom &g, int w, const double *xe, const double *xo,
+                                                       int r, int i, double *x) {
+    int q = i, par = 0;
+    for (int mu = 0; mu < 4; ++mu) { par += q % g.D[mu]; q /= g.D[mu]; }
+    const double *src = ((par & 1) ? xo : xe) + ((size_t)r * g.Nh + (i >> 1)) * w;
+    double *dst = x + ((size_t)r * g.N + i) * w;
+    for (int k = 0; k < w; ++k) dst[k] = src[k];
+}
+
+// ---------------------------------------------------------------- kernels
+__global__ void __launch_bounds__(128) k_eo_axpby_hop(EoGeom g, PackedLinks U, EoOp o, int par_out, UserField self,
+                                                      double alpha, UserField src, double beta, int nrhs,
+                                                      double *out) {
     const long total = (long)nrhs * g.Nh;
     for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
         const int r = (int)(t / g.Nh), h = (int)(t - (long)r * g.Nh);
-        int x[4];
-        const int i = eo_full_site(g, par_out, h, x);
-        if constexpr (KIND == 0) {
-            const double *sb = src.f + (size_t)r * src.sites;
-            double hop = 0.0;
-#pragma unroll
-            for (int mu = 0; mu < 4; ++mu) {
-                hop += sb[src.at(eo_neighbour(g, i, x, mu, 1))];
-                hop += sb[src.at(eo_neighbour(g, i, x, mu, -1))];
-            }
-            double v = beta * hop;
-            if (self.f) v += alpha * self.f[(size_t)r * self.sites + self.at(i)];
-            out[(size_t)r * g.Nh + h] = v;
-        } else {
-            Cx<double> acc[4][3];
-            eo_wilson_hop(g, U64, antip, src, r, i, x, acc);
-            double *o = out + ((size_t)r * g.Nh + h) * 24;
-            const double *sp = self.f ? self.f + ((size_t)r * self.sites + self.at(i)) * 24 : nullptr;
-#pragma unroll
-            for (int c = 0; c < 12; ++c) {
-                double re = beta * acc[c / 3][c % 3].re, im = beta * acc[c / 3][c % 3].im;
-                if (sp) { re += alpha * sp[2 * c]; im += alpha * sp[2 * c + 1]; }
-                o[2 * c] = re;
-                o[2 * c + 1] = im;
-            }
-        }
+        eo_axpby_site(g, U, o, par_out, self, alpha, src, beta, r, h, out);
     }
 }
 
-// x[r][i] = (even i) x_e[r][i >> 1], (odd i) x_o[r][i >> 1]; reals per site: w
 __global__ void k_eo_merge(EoGeom g, int w, const double *xe, const double *xo, int nrhs, double *x) {
     const long total = (long)nrhs * g.N;
     for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
         const int r = (int)(t / g.N), i = (int)(t - (long)r * g.N);
-        int c[4];
-        int q = i;
-        for (int mu = 0; mu < 4; ++mu) { c[mu] = q % g.D[mu]; q /= g.D[mu]; }
-        const int par = (c[0] + c[1] + c[2] + c[3]) & 1;
-        const double *src = (par ? xo : xe) + ((size_t)r * g.Nh + (i >> 1)) * w;
-        double *dst = x + ((size_t)r * g.N + i) * w;
-        for (int k = 0; k < w; ++k) dst[k] = src[k];
+        eo_merge_site(g, w, xe, xo, r, i, x);
     }
 }
 
+// ---------------------------------------------------------------- executors
+// The steps below run the site arithmetic either as kernels on the context
+// stream (DevExec) or as host loops (HostExec); both offer the same calls.
+struct DevExec {
+    pt_ctx *c;
+    EoGeom g;
+    PackedLinks U;
+    EoOp o;
+    double *alloc(size_t n) {
+        double *p = nullptr;
+        if (cudaMallocAsync((void **)&p, n * sizeof(double), c->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return p;
+    }
+    void release(double *p) { cudaFreeAsync(p, c->stream); }
+    int hop(int par_out, UserField self, double alpha, UserField src, double beta, int nrhs, double *out) {
+        const long total = (long)nrhs * g.Nh;
+        const int grid = (int)std::max(1L, std::min((total + 127) / 128, 64L * c->num_sms));
+        k_eo_axpby_hop<<<grid, 128, 0, c->stream>>>(g, U, o, par_out, self, alpha, src, beta, nrhs, out);
+        ++pt_kernel_launch_count;
+        PT_CUDA(cudaGetLastError());
+        return PT_OK;
+    }
+    int merge(int w, const double *xe, const double *xo, int nrhs, double *x) {
+        const long total = (long)nrhs * g.N;
+        const int grid = (int)std::max(1L, std::min((total + 255) / 256, 64L * c->num_sms));
+        k_eo_merge<<<grid, 256, 0, c->stream>>>(g, w, xe, xo, nrhs, x);
+        ++pt_kernel_launch_count;
+        PT_CUDA(cudaGetLastError());
+        return PT_OK;
+    }
+};
+
+struct HostExec {
+    EoGeom g;
+    UserLinks U;
+    EoOp o;
+    std::vector<std::vector<double>> bufs;
+    double *alloc(size_t n) {
+        bufs.emplace_back(n, 0.0);
+        return bufs.back().data();
+    }
+    void release(double *) {}
+    int hop(int par_out, UserField self, double alpha, UserField src, double beta, int nrhs, double *out) {
+        for (int r = 0; r < nrhs; ++r)
+            for (int h = 0; h < g.Nh; ++h) eo_axpby_site(g, U, o, par_out, self, alpha, src, beta, r, h, out);
+        return PT_OK;
+    }
+    int merge(int w, const double *xe, const double *xo, int nrhs, double *x) {
+        for (int r = 0; r < nrhs; ++r)
+            for (int i = 0; i < g.N; ++i) eo_merge_site(g, w, xe, xo, r, i, x);
+        return PT_OK;
+    }
+};
+
+// ---------------------------------------------------------------- the steps
+struct EoParams {
+    int kind;
+    double m2, kappa;
+};
+
+template <class X>
+static int eo_schur_run(X &ex, const EoParams &P, const double *xe, double *ye, int nrhs) {
+    const EoGeom &g = ex.g;
+    const int w = P.kind == 0 ? 1 : 24;
+    double *to = ex.alloc((size_t)nrhs * g.Nh * w);
+    if (!to) {
+        pt_set_error("pt_eo_schur: allocation of the odd half field failed");
+        return PT_ERR_OOM;
+    }
+    const UserField none{nullptr, 1, g.Nh}, xef{xe, 1, g.Nh}, tof{to, 1, g.Nh};
+    int rc = ex.hop(1, none, 0.0, xef, 1.0, nrhs, to);                               // t_o = hop(x_e)
+    if (!rc) {
+        if (P.kind == 0) {
+            const double d = 8.0 + P.m2;
+            rc = ex.hop(0, xef, d, tof, -1.0 / d, nrhs, ye);                         // d x_e - hop(t_o) / d
+        } else {
+            rc = ex.hop(0, xef, 1.0, tof, -P.kappa * P.kappa, nrhs, ye);             // x_e - kappa^2 hop(t_o)
+        }
+    }
+    ex.release(to);
+    return rc;
+}
+
+template <class X>
+static int eo_prepare_run(X &ex, const EoParams &P, const double *b, double *be, int nrhs) {
+    const UserField bf{b, 0, ex.g.N};
+    const double beta = P.kind == 0 ? 1.0 / (8.0 + P.m2) : P.kappa;
+    return ex.hop(0, bf, 1.0, bf, beta, nrhs, be);                                   // b_e + beta hop(b_o)
+}
+
+template <class X>
+static int eo_reconstruct_run(X &ex, const EoParams &P, const double *xe, const double *b, double *x, int nrhs) {
+    const EoGeom &g = ex.g;
+    const int w = P.kind == 0 ? 1 : 24;
+    double *xo = ex.alloc((size_t)nrhs * g.Nh * w);
+    if (!xo) {
+        pt_set_error("pt_eo_reconstruct: allocation of the odd half field failed");
+        return PT_ERR_OOM;
+    }
+    const UserField bf{b, 0, g.N}, xef{xe, 1, g.Nh};
+    int rc;
+    if (P.kind == 0) {
+        const double inv_d = 1.0 / (8.0 + P.m2);
+        rc = ex.hop(1, bf, inv_d, xef, inv_d, nrhs, xo);                             // (b_o + hop(x_e)) / d
+    } else {
+        rc = ex.hop(1, bf, 1.0, xef, P.kappa, nrhs, xo);                             // b_o + kappa hop(x_e)
+    }
+    if (!rc) rc = ex.merge(w, xe, xo, nrhs, x);
+    ex.release(xo);
+    return rc;
+}
+
 // ---------------------------------------------------------------- host side
-static int eo_check(pt_ctx *c, const pt_op *op, int nrhs, const char *fn) {
-    PT_CHECK_ARG(c && op && op->ctx == c, "%s: bad context/operator", fn);
-    PT_CHECK_ARG(nrhs >= 0 && nrhs <= 65535, "%s: nrhs must be in [0, 65535]", fn);
-    for (int mu = 0; mu < 4; ++mu)
-        PT_CHECK_ARG(op->dims[mu] % 2 == 0, "%s: every lattice side must be even (side %d is %d)", fn, mu,
-                     op->dims[mu]);
+static int eo_check_dims(const int dims[4], const char *fn) {
+    PT_CHECK_ARG(dims, "%s: NULL dims", fn);
+    long N = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        PT_CHECK_ARG(dims[mu] >= 2 && dims[mu] % 2 == 0, "%s: every lattice side must be even (side %d is %d)", fn,
+                     mu, dims[mu]);
+        N *= dims[mu];
+    }
+    PT_CHECK_ARG(N <= (1L << 30), "%s: lattice too large", fn);
     return PT_OK;
 }
 
-static int eo_launch(pt_ctx *c, const pt_op *op, const EoGeom &g, int par_out, UserField self, double alpha,
-                     UserField src, double beta, int nrhs, double *out) {
-    const long total = (long)nrhs * g.Nh;
-    const int grid = (int)std::min<long>((total + 127) / 128, 64L * c->num_sms);
-    if (op->kind == 0)
-        k_eo_axpby_hop<0><<<grid, 128, 0, c->stream>>>(g, nullptr, 0, par_out, self, alpha, src, beta, nrhs, out);
-    else
-        k_eo_axpby_hop<1><<<grid, 128, 0, c->stream>>>(g, op->U64, op->antip, par_out, self, alpha, src, beta,
-                                                       nrhs, out);
-    ++pt_kernel_launch_count;
-    PT_CUDA(cudaGetLastError());
+static int eo_dev(pt_ctx *c, const pt_op *op, int nrhs, const char *fn, DevExec *ex, EoParams *P) {
+    PT_CHECK_ARG(c && op && op->ctx == c, "%s: bad context/operator", fn);
+    PT_CHECK_ARG(nrhs >= 0 && nrhs <= 65535, "%s: nrhs must be in [0, 65535]", fn);
+    int rc = eo_check_dims(op->dims, fn);
+    if (rc) return rc;
+    PT_CUDA(cudaSetDevice(c->device));
+    ex->c = c;
+    ex->g = make_eo_geom(op->dims);
+    ex->U = PackedLinks{op->kind == 1 ? op->U64 : nullptr, ex->g.N};
+    ex->o.kind = op->kind;
+    ex->o.antip = op->antip;
+    ex->o.G = make_gammas();
+    P->kind = op->kind;
+    P->m2 = op->m2;
+    P->kappa = op->kappa;
+    return PT_OK;
+}
+
+static int eo_host(int kind, const int dims[4], double m2, double kappa, const double *U_host, int antip,
+                   const char *fn, HostExec *ex, EoParams *P) {
+    PT_CHECK_ARG(kind == 0 || kind == 1, "%s: kind must be 0 (Laplacian) or 1 (Wilson)", fn);
+    PT_CHECK_ARG(kind == 0 || U_host, "%s: Wilson needs links", fn);
+    int rc = eo_check_dims(dims, fn);
+    if (rc) return rc;
+    ex->g = make_eo_geom(dims);
+    ex->U = UserLinks{U_host};
+    ex->o.kind = kind;
+    ex->o.antip = antip ? 1 : 0;
+    ex->o.G = make_gammas();
+    P->kind = kind;
+    P->m2 = m2;
+    P->kappa = kappa;
     return PT_OK;
 }
 
 extern "C" int pt_eo_layout(const int dims[4], int parity, int32_t *site_out, int32_t *nbr_out) {
-    PT_CHECK_ARG(dims && site_out && nbr_out, "pt_eo_layout: NULL argument");
+    PT_CHECK_ARG(site_out && nbr_out, "pt_eo_layout: NULL argument");
     PT_CHECK_ARG(parity == 0 || parity == 1, "pt_eo_layout: parity must be 0 or 1");
-    long N = 1;
-    for (int mu = 0; mu < 4; ++mu) {
-        PT_CHECK_ARG(dims[mu] >= 2 && dims[mu] % 2 == 0, "pt_eo_layout: every side must be even");
-        N *= dims[mu];
-    }
-    PT_CHECK_ARG(N <= (1L << 30), "pt_eo_layout: lattice too large");
+    int rc = eo_check_dims(dims, "pt_eo_layout");
+    if (rc) return rc;
     const EoGeom g = make_eo_geom(dims);
     for (int h = 0; h < g.Nh; ++h) {
         int x[4];
@@ -212,73 +355,43 @@ extern "C" int pt_eo_layout(const int dims[4], int parity, int32_t *site_out, in
 }
 
 extern "C" int pt_eo_schur(pt_ctx *c, const pt_op *op, const double *xe_dev, double *ye_dev, int nrhs) {
-    int rc = eo_check(c, op, nrhs, "pt_eo_schur");
-    if (rc) return rc;
-    if (nrhs == 0) return PT_OK;
+    DevExec ex;
+    EoParams P;
+    int rc = eo_dev(c, op, nrhs, "pt_eo_schur", &ex, &P);
+    if (rc || nrhs == 0) return rc;
     PT_CHECK_ARG(xe_dev && ye_dev && xe_dev != ye_dev, "pt_eo_schur: NULL or aliased fields");
-    PT_CUDA(cudaSetDevice(c->device));
-    const EoGeom g = make_eo_geom(op->dims);
-    const int w = op->kind == 0 ? 1 : 24;
-    double *to = nullptr;
-    if (cudaMallocAsync((void **)&to, sizeof(double) * (size_t)nrhs * g.Nh * w, c->stream) != cudaSuccess) {
-        cudaGetLastError();
-        pt_set_error("pt_eo_schur: device allocation failed");
-        return PT_ERR_OOM;
-    }
-    const UserField none{nullptr, 1, g.Nh}, xe{xe_dev, 1, g.Nh}, tof{to, 1, g.Nh};
-    const double d = 8.0 + op->m2, k2 = op->kappa * op->kappa;
-    rc = eo_launch(c, op, g, 1, none, 0.0, xe, 1.0, nrhs, to);                       // t_o = hop(x_e)
-    if (!rc) {
-        if (op->kind == 0) rc = eo_launch(c, op, g, 0, xe, d, tof, -1.0 / d, nrhs, ye_dev);
-        else rc = eo_launch(c, op, g, 0, xe, 1.0, tof, -k2, nrhs, ye_dev);
-    }
-    cudaFreeAsync(to, c->stream);
-    return rc;
+    return eo_schur_run(ex, P, xe_dev, ye_dev, nrhs);
 }
 
 extern "C" int pt_eo_prepare(pt_ctx *c, const pt_op *op, const double *b_dev, double *be_dev, int nrhs) {
-    int rc = eo_check(c, op, nrhs, "pt_eo_prepare");
-    if (rc) return rc;
-    if (nrhs == 0) return PT_OK;
+    DevExec ex;
+    EoParams P;
+    int rc = eo_dev(c, op, nrhs, "pt_eo_prepare", &ex, &P);
+    if (rc || nrhs == 0) return rc;
     PT_CHECK_ARG(b_dev && be_dev && (const double *)be_dev != b_dev, "pt_eo_prepare: NULL or aliased fields");
-    PT_CUDA(cudaSetDevice(c->device));
-    const EoGeom g = make_eo_geom(op->dims);
-    const UserField b{b_dev, 0, g.N};
-    const double beta = op->kind == 0 ? 1.0 / (8.0 + op->m2) : op->kappa;
-    return eo_launch(c, op, g, 0, b, 1.0, b, beta, nrhs, be_dev);
+    return eo_prepare_run(ex, P, b_dev, be_dev, nrhs);
 }
 
 extern "C" int pt_eo_reconstruct(pt_ctx *c, const pt_op *op, const double *xe_dev, const double *b_dev,
                                  double *x_dev, int nrhs) {
-    int rc = eo_check(c, op, nrhs, "pt_eo_reconstruct");
-    if (rc) return rc;
-    if (nrhs == 0) return PT_OK;
+    DevExec ex;
+    EoParams P;
+    int rc = eo_dev(c, op, nrhs, "pt_eo_reconstruct", &ex, &P);
+    if (rc || nrhs == 0) return rc;
     PT_CHECK_ARG(xe_dev && b_dev && x_dev && x_dev != xe_dev && (const double *)x_dev != b_dev,
                  "pt_eo_reconstruct: NULL or aliased fields");
-    PT_CUDA(cudaSetDevice(c->device));
-    const EoGeom g = make_eo_geom(op->dims);
-    const int w = op->kind == 0 ? 1 : 24;
-    double *xo = nullptr;
-    if (cudaMallocAsync((void **)&xo, sizeof(double) * (size_t)nrhs * g.Nh * w, c->stream) != cudaSuccess) {
-        cudaGetLastError();
-        pt_set_error("pt_eo_reconstruct: device allocation failed");
-        return PT_ERR_OOM;
-    }
-    const UserField b{b_dev, 0, g.N}, xe{xe_dev, 1, g.Nh};
-    if (op->kind == 0) {
-        const double inv_d = 1.0 / (8.0 + op->m2);
-        rc = eo_launch(c, op, g, 1, b, inv_d, xe, inv_d, nrhs, xo);
-    } else {
-        rc = eo_launch(c, op, g, 1, b, 1.0, xe, op->kappa, nrhs, xo);
-    }
-    if (!rc) {
-        const long total = (long)nrhs * g.N;
-        const int grid = (int)std::min<long>((total + 255) / 256, 64L * c->num_sms);
-        k_eo_merge<<<grid, 256, 0, c->stream>>>(g, w, xe_dev, xo, nrhs, x_dev);
-        ++pt_kernel_launch_count;
-        const cudaError_t ce = cudaGetLastError();
-        if (ce != cudaSuccess) rc = pt_cuda_fail(ce, "k_eo_merge", __FILE__, __LINE__);
-    }
-    cudaFreeAsync(xo, c->stream);
-    return rc;
+    return eo_reconstruct_run(ex, P, xe_dev, b_dev, x_dev, nrhs);
+}
+
+extern "C" int pt_eo_host(int kind, const int dims[4], double m2, double kappa, const double *U_host, int antip,
+                          int step, const double *in1, const double *in2, double *out, int nrhs) {
+    HostExec ex;
+    EoParams P;
+    int rc = eo_host(kind, dims, m2, kappa, U_host, antip, "pt_eo_host", &ex, &P);
+    if (rc) return rc;
+    PT_CHECK_ARG(nrhs >= 0 && in1 && out && (step != 2 || in2), "pt_eo_host: bad argument");
+    if (step == 0) return eo_schur_run(ex, P, in1, out, nrhs);
+    if (step == 1) return eo_prepare_run(ex, P, in1, out, nrhs);
+    PT_CHECK_ARG(step == 2, "pt_eo_host: step must be 0 (Schur), 1 (prepare) or 2 (reconstruct)");
+    return eo_reconstruct_run(ex, P, in1, in2, out, nrhs);
 }

@@ -100,6 +100,7 @@ _SIGS = {
     "pt_hermitian_eig": ([_I, _P, _I, _P, _P], _I),
     "pt_singular_triplets": ([_P, _P, _I, _I, _I, _P, _P, _P, _P], _I),
     "pt_eo_layout": ([ctypes.POINTER(_I), _I, _P, _P], _I),
+    "pt_eo_host": ([_I, ctypes.POINTER(_I), _D, _D, _P, _I, _I, _P, _P, _P, _I], _I),
     "pt_eo_schur": ([_P, _P, _P, _P, _I], _I),
     "pt_eo_prepare": ([_P, _P, _P, _P, _I], _I),
     "pt_eo_reconstruct": ([_P, _P, _P, _P, _P, _I], _I),
@@ -540,6 +541,26 @@ def eo_layout(dims, parity):
     nbr = np.zeros((Nh, 8), dtype=np.int32)
     _check(lib().pt_eo_layout(_ints(dims), int(parity), _np_ptr(site), _np_ptr(nbr)))
     return site, nbr
+
+
+def eo_host(kind, dims, step, in1, in2=None, m2=0.0, kappa=0.0, U=None, antiperiodic_t=True):
+    """pt_eo_host (host only): step 0 S in1, 1 b'_e from in1, 2 full x from
+    (in1 = x_e, in2 = b); numpy arrays [nrhs, sites] (Laplacian) or
+    [nrhs, sites, 4, 3] complex (Wilson)."""
+    N = int(np.prod(dims))
+    dt = np.float64 if kind == 0 else np.complex128
+    tail = () if kind == 0 else (4, 3)
+    in1 = np.ascontiguousarray(np.asarray(in1, dtype=dt))
+    nrhs = in1.shape[0]
+    out_sites = N if step == 2 else N // 2
+    out = np.zeros((nrhs, out_sites) + tail, dtype=dt)
+    U = None if U is None else np.ascontiguousarray(np.asarray(U, dtype=np.complex128))
+    if in2 is not None:
+        in2 = np.ascontiguousarray(np.asarray(in2, dtype=dt))
+    _check(lib().pt_eo_host(int(kind), _ints(dims), float(m2), float(kappa),
+                            _np_ptr(U) if U is not None else None, 1 if antiperiodic_t else 0, int(step),
+                            _np_ptr(in1), _np_ptr(in2) if in2 is not None else None, _np_ptr(out), int(nrhs)))
+    return out
 
 
 def _eo_field(op, x, sites, name):

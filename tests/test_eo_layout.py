@@ -40,3 +40,55 @@ def test_odd_sides_refused(ptlib):
         ptlib.eo_layout([4, 3, 4, 4], 0)
     with pytest.raises(ptlib.PtraceError):
         ptlib.eo_layout([4, 4, 4, 4], 2)
+
+
+def test_laplacian_steps_on_the_host_match_the_oracle(ptlib):
+    """The library's even-odd site arithmetic and sequence of steps (run on
+    the host): S, b'_e and the reconstruction against the oracle, and the
+    composed even solve reproduces A^{-1} b."""
+    from oracle import deflation as D
+    import oracle.estimator as OE
+    dims, m2 = [4, 2, 6, 2], 0.3
+    N = int(np.prod(dims))
+    eo = EO.LaplacianEO(dims, m2)
+    rng = np.random.default_rng(1)
+    xe = rng.standard_normal((2, N // 2))
+    b = rng.standard_normal((2, N))
+    ye = ptlib.eo_host(0, dims, 0, xe, m2=m2)
+    be = ptlib.eo_host(0, dims, 1, b, m2=m2)
+    x = ptlib.eo_host(0, dims, 2, xe, b, m2=m2)
+    for r in range(2):
+        assert np.allclose(ye[r], eo.schur(xe[r]), rtol=0, atol=1e-13)
+        assert np.allclose(be[r], eo.rhs(b[r]), rtol=0, atol=1e-13)
+        assert np.allclose(x[r], eo.reconstruct(xe[r], b[r]), rtol=0, atol=1e-13)
+    S = ptlib.eo_host(0, dims, 0, np.eye(N // 2), m2=m2).T              # column j = S e_j
+    x_e = np.linalg.solve(S, be[0])
+    xs = ptlib.eo_host(0, dims, 2, x_e[None], b[:1], m2=m2)[0]
+    assert np.allclose(xs, np.linalg.solve(D.dense_matrix(OE.Laplacian(dims, m2)), b[0]), atol=1e-12)
+
+
+@pytest.mark.parametrize("dims,ap", [([2, 2, 4, 2], True), ([4, 2, 2, 6], False)])
+def test_wilson_steps_on_the_host_match_the_oracle(ptlib, dims, ap):
+    from oracle import deflation as D
+    import oracle.estimator as OE
+    from paper_2106_01275_gb300 import inputs
+    kappa, N = 0.13, int(np.prod(dims))
+    U = inputs.gauge_links(dims, 31, eps=0.7)
+    eo = EO.WilsonEO(dims, U, kappa, ap)
+    rng = np.random.default_rng(2)
+    xe = rng.standard_normal((2, N // 2, 4, 3)) + 1j * rng.standard_normal((2, N // 2, 4, 3))
+    b = rng.standard_normal((2, N, 4, 3)) + 1j * rng.standard_normal((2, N, 4, 3))
+    kw = dict(kappa=kappa, U=U, antiperiodic_t=ap)
+    ye = ptlib.eo_host(1, dims, 0, xe, **kw)
+    be = ptlib.eo_host(1, dims, 1, b, **kw)
+    x = ptlib.eo_host(1, dims, 2, xe, b, **kw)
+    for r in range(2):
+        assert np.allclose(ye[r].reshape(-1, 12), eo.schur(xe[r].reshape(-1, 12)), rtol=0, atol=1e-13)
+        assert np.allclose(be[r].reshape(-1, 12), eo.rhs(b[r]), rtol=0, atol=1e-13)
+        assert np.allclose(x[r].reshape(-1, 12), eo.reconstruct(xe[r].reshape(-1, 12), b[r]), rtol=0, atol=1e-13)
+    n_e = 6 * N
+    S = ptlib.eo_host(1, dims, 0, np.eye(n_e).reshape(n_e, N // 2, 4, 3), **kw).reshape(n_e, n_e).T
+    x_e = np.linalg.solve(S, be[0].reshape(-1)).reshape(1, N // 2, 4, 3)
+    xs = ptlib.eo_host(1, dims, 2, x_e, b[:1], **kw)[0]
+    A = D.dense_matrix(OE.Wilson(dims, U, kappa, ap))
+    assert np.allclose(xs.reshape(-1), np.linalg.solve(A, b[0].reshape(-1)), atol=1e-11)
