@@ -447,26 +447,44 @@ PT_API int pt_singular_triplets(pt_ctx *ctx, const pt_op *op, int n_ev, int bloc
  * [N/2][8]) = half-field index (in the other parity) of x + mu / x - mu. */
 PT_API int pt_eo_layout(const int dims[4], int parity, int32_t *site_out, int32_t *nbr_out);
 
-/* ye = S xe for nrhs even half fields (xe, ye must not overlap; a temporary
- * stream-ordered odd half field per right-hand side). */
-PT_API int pt_eo_schur(pt_ctx *ctx, const pt_op *op, const double *xe_dev, double *ye_dev, int nrhs);
+/* Clover Wilson operators (A_c = A_W + C, see pt_clover_blocks) enter
+ * through their diagonal blocks: Aee = 1 + C on the even sites and
+ * Aoo_inv = (1 + C)^{-1} on the odd ones, complex128 [N/2][12][12] by
+ * half-field entry (device; pt_eo_clover_blocks makes both), or NULL for the
+ * plain operators (Laplacian: must be NULL).  Then
+ *   S = A_ee - kappa^2 D_eo A_oo^{-1} D_oe,  b'_e = b_e + kappa D_eo A_oo^{-1} b_o,
+ *   x_o = A_oo^{-1} (b_o + kappa D_oe x_e).
+ *
+ * pt_eo_schur: ye = S xe for nrhs even half fields (xe, ye must not overlap;
+ * temporary stream-ordered half fields). */
+PT_API int pt_eo_schur(pt_ctx *ctx, const pt_op *op, const double *Aee_dev, const double *Aoo_inv_dev,
+                       const double *xe_dev, double *ye_dev, int nrhs);
 
 /* be = b'_e (even half fields) from full fields b. */
-PT_API int pt_eo_prepare(pt_ctx *ctx, const pt_op *op, const double *b_dev, double *be_dev, int nrhs);
+PT_API int pt_eo_prepare(pt_ctx *ctx, const pt_op *op, const double *Aoo_inv_dev, const double *b_dev,
+                         double *be_dev, int nrhs);
 
 /* x (full fields) = x_e on the even sites and x_o = A_oo^{-1}(b_o - A_oe x_e)
- * on the odd ones, from even half fields xe and full fields b (a temporary
- * stream-ordered odd half field per right-hand side). */
-PT_API int pt_eo_reconstruct(pt_ctx *ctx, const pt_op *op, const double *xe_dev, const double *b_dev,
-                             double *x_dev, int nrhs);
+ * on the odd ones, from even half fields xe and full fields b (temporary
+ * stream-ordered half fields). */
+PT_API int pt_eo_reconstruct(pt_ctx *ctx, const pt_op *op, const double *Aoo_inv_dev, const double *xe_dev,
+                             const double *b_dev, double *x_dev, int nrhs);
+
+/* The clover diagonal blocks for the calls above, from a Wilson operator's
+ * links: Aee_dev = 1 + C_ee, Aoo_inv_dev = (1 + C_oo)^{-1} (device, written;
+ * temporary stream-ordered buffers; PT_ERR_NUMERIC if a block is singular).
+ * Synchronises. */
+PT_API int pt_eo_clover_blocks(pt_ctx *ctx, const pt_op *op, double csw, double *Aee_dev, double *Aoo_inv_dev);
 
 /* The same three steps on the host, with the device entries' site arithmetic
  * and sequence of steps (no GPU needed): kind 0 (Laplacian, m2) or 1 (Wilson,
- * kappa, links U_host in the user layout, antip); step 0: out = S in1 (even
- * half fields), 1: out = b'_e from full fields in1, 2: out = full x from
- * even half fields in1 and full fields in2.  Host buffers. */
+ * kappa, links U_host in the user layout, antip, optional clover blocks Aee,
+ * Aoo_inv as above); step 0: out = S in1 (even half fields), 1: out = b'_e
+ * from full fields in1, 2: out = full x from even half fields in1 and full
+ * fields in2.  Host buffers. */
 PT_API int pt_eo_host(int kind, const int dims[4], double m2, double kappa, const double *U_host, int antip,
-                      int step, const double *in1, const double *in2, double *out, int nrhs);
+                      const double *Aee, const double *Aoo_inv, int step, const double *in1, const double *in2,
+                      double *out, int nrhs);
 
 /* ---------------------------------------------------------------- clover */
 

@@ -77,6 +77,23 @@ struct EoOp {
     GammaTab G;
 };
 
+// per-site 12 x 12 blocks of one parity (entry h of a half field), e.g. the
+// clover diagonal A_ee or the inverses A_oo^{-1}: out = B(h) in(site)
+__host__ __device__ __forceinline__ void eo_block_site(const EoGeom &g, const double *B, int par_out,
+                                                       const UserField &in, int r, int h, double *out) {
+    int x[4];
+    const int i = eo_full_site(g, par_out, h, x);
+    const double *b = B + (size_t)h * 288, *v = in.f + ((size_t)r * in.sites + in.at(i)) * 24;
+    double *o = out + ((size_t)r * g.Nh + h) * 24;
+    for (int row = 0; row < 12; ++row) {
+        zd acc = {0.0, 0.0};
+        for (int c = 0; c < 12; ++c)
+            acc = zadd(acc, zmulc(zd{b[(row * 12 + c) * 2], b[(row * 12 + c) * 2 + 1]}, zd{v[2 * c], v[2 * c + 1]}));
+        o[2 * row] = acc.re;
+        o[2 * row + 1] = acc.im;
+    }
+}
+
 // (H psi)(x) of the Wilson hopping term at storage index i, from its
 // definition: sum over mu of (1 - g_mu) U_mu(x) psi(x + mu) and
 // (1 + g_mu) U_mu(x - mu)^H psi(x - mu), times -1 on the hops that cross the
@@ -165,6 +182,14 @@ __global__ void __launch_bounds__(128) k_eo_axpby_hop(EoGeom g, PackedLinks U, E
     }
 }
 
+__global__ void k_eo_block(EoGeom g, const double *B, int par_out, UserField in, int nrhs, double *out) {
+    const long total = (long)nrhs * g.Nh;
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(t / g.Nh), h = (int)(t - (long)r * g.Nh);
+        eo_block_site(g, B, par_out, in, r, h, out);
+    }
+}
+
 __global__ void k_eo_merge(EoGeom g, int w, const double *xe, const double *xo, int nrhs, double *x) {
     const long total = (long)nrhs * g.N;
     for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
@@ -198,6 +223,14 @@ struct DevExec {
         PT_CUDA(cudaGetLastError());
         return PT_OK;
     }
+    int blk(int par_out, const double *B, UserField in, int nrhs, double *out) {
+        const long total = (long)nrhs * g.Nh;
+        const int grid = (int)std::max(1L, std::min((total + 127) / 128, 64L * c->num_sms));
+        k_eo_block<<<grid, 128, 0, c->stream>>>(g, B, par_out, in, nrhs, out);
+        ++pt_kernel_launch_count;
+        PT_CUDA(cudaGetLastError());
+        return PT_OK;
+    }
     int merge(int w, const double *xe, const double *xo, int nrhs, double *x) {
         const long total = (long)nrhs * g.N;
         const int grid = (int)std::max(1L, std::min((total + 255) / 256, 64L * c->num_sms));
@@ -223,6 +256,11 @@ struct HostExec {
             for (int h = 0; h < g.Nh; ++h) eo_axpby_site(g, U, o, par_out, self, alpha, src, beta, r, h, out);
         return PT_OK;
     }
+    int blk(int par_out, const double *B, UserField in, int nrhs, double *out) {
+        for (int r = 0; r < nrhs; ++r)
+            for (int h = 0; h < g.Nh; ++h) eo_block_site(g, B, par_out, in, r, h, out);
+        return PT_OK;
+    }
     int merge(int w, const double *xe, const double *xo, int nrhs, double *x) {
         for (int r = 0; r < nrhs; ++r)
             for (int i = 0; i < g.N; ++i) eo_merge_site(g, w, xe, xo, r, i, x);
@@ -231,29 +269,45 @@ struct HostExec {
 };
 
 // ---------------------------------------------------------------- the steps
+// Aee, Aoo_inv: the clover Wilson operator's diagonal blocks 1 + C on the even
+// sites and the inverses of those on the odd sites ([N/2][12][12] complex, by
+// half-field entry), or NULL for the plain operators (A_ee = A_oo = d):
+//   S x_e = A_ee x_e - kappa^2 D_eo A_oo^{-1} D_oe x_e,
+//   b'_e = b_e + kappa D_eo A_oo^{-1} b_o,  x_o = A_oo^{-1} (b_o + kappa D_oe x_e).
 struct EoParams {
     int kind;
     double m2, kappa;
+    const double *Aee, *Aoo_inv;
 };
 
 template <class X>
 static int eo_schur_run(X &ex, const EoParams &P, const double *xe, double *ye, int nrhs) {
     const EoGeom &g = ex.g;
     const int w = P.kind == 0 ? 1 : 24;
-    double *to = ex.alloc((size_t)nrhs * g.Nh * w);
+    const size_t half = (size_t)nrhs * g.Nh * w;
+    double *to = ex.alloc(half * (P.Aoo_inv ? 2 : 1) + (P.Aee ? half : 0));
     if (!to) {
-        pt_set_error("pt_eo_schur: allocation of the odd half field failed");
+        pt_set_error("pt_eo_schur: allocation of the work fields failed");
         return PT_ERR_OOM;
     }
-    const UserField none{nullptr, 1, g.Nh}, xef{xe, 1, g.Nh}, tof{to, 1, g.Nh};
+    const UserField none{nullptr, 1, g.Nh}, xef{xe, 1, g.Nh};
     int rc = ex.hop(1, none, 0.0, xef, 1.0, nrhs, to);                               // t_o = hop(x_e)
-    if (!rc) {
-        if (P.kind == 0) {
-            const double d = 8.0 + P.m2;
-            rc = ex.hop(0, xef, d, tof, -1.0 / d, nrhs, ye);                         // d x_e - hop(t_o) / d
-        } else {
-            rc = ex.hop(0, xef, 1.0, tof, -P.kappa * P.kappa, nrhs, ye);             // x_e - kappa^2 hop(t_o)
+    if (!rc && P.kind == 0) {
+        const double d = 8.0 + P.m2;
+        rc = ex.hop(0, xef, d, UserField{to, 1, g.Nh}, -1.0 / d, nrhs, ye);          // d x_e - hop(t_o) / d
+    } else if (!rc) {
+        double *uo = to, *we = nullptr;
+        if (P.Aoo_inv) {
+            uo = to + half;
+            rc = ex.blk(1, P.Aoo_inv, UserField{to, 1, g.Nh}, nrhs, uo);             // A_oo^{-1} t_o
         }
+        UserField self = xef;
+        if (!rc && P.Aee) {
+            we = to + half * (P.Aoo_inv ? 2 : 1);
+            rc = ex.blk(0, P.Aee, xef, nrhs, we);                                    // A_ee x_e
+            self = UserField{we, 1, g.Nh};
+        }
+        if (!rc) rc = ex.hop(0, self, 1.0, UserField{uo, 1, g.Nh}, -P.kappa * P.kappa, nrhs, ye);
     }
     ex.release(to);
     return rc;
@@ -261,30 +315,46 @@ static int eo_schur_run(X &ex, const EoParams &P, const double *xe, double *ye, 
 
 template <class X>
 static int eo_prepare_run(X &ex, const EoParams &P, const double *b, double *be, int nrhs) {
-    const UserField bf{b, 0, ex.g.N};
-    const double beta = P.kind == 0 ? 1.0 / (8.0 + P.m2) : P.kappa;
-    return ex.hop(0, bf, 1.0, bf, beta, nrhs, be);                                   // b_e + beta hop(b_o)
+    const EoGeom &g = ex.g;
+    const UserField bf{b, 0, g.N};
+    if (P.kind == 0) return ex.hop(0, bf, 1.0, bf, 1.0 / (8.0 + P.m2), nrhs, be);    // b_e + hop(b_o) / d
+    if (!P.Aoo_inv) return ex.hop(0, bf, 1.0, bf, P.kappa, nrhs, be);                // b_e + kappa hop(b_o)
+    double *uo = ex.alloc((size_t)nrhs * g.Nh * 24);
+    if (!uo) {
+        pt_set_error("pt_eo_prepare: allocation of the odd half field failed");
+        return PT_ERR_OOM;
+    }
+    int rc = ex.blk(1, P.Aoo_inv, bf, nrhs, uo);                                     // A_oo^{-1} b_o
+    if (!rc) rc = ex.hop(0, bf, 1.0, UserField{uo, 1, g.Nh}, P.kappa, nrhs, be);
+    ex.release(uo);
+    return rc;
 }
 
 template <class X>
 static int eo_reconstruct_run(X &ex, const EoParams &P, const double *xe, const double *b, double *x, int nrhs) {
     const EoGeom &g = ex.g;
     const int w = P.kind == 0 ? 1 : 24;
-    double *xo = ex.alloc((size_t)nrhs * g.Nh * w);
-    if (!xo) {
+    const size_t half = (size_t)nrhs * g.Nh * w;
+    double *vo = ex.alloc(half * (P.Aoo_inv ? 2 : 1));
+    if (!vo) {
         pt_set_error("pt_eo_reconstruct: allocation of the odd half field failed");
         return PT_ERR_OOM;
     }
     const UserField bf{b, 0, g.N}, xef{xe, 1, g.Nh};
     int rc;
+    double *xo = vo;
     if (P.kind == 0) {
         const double inv_d = 1.0 / (8.0 + P.m2);
-        rc = ex.hop(1, bf, inv_d, xef, inv_d, nrhs, xo);                             // (b_o + hop(x_e)) / d
+        rc = ex.hop(1, bf, inv_d, xef, inv_d, nrhs, vo);                             // (b_o + hop(x_e)) / d
     } else {
-        rc = ex.hop(1, bf, 1.0, xef, P.kappa, nrhs, xo);                             // b_o + kappa hop(x_e)
+        rc = ex.hop(1, bf, 1.0, xef, P.kappa, nrhs, vo);                             // b_o + kappa hop(x_e)
+        if (!rc && P.Aoo_inv) {
+            xo = vo + half;
+            rc = ex.blk(1, P.Aoo_inv, UserField{vo, 1, g.Nh}, nrhs, xo);             // A_oo^{-1} (...)
+        }
     }
     if (!rc) rc = ex.merge(w, xe, xo, nrhs, x);
-    ex.release(xo);
+    ex.release(vo);
     return rc;
 }
 
@@ -316,6 +386,7 @@ static int eo_dev(pt_ctx *c, const pt_op *op, int nrhs, const char *fn, DevExec 
     P->kind = op->kind;
     P->m2 = op->m2;
     P->kappa = op->kappa;
+    P->Aee = P->Aoo_inv = nullptr;
     return PT_OK;
 }
 
@@ -333,6 +404,7 @@ static int eo_host(int kind, const int dims[4], double m2, double kappa, const d
     P->kind = kind;
     P->m2 = m2;
     P->kappa = kappa;
+    P->Aee = P->Aoo_inv = nullptr;
     return PT_OK;
 }
 
@@ -354,40 +426,101 @@ extern "C" int pt_eo_layout(const int dims[4], int parity, int32_t *site_out, in
     return PT_OK;
 }
 
-extern "C" int pt_eo_schur(pt_ctx *c, const pt_op *op, const double *xe_dev, double *ye_dev, int nrhs) {
+static int eo_blocks(EoParams *P, const double *Aee, const double *Aoo_inv, const char *fn) {
+    PT_CHECK_ARG(P->kind == 1 || (!Aee && !Aoo_inv), "%s: site blocks apply to the Wilson operator only", fn);
+    P->Aee = Aee;
+    P->Aoo_inv = Aoo_inv;
+    return PT_OK;
+}
+
+extern "C" int pt_eo_schur(pt_ctx *c, const pt_op *op, const double *Aee_dev, const double *Aoo_inv_dev,
+                           const double *xe_dev, double *ye_dev, int nrhs) {
     DevExec ex;
     EoParams P;
     int rc = eo_dev(c, op, nrhs, "pt_eo_schur", &ex, &P);
+    if (!rc) rc = eo_blocks(&P, Aee_dev, Aoo_inv_dev, "pt_eo_schur");
     if (rc || nrhs == 0) return rc;
     PT_CHECK_ARG(xe_dev && ye_dev && xe_dev != ye_dev, "pt_eo_schur: NULL or aliased fields");
     return eo_schur_run(ex, P, xe_dev, ye_dev, nrhs);
 }
 
-extern "C" int pt_eo_prepare(pt_ctx *c, const pt_op *op, const double *b_dev, double *be_dev, int nrhs) {
+extern "C" int pt_eo_prepare(pt_ctx *c, const pt_op *op, const double *Aoo_inv_dev, const double *b_dev,
+                             double *be_dev, int nrhs) {
     DevExec ex;
     EoParams P;
     int rc = eo_dev(c, op, nrhs, "pt_eo_prepare", &ex, &P);
+    if (!rc) rc = eo_blocks(&P, nullptr, Aoo_inv_dev, "pt_eo_prepare");
     if (rc || nrhs == 0) return rc;
     PT_CHECK_ARG(b_dev && be_dev && (const double *)be_dev != b_dev, "pt_eo_prepare: NULL or aliased fields");
     return eo_prepare_run(ex, P, b_dev, be_dev, nrhs);
 }
 
-extern "C" int pt_eo_reconstruct(pt_ctx *c, const pt_op *op, const double *xe_dev, const double *b_dev,
-                                 double *x_dev, int nrhs) {
+extern "C" int pt_eo_reconstruct(pt_ctx *c, const pt_op *op, const double *Aoo_inv_dev, const double *xe_dev,
+                                 const double *b_dev, double *x_dev, int nrhs) {
     DevExec ex;
     EoParams P;
     int rc = eo_dev(c, op, nrhs, "pt_eo_reconstruct", &ex, &P);
+    if (!rc) rc = eo_blocks(&P, nullptr, Aoo_inv_dev, "pt_eo_reconstruct");
     if (rc || nrhs == 0) return rc;
     PT_CHECK_ARG(xe_dev && b_dev && x_dev && x_dev != xe_dev && (const double *)x_dev != b_dev,
                  "pt_eo_reconstruct: NULL or aliased fields");
     return eo_reconstruct_run(ex, P, xe_dev, b_dev, x_dev, nrhs);
 }
 
+// A_ee = 1 + C on the even sites and A_oo^{-1} = (1 + C)^{-1} on the odd ones,
+// by half-field entry, from full-lattice blocks C [N][12][12]
+__global__ void k_eo_split_blocks(EoGeom g, const double *C, double *Aee, double *Aoo) {
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.Nh; h += gridDim.x * blockDim.x) {
+        for (int par = 0; par < 2; ++par) {
+            int x[4];
+            const int i = eo_full_site(g, par, h, x);
+            const double *src = C + (size_t)i * 288;
+            double *dst = (par ? Aoo : Aee) + (size_t)h * 288;
+            for (int e = 0; e < 288; ++e) dst[e] = src[e] + ((e & 1) == 0 && (e >> 1) % 13 == 0 && par == 0 ? 1.0 : 0.0);
+        }
+    }
+}
+
+extern "C" int pt_eo_clover_blocks(pt_ctx *c, const pt_op *op, double csw, double *Aee_dev, double *Aoo_inv_dev) {
+    PT_CHECK_ARG(c && op && op->ctx == c && op->kind == 1, "pt_eo_clover_blocks: a Wilson operator is required");
+    PT_CHECK_ARG(Aee_dev && Aoo_inv_dev && Aee_dev != Aoo_inv_dev, "pt_eo_clover_blocks: NULL or aliased output");
+    int rc = eo_check_dims(op->dims, "pt_eo_clover_blocks");
+    if (rc) return rc;
+    PT_CUDA(cudaSetDevice(c->device));
+    const EoGeom g = make_eo_geom(op->dims);
+    double *C = nullptr;
+    if (cudaMallocAsync((void **)&C, sizeof(double) * 288 * (size_t)g.N, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        pt_set_error("pt_eo_clover_blocks: device allocation failed");
+        return PT_ERR_OOM;
+    }
+    rc = pt_clover_blocks(c, op, csw, C);
+    double *tmp_o = nullptr;
+    if (!rc && cudaMallocAsync((void **)&tmp_o, sizeof(double) * 288 * (size_t)g.Nh, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        pt_set_error("pt_eo_clover_blocks: device allocation failed");
+        rc = PT_ERR_OOM;
+    }
+    if (!rc) {
+        const int grid = std::max(1, std::min((g.Nh + 127) / 128, 16 * c->num_sms));
+        k_eo_split_blocks<<<grid, 128, 0, c->stream>>>(g, C, Aee_dev, tmp_o);
+        ++pt_kernel_launch_count;
+        const cudaError_t ce = cudaGetLastError();
+        if (ce != cudaSuccess) rc = pt_cuda_fail(ce, "k_eo_split_blocks", __FILE__, __LINE__);
+    }
+    if (!rc) rc = pt_site_blocks_invert(c, g.Nh, tmp_o, 1.0, Aoo_inv_dev);          // (1 + C_oo)^{-1}
+    if (tmp_o) cudaFreeAsync(tmp_o, c->stream);
+    cudaFreeAsync(C, c->stream);
+    return rc;
+}
+
 extern "C" int pt_eo_host(int kind, const int dims[4], double m2, double kappa, const double *U_host, int antip,
-                          int step, const double *in1, const double *in2, double *out, int nrhs) {
+                          const double *Aee, const double *Aoo_inv, int step, const double *in1, const double *in2,
+                          double *out, int nrhs) {
     HostExec ex;
     EoParams P;
     int rc = eo_host(kind, dims, m2, kappa, U_host, antip, "pt_eo_host", &ex, &P);
+    if (!rc) rc = eo_blocks(&P, Aee, Aoo_inv, "pt_eo_host");
     if (rc) return rc;
     PT_CHECK_ARG(nrhs >= 0 && in1 && out && (step != 2 || in2), "pt_eo_host: bad argument");
     if (step == 0) return eo_schur_run(ex, P, in1, out, nrhs);

@@ -100,10 +100,11 @@ _SIGS = {
     "pt_hermitian_eig": ([_I, _P, _I, _P, _P], _I),
     "pt_singular_triplets": ([_P, _P, _I, _I, _I, _P, _P, _P, _P], _I),
     "pt_eo_layout": ([ctypes.POINTER(_I), _I, _P, _P], _I),
-    "pt_eo_host": ([_I, ctypes.POINTER(_I), _D, _D, _P, _I, _I, _P, _P, _P, _I], _I),
-    "pt_eo_schur": ([_P, _P, _P, _P, _I], _I),
-    "pt_eo_prepare": ([_P, _P, _P, _P, _I], _I),
-    "pt_eo_reconstruct": ([_P, _P, _P, _P, _P, _I], _I),
+    "pt_eo_host": ([_I, ctypes.POINTER(_I), _D, _D, _P, _I, _P, _P, _I, _P, _P, _P, _I], _I),
+    "pt_eo_schur": ([_P, _P, _P, _P, _P, _P, _I], _I),
+    "pt_eo_prepare": ([_P, _P, _P, _P, _P, _I], _I),
+    "pt_eo_reconstruct": ([_P, _P, _P, _P, _P, _P, _I], _I),
+    "pt_eo_clover_blocks": ([_P, _P, _D, _P, _P], _I),
     "pt_clover_blocks_host": ([ctypes.POINTER(_I), _P, _D, _D, _P], _I),
     "pt_clover_blocks": ([_P, _P, _D, _P], _I),
     "pt_site_blocks_apply": ([_P, _I, _P, _P, _D, _P, _I], _I),
@@ -543,10 +544,11 @@ def eo_layout(dims, parity):
     return site, nbr
 
 
-def eo_host(kind, dims, step, in1, in2=None, m2=0.0, kappa=0.0, U=None, antiperiodic_t=True):
+def eo_host(kind, dims, step, in1, in2=None, m2=0.0, kappa=0.0, U=None, antiperiodic_t=True, blocks=None):
     """pt_eo_host (host only): step 0 S in1, 1 b'_e from in1, 2 full x from
     (in1 = x_e, in2 = b); numpy arrays [nrhs, sites] (Laplacian) or
-    [nrhs, sites, 4, 3] complex (Wilson)."""
+    [nrhs, sites, 4, 3] complex (Wilson); blocks: None or the clover
+    (Aee, Aoo_inv), numpy complex128 [N/2, 12, 12] each."""
     N = int(np.prod(dims))
     dt = np.float64 if kind == 0 else np.complex128
     tail = () if kind == 0 else (4, 3)
@@ -557,8 +559,14 @@ def eo_host(kind, dims, step, in1, in2=None, m2=0.0, kappa=0.0, U=None, antiperi
     U = None if U is None else np.ascontiguousarray(np.asarray(U, dtype=np.complex128))
     if in2 is not None:
         in2 = np.ascontiguousarray(np.asarray(in2, dtype=dt))
+    Aee = Aoo = None
+    if blocks is not None:
+        Aee = np.ascontiguousarray(np.asarray(blocks[0], dtype=np.complex128)).reshape(N // 2, 12, 12)
+        Aoo = np.ascontiguousarray(np.asarray(blocks[1], dtype=np.complex128)).reshape(N // 2, 12, 12)
     _check(lib().pt_eo_host(int(kind), _ints(dims), float(m2), float(kappa),
-                            _np_ptr(U) if U is not None else None, 1 if antiperiodic_t else 0, int(step),
+                            _np_ptr(U) if U is not None else None, 1 if antiperiodic_t else 0,
+                            _np_ptr(Aee) if Aee is not None else None, _np_ptr(Aoo) if Aoo is not None else None,
+                            int(step),
                             _np_ptr(in1), _np_ptr(in2) if in2 is not None else None, _np_ptr(out), int(nrhs)))
     return out
 
@@ -577,25 +585,52 @@ def _eo_ptr(t):
     return _ptr(torch.view_as_real(t) if t.is_complex() else t)
 
 
-def eo_schur(op, xe):
-    """pt_eo_schur: S xe for even half fields xe [nrhs, N/2(, 4, 3)]."""
+def _eo_blocks(op, blocks):
+    """(Aee, Aoo_inv) device pointers, or NULLs"""
+    import torch
+    if blocks is None:
+        return _ptr(None), _ptr(None)
+    out = []
+    for B in blocks:
+        if B.dtype != torch.complex128 or not B.is_cuda or tuple(B.shape) != (op.N // 2, 12, 12) or \
+                not B.is_contiguous():
+            raise ValueError("blocks: contiguous torch complex128 [N/2, 12, 12] on the device")
+        out.append(_ptr(torch.view_as_real(B)))
+    return out[0], out[1]
+
+
+def eo_clover_blocks(op, csw):
+    """pt_eo_clover_blocks: (Aee, Aoo_inv), torch complex128 [N/2, 12, 12] on the device."""
+    import torch
+    Aee = torch.empty((op.N // 2, 12, 12), dtype=torch.complex128, device="cuda:%d" % op.ctx.device)
+    Aoo = torch.empty_like(Aee)
+    _check(lib().pt_eo_clover_blocks(op.ctx.handle, op._h, float(csw), _ptr(torch.view_as_real(Aee)),
+                                     _ptr(torch.view_as_real(Aoo))))
+    return Aee, Aoo
+
+
+def eo_schur(op, xe, blocks=None):
+    """pt_eo_schur: S xe for even half fields xe [nrhs, N/2(, 4, 3)]; blocks:
+    the clover (Aee, Aoo_inv) or None."""
     import torch
     xe = _eo_field(op, xe, op.N // 2, "xe")
     ye = torch.empty_like(xe)
-    _check(lib().pt_eo_schur(op.ctx.handle, op._h, _eo_ptr(xe), _eo_ptr(ye), int(xe.shape[0])))
+    ae, ao = _eo_blocks(op, blocks)
+    _check(lib().pt_eo_schur(op.ctx.handle, op._h, ae, ao, _eo_ptr(xe), _eo_ptr(ye), int(xe.shape[0])))
     return ye
 
 
-def eo_prepare(op, b):
+def eo_prepare(op, b, blocks=None):
     """pt_eo_prepare: b'_e [nrhs, N/2(, 4, 3)] from full fields b [nrhs, N(, 4, 3)]."""
     import torch
     b = _eo_field(op, b, op.N, "b")
     be = torch.empty((b.shape[0], op.N // 2) + tuple(b.shape[2:]), dtype=b.dtype, device=b.device)
-    _check(lib().pt_eo_prepare(op.ctx.handle, op._h, _eo_ptr(b), _eo_ptr(be), int(b.shape[0])))
+    _, ao = _eo_blocks(op, blocks)
+    _check(lib().pt_eo_prepare(op.ctx.handle, op._h, ao, _eo_ptr(b), _eo_ptr(be), int(b.shape[0])))
     return be
 
 
-def eo_reconstruct(op, xe, b):
+def eo_reconstruct(op, xe, b, blocks=None):
     """pt_eo_reconstruct: full solutions x [nrhs, N(, 4, 3)] from xe and b."""
     import torch
     xe = _eo_field(op, xe, op.N // 2, "xe")
@@ -603,7 +638,9 @@ def eo_reconstruct(op, xe, b):
     if xe.shape[0] != b.shape[0]:
         raise ValueError("xe and b hold different numbers of right-hand sides")
     x = torch.empty_like(b)
-    _check(lib().pt_eo_reconstruct(op.ctx.handle, op._h, _eo_ptr(xe), _eo_ptr(b), _eo_ptr(x), int(b.shape[0])))
+    _, ao = _eo_blocks(op, blocks)
+    _check(lib().pt_eo_reconstruct(op.ctx.handle, op._h, ao, _eo_ptr(xe), _eo_ptr(b), _eo_ptr(x),
+                                   int(b.shape[0])))
     return x
 
 

@@ -92,3 +92,38 @@ def test_wilson_steps_on_the_host_match_the_oracle(ptlib, dims, ap):
     xs = ptlib.eo_host(1, dims, 2, x_e, b[:1], **kw)[0]
     A = D.dense_matrix(OE.Wilson(dims, U, kappa, ap))
     assert np.allclose(xs.reshape(-1), np.linalg.solve(A, b[0].reshape(-1)), atol=1e-11)
+
+
+def test_clover_steps_on_the_host_match_the_oracle(ptlib):
+    """With the clover site blocks (A_ee = 1 + C_ee, A_oo^{-1} per site) the
+    steps match the oracle's clover Schur complement and compose to A_c^{-1} b."""
+    from oracle import clover as CL
+    from oracle import deflation as D
+    from paper_2106_01275_gb300 import inputs
+    dims, kappa, csw = [2, 2, 2, 4], 0.12, 1.8
+    N = int(np.prod(dims))
+    U = inputs.gauge_links(dims, 24, eps=0.8)
+    C = ptlib.clover_blocks_host(dims, U, kappa, csw)
+    ev, od = EO.split(dims)
+    Aee = np.eye(12)[None] + C[ev]
+    Aoo_inv = ptlib.site_blocks_invert_host(C[od], 1.0)
+    eo = EO.WilsonCloverEO(dims, U, kappa, csw)
+    rng = np.random.default_rng(6)
+    xe = rng.standard_normal((2, N // 2, 4, 3)) + 1j * rng.standard_normal((2, N // 2, 4, 3))
+    b = rng.standard_normal((2, N, 4, 3)) + 1j * rng.standard_normal((2, N, 4, 3))
+    kw = dict(kappa=kappa, U=U, blocks=(Aee, Aoo_inv))
+    ye = ptlib.eo_host(1, dims, 0, xe, **kw)
+    be = ptlib.eo_host(1, dims, 1, b, **kw)
+    x = ptlib.eo_host(1, dims, 2, xe, b, **kw)
+    for r in range(2):
+        assert np.allclose(ye[r].reshape(-1, 12), eo.schur(xe[r].reshape(-1, 12)), rtol=0, atol=1e-12)
+        assert np.allclose(be[r].reshape(-1, 12), eo.rhs(b[r]), rtol=0, atol=1e-12)
+        assert np.allclose(x[r].reshape(-1, 12), eo.reconstruct(xe[r].reshape(-1, 12), b[r]), rtol=0, atol=1e-12)
+    n_e = 6 * N
+    S = ptlib.eo_host(1, dims, 0, np.eye(n_e).reshape(n_e, N // 2, 4, 3), **kw).reshape(n_e, n_e).T
+    x_e = np.linalg.solve(S, be[0].reshape(-1)).reshape(1, N // 2, 4, 3)
+    xs = ptlib.eo_host(1, dims, 2, x_e, b[:1], **kw)[0]
+    A = D.dense_matrix(CL.WilsonClover(dims, U, kappa, csw))
+    assert np.allclose(xs.reshape(-1), np.linalg.solve(A, b[0].reshape(-1)), atol=1e-11)
+    with pytest.raises(ptlib.PtraceError):                       # no site blocks for the Laplacian
+        ptlib.eo_host(0, dims, 0, np.zeros((1, N // 2)), m2=0.1, blocks=(Aee, Aoo_inv))
