@@ -486,6 +486,25 @@ PT_API int pt_eo_host(int kind, const int dims[4], double m2, double kappa, cons
                       const double *Aee, const double *Aoo_inv, int step, const double *in1, const double *in2,
                       double *out, int nrhs);
 
+/* A x = b through the even system, for nrhs full fields (user layout,
+ * device; x and b must not overlap): b'_e (pt_eo_prepare), S x_e = b'_e from
+ * x_e = 0 by CG (Laplacian: S is symmetric positive definite) or BiCGStab
+ * (Wilson, clover: restarted from the true residual) in FP64 until
+ * ||b'_e - S x_e|| <= tol ||b'_e||, then the reconstruction.  One right-hand
+ * side at a time; each dot product is summed in a fixed order and read back
+ * (the building-block solver, not the batched engine).  iters_out (int32
+ * [nrhs]) and relres_out (float64 [nrhs], the even system's true relative
+ * residual): host, may be NULL.  PT_ERR_NOCONV if a right-hand side reaches
+ * maxit first (outputs still written).  Synchronises. */
+PT_API int pt_eo_solve(pt_ctx *ctx, const pt_op *op, const double *Aee_dev, const double *Aoo_inv_dev,
+                       const double *b_dev, double *x_dev, int nrhs, double tol, int maxit, int *iters_out,
+                       double *relres_out);
+
+/* The same solve on the host (no GPU; the same steps, host buffers). */
+PT_API int pt_eo_solve_host(int kind, const int dims[4], double m2, double kappa, const double *U_host, int antip,
+                            const double *Aee, const double *Aoo_inv, const double *b, double *x, int nrhs,
+                            double tol, int maxit, int *iters_out, double *relres_out);
+
 /* ---------------------------------------------------------------- clover */
 
 /* Clover (Sheikholeslami-Wohlert) site blocks of the Wilson-Dirac operator

@@ -198,6 +198,62 @@ __global__ void k_eo_merge(EoGeom g, int w, const double *xe, const double *xo, 
     }
 }
 
+// vector operations of the even-odd solver on n reals (complex fields: pairs)
+__global__ void k_eo_axpy(long n, int cplx, double ar, double ai, const double *x, double *y) {
+    const long m = cplx ? n / 2 : n;
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (long)gridDim.x * blockDim.x) {
+        if (cplx) {
+            const double xr = x[2 * t], xi = x[2 * t + 1];
+            y[2 * t] += ar * xr - ai * xi;
+            y[2 * t + 1] += ar * xi + ai * xr;
+        } else {
+            y[t] += ar * x[t];
+        }
+    }
+}
+__global__ void k_eo_xpay(long n, int cplx, const double *x, double br, double bi, double *y) {
+    const long m = cplx ? n / 2 : n;
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (long)gridDim.x * blockDim.x) {
+        if (cplx) {
+            const double yr = y[2 * t], yi = y[2 * t + 1];
+            y[2 * t] = x[2 * t] + br * yr - bi * yi;
+            y[2 * t + 1] = x[2 * t + 1] + br * yi + bi * yr;
+        } else {
+            y[t] = x[t] + br * y[t];
+        }
+    }
+}
+// partials[block] = sum over the block's elements of conj(x) y, in a fixed order
+#define EO_DOT_BLOCKS 256
+__global__ void __launch_bounds__(256) k_eo_dot(long n, int cplx, const double *x, const double *y,
+                                                double *partials) {
+    __shared__ double sh[2][8];
+    const long m = cplx ? n / 2 : n;
+    double re = 0.0, im = 0.0;
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (long)gridDim.x * blockDim.x) {
+        if (cplx) {
+            const double xr = x[2 * t], xi = x[2 * t + 1], yr = y[2 * t], yi = y[2 * t + 1];
+            re += xr * yr + xi * yi;
+            im += xr * yi - xi * yr;
+        } else {
+            re += x[t] * y[t];
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_down_sync(0xffffffffu, re, o);
+        im += __shfl_down_sync(0xffffffffu, im, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { sh[0][warp] = re; sh[1][warp] = im; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < 8; ++w) { a += sh[0][w]; b += sh[1][w]; }
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = b;
+    }
+}
+
 // ---------------------------------------------------------------- executors
 // The steps below run the site arithmetic either as kernels on the context
 // stream (DevExec) or as host loops (HostExec); both offer the same calls.
@@ -231,6 +287,42 @@ struct DevExec {
         PT_CUDA(cudaGetLastError());
         return PT_OK;
     }
+    double *dot_part = nullptr;   // EO_DOT_BLOCKS complex partials (allocated by the solver)
+    std::vector<double> h_part;
+    int vgrid(long m) const { return (int)std::max(1L, std::min((m + 255) / 256, 16L * c->num_sms)); }
+    int axpy(long n, int cplx, zd a, const double *x, double *y) {
+        k_eo_axpy<<<vgrid(cplx ? n / 2 : n), 256, 0, c->stream>>>(n, cplx, a.re, a.im, x, y);
+        ++pt_kernel_launch_count;
+        PT_CUDA(cudaGetLastError());
+        return PT_OK;
+    }
+    int xpay(long n, int cplx, const double *x, zd b, double *y) {
+        k_eo_xpay<<<vgrid(cplx ? n / 2 : n), 256, 0, c->stream>>>(n, cplx, x, b.re, b.im, y);
+        ++pt_kernel_launch_count;
+        PT_CUDA(cudaGetLastError());
+        return PT_OK;
+    }
+    int copy(long n, const double *x, double *y) {
+        PT_CUDA(cudaMemcpyAsync(y, x, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        return PT_OK;
+    }
+    int zero(long n, double *y) {
+        PT_CUDA(cudaMemsetAsync(y, 0, (size_t)n * sizeof(double), c->stream));
+        return PT_OK;
+    }
+    int dot(long n, int cplx, const double *x, const double *y, zd *out) {
+        k_eo_dot<<<EO_DOT_BLOCKS, 256, 0, c->stream>>>(n, cplx, x, y, dot_part);
+        ++pt_kernel_launch_count;
+        PT_CUDA(cudaGetLastError());
+        h_part.resize(2 * EO_DOT_BLOCKS);
+        PT_CUDA(cudaMemcpyAsync(h_part.data(), dot_part, h_part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                c->stream));
+        PT_CUDA(cudaStreamSynchronize(c->stream));
+        zd acc = {0.0, 0.0};
+        for (int k = 0; k < EO_DOT_BLOCKS; ++k) acc = zadd(acc, zd{h_part[2 * k], h_part[2 * k + 1]});
+        *out = acc;
+        return PT_OK;
+    }
     int merge(int w, const double *xe, const double *xo, int nrhs, double *x) {
         const long total = (long)nrhs * g.N;
         const int grid = (int)std::max(1L, std::min((total + 255) / 256, 64L * c->num_sms));
@@ -245,12 +337,16 @@ struct HostExec {
     EoGeom g;
     UserLinks U;
     EoOp o;
+    double *dot_part = nullptr;   // unused on the host
     std::vector<std::vector<double>> bufs;
     double *alloc(size_t n) {
         bufs.emplace_back(n, 0.0);
         return bufs.back().data();
     }
-    void release(double *) {}
+    void release(double *p) {
+        for (size_t k = 0; k < bufs.size(); ++k)
+            if (bufs[k].data() == p) { bufs.erase(bufs.begin() + (long)k); return; }
+    }
     int hop(int par_out, UserField self, double alpha, UserField src, double beta, int nrhs, double *out) {
         for (int r = 0; r < nrhs; ++r)
             for (int h = 0; h < g.Nh; ++h) eo_axpby_site(g, U, o, par_out, self, alpha, src, beta, r, h, out);
@@ -259,6 +355,45 @@ struct HostExec {
     int blk(int par_out, const double *B, UserField in, int nrhs, double *out) {
         for (int r = 0; r < nrhs; ++r)
             for (int h = 0; h < g.Nh; ++h) eo_block_site(g, B, par_out, in, r, h, out);
+        return PT_OK;
+    }
+    int axpy(long n, int cplx, zd a, const double *x, double *y) {
+        if (cplx)
+            for (long t = 0; t < n / 2; ++t) {
+                const zd v = zadd(zd{y[2 * t], y[2 * t + 1]}, zmulc(a, zd{x[2 * t], x[2 * t + 1]}));
+                y[2 * t] = v.re;
+                y[2 * t + 1] = v.im;
+            }
+        else
+            for (long t = 0; t < n; ++t) y[t] += a.re * x[t];
+        return PT_OK;
+    }
+    int xpay(long n, int cplx, const double *x, zd b, double *y) {
+        if (cplx)
+            for (long t = 0; t < n / 2; ++t) {
+                const zd v = zadd(zd{x[2 * t], x[2 * t + 1]}, zmulc(b, zd{y[2 * t], y[2 * t + 1]}));
+                y[2 * t] = v.re;
+                y[2 * t + 1] = v.im;
+            }
+        else
+            for (long t = 0; t < n; ++t) y[t] = x[t] + b.re * y[t];
+        return PT_OK;
+    }
+    int copy(long n, const double *x, double *y) {
+        for (long t = 0; t < n; ++t) y[t] = x[t];
+        return PT_OK;
+    }
+    int zero(long n, double *y) {
+        for (long t = 0; t < n; ++t) y[t] = 0.0;
+        return PT_OK;
+    }
+    int dot(long n, int cplx, const double *x, const double *y, zd *out) {
+        zd acc = {0.0, 0.0};
+        if (cplx)
+            for (long t = 0; t < n / 2; ++t) acc = zadd(acc, zmulc(zconj(zd{x[2 * t], x[2 * t + 1]}), zd{y[2 * t], y[2 * t + 1]}));
+        else
+            for (long t = 0; t < n; ++t) acc.re += x[t] * y[t];
+        *out = acc;
         return PT_OK;
     }
     int merge(int w, const double *xe, const double *xo, int nrhs, double *x) {
@@ -356,6 +491,129 @@ static int eo_reconstruct_run(X &ex, const EoParams &P, const double *xe, const 
     if (!rc) rc = ex.merge(w, xe, xo, nrhs, x);
     ex.release(vo);
     return rc;
+}
+
+// ---------------------------------------------------------------- the even solve
+__host__ __device__ __forceinline__ zd zdiv(zd a, zd b) {
+    const double d = b.re * b.re + b.im * b.im;
+    return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+
+// S x = b' for one right-hand side (even half fields of n reals), from x = 0:
+// CG for the Laplacian (S symmetric positive definite), BiCGStab for Wilson
+// (restarted from the true residual, as the oracle's).  work: 6 n reals.
+// *iters: Krylov iterations; *relres: ||b' - S x|| / ||b'|| recomputed at the
+// end.  PT_ERR_NOCONV if the iteration limit is reached first.
+template <class X>
+static int eo_krylov(X &ex, const EoParams &P, const double *bp, double *x, double *work, double tol, int maxit,
+                     int *iters, double *relres) {
+    const EoGeom &g = ex.g;
+    const int cplx = P.kind == 1;
+    const long n = (long)g.Nh * (cplx ? 24 : 1);
+    double *r = work, *p = work + n, *q = work + 2 * n, *r0 = work + 3 * n, *s = work + 4 * n, *t = work + 5 * n;
+    int rc;
+    zd z, z2;
+    *iters = 0;
+    *relres = 0.0;
+    if ((rc = ex.zero(n, x)) || (rc = ex.dot(n, cplx, bp, bp, &z))) return rc;
+    const double bn = sqrt(z.re);
+    if (bn == 0.0) return PT_OK;
+    const double stop = tol * bn;
+    bool converged = false;
+    if (!cplx) {                                                         // CG
+        if ((rc = ex.copy(n, bp, r)) || (rc = ex.copy(n, r, p)) || (rc = ex.dot(n, 0, r, r, &z))) return rc;
+        double rr = z.re;
+        while (*iters < maxit) {
+            if ((rc = eo_schur_run(ex, P, p, q, 1)) || (rc = ex.dot(n, 0, p, q, &z))) return rc;
+            if (!(z.re > 0.0)) {
+                pt_set_error("even-odd CG: p^T S p = %g is not positive", z.re);
+                return PT_ERR_NUMERIC;
+            }
+            const double alpha = rr / z.re;
+            if ((rc = ex.axpy(n, 0, zd{alpha, 0.0}, p, x)) || (rc = ex.axpy(n, 0, zd{-alpha, 0.0}, q, r))) return rc;
+            ++*iters;
+            if ((rc = ex.dot(n, 0, r, r, &z))) return rc;
+            if (sqrt(z.re) <= stop) { converged = true; break; }
+            if ((rc = ex.xpay(n, 0, r, zd{z.re / rr, 0.0}, p))) return rc;           // p = r + beta p
+            rr = z.re;
+        }
+    } else {                                                             // BiCGStab
+        for (;;) {
+            if ((rc = eo_schur_run(ex, P, x, q, 1)) || (rc = ex.copy(n, bp, r)) ||
+                (rc = ex.axpy(n, 1, zd{-1.0, 0.0}, q, r)) || (rc = ex.dot(n, 1, r, r, &z)))
+                return rc;
+            if (sqrt(z.re) <= stop) { converged = true; break; }
+            if (*iters >= maxit) break;
+            zd rho;
+            if ((rc = ex.copy(n, r, r0)) || (rc = ex.copy(n, r, p)) || (rc = ex.dot(n, 1, r0, r, &rho))) return rc;
+            while (*iters < maxit) {
+                if ((rc = eo_schur_run(ex, P, p, q, 1)) || (rc = ex.dot(n, 1, r0, q, &z))) return rc;   // v = S p
+                const zd alpha = zdiv(rho, z);
+                if (!isfinite(alpha.re) || !isfinite(alpha.im)) {
+                    pt_set_error("even-odd BiCGStab: breakdown (r0^H v = 0)");
+                    return PT_ERR_NUMERIC;
+                }
+                if ((rc = ex.copy(n, r, s)) || (rc = ex.axpy(n, 1, zd{-alpha.re, -alpha.im}, q, s)) ||
+                    (rc = eo_schur_run(ex, P, s, t, 1)) || (rc = ex.dot(n, 1, t, t, &z)) ||
+                    (rc = ex.dot(n, 1, t, s, &z2)))
+                    return rc;
+                const zd omega = z.re > 0.0 ? zd{z2.re / z.re, z2.im / z.re} : zd{0.0, 0.0};
+                if ((rc = ex.axpy(n, 1, alpha, p, x)) || (rc = ex.axpy(n, 1, omega, s, x)) ||
+                    (rc = ex.copy(n, s, r)) || (rc = ex.axpy(n, 1, zd{-omega.re, -omega.im}, t, r)) ||
+                    (rc = ex.dot(n, 1, r, r, &z)))
+                    return rc;
+                ++*iters;
+                if (sqrt(z.re) <= stop || (omega.re == 0.0 && omega.im == 0.0)) break;
+                zd rho_new;
+                if ((rc = ex.dot(n, 1, r0, r, &rho_new))) return rc;
+                const zd beta = zmulc(zdiv(rho_new, rho), zdiv(alpha, omega));
+                if ((rc = ex.axpy(n, 1, zd{-omega.re, -omega.im}, q, p)) || (rc = ex.xpay(n, 1, r, beta, p)))
+                    return rc;                                                          // p = r + beta (p - omega v)
+                rho = rho_new;
+            }
+        }
+    }
+    // the true residual of the even system
+    if ((rc = eo_schur_run(ex, P, x, q, 1)) || (rc = ex.copy(n, bp, r)) ||
+        (rc = ex.axpy(n, cplx, zd{-1.0, 0.0}, q, r)) || (rc = ex.dot(n, cplx, r, r, &z)))
+        return rc;
+    *relres = sqrt(z.re) / bn;
+    if (!converged && !(*relres <= tol)) {
+        pt_set_error("even-odd solve: %d iterations, relative residual %g", *iters, *relres);
+        return PT_ERR_NOCONV;
+    }
+    return PT_OK;
+}
+
+// A x = b for nrhs full fields: b'_e, the even solve per right-hand side, the
+// reconstruction.  iters / relres (host, may be NULL): per right-hand side.
+template <class X>
+static int eo_solve_run(X &ex, const EoParams &P, const double *b, double *x, int nrhs, double tol, int maxit,
+                        int *iters, double *relres) {
+    const EoGeom &g = ex.g;
+    const long n = (long)g.Nh * (P.kind == 1 ? 24 : 1);
+    double *be = ex.alloc((size_t)nrhs * n), *xe = ex.alloc((size_t)nrhs * n), *work = ex.alloc((size_t)6 * n);
+    double *part = ex.alloc((size_t)2 * EO_DOT_BLOCKS);
+    int rc = PT_OK, rc_nc = PT_OK;
+    if (!be || !xe || !work || !part) {
+        pt_set_error("even-odd solve: allocation failed");
+        rc = PT_ERR_OOM;
+    }
+    ex.dot_part = part;
+    if (!rc) rc = eo_prepare_run(ex, P, b, be, nrhs);
+    for (int r = 0; r < nrhs && !rc; ++r) {
+        int it = 0;
+        double rel = 0.0;
+        const int k = eo_krylov(ex, P, be + (size_t)r * n, xe + (size_t)r * n, work, tol, maxit, &it, &rel);
+        if (iters) iters[r] = it;
+        if (relres) relres[r] = rel;
+        if (k == PT_ERR_NOCONV) rc_nc = k;
+        else rc = k;
+    }
+    if (!rc) rc = eo_reconstruct_run(ex, P, xe, b, x, nrhs);
+    for (double *q : {part, work, xe, be})
+        if (q) ex.release(q);
+    return rc ? rc : rc_nc;
 }
 
 // ---------------------------------------------------------------- host side
@@ -527,4 +785,32 @@ extern "C" int pt_eo_host(int kind, const int dims[4], double m2, double kappa, 
     if (step == 1) return eo_prepare_run(ex, P, in1, out, nrhs);
     PT_CHECK_ARG(step == 2, "pt_eo_host: step must be 0 (Schur), 1 (prepare) or 2 (reconstruct)");
     return eo_reconstruct_run(ex, P, in1, in2, out, nrhs);
+}
+
+extern "C" int pt_eo_solve(pt_ctx *c, const pt_op *op, const double *Aee_dev, const double *Aoo_inv_dev,
+                           const double *b_dev, double *x_dev, int nrhs, double tol, int maxit, int *iters_out,
+                           double *relres_out) {
+    DevExec ex;
+    EoParams P;
+    int rc = eo_dev(c, op, nrhs, "pt_eo_solve", &ex, &P);
+    if (!rc) rc = eo_blocks(&P, Aee_dev, Aoo_inv_dev, "pt_eo_solve");
+    if (rc || nrhs == 0) return rc;
+    PT_CHECK_ARG(b_dev && x_dev && (const double *)x_dev != b_dev, "pt_eo_solve: NULL or aliased fields");
+    PT_CHECK_ARG(tol > 0.0 && maxit >= 1, "pt_eo_solve: tol > 0 and maxit >= 1 required");
+    rc = eo_solve_run(ex, P, b_dev, x_dev, nrhs, tol, maxit, iters_out, relres_out);
+    const cudaError_t ce = cudaStreamSynchronize(c->stream);
+    if (!rc && ce != cudaSuccess) rc = pt_cuda_fail(ce, "pt_eo_solve", __FILE__, __LINE__);
+    return rc;
+}
+
+extern "C" int pt_eo_solve_host(int kind, const int dims[4], double m2, double kappa, const double *U_host,
+                                int antip, const double *Aee, const double *Aoo_inv, const double *b, double *x,
+                                int nrhs, double tol, int maxit, int *iters_out, double *relres_out) {
+    HostExec ex;
+    EoParams P;
+    int rc = eo_host(kind, dims, m2, kappa, U_host, antip, "pt_eo_solve_host", &ex, &P);
+    if (!rc) rc = eo_blocks(&P, Aee, Aoo_inv, "pt_eo_solve_host");
+    if (rc) return rc;
+    PT_CHECK_ARG(nrhs >= 0 && b && x && tol > 0.0 && maxit >= 1, "pt_eo_solve_host: bad argument");
+    return eo_solve_run(ex, P, b, x, nrhs, tol, maxit, iters_out, relres_out);
 }

@@ -105,6 +105,8 @@ _SIGS = {
     "pt_eo_prepare": ([_P, _P, _P, _P, _P, _I], _I),
     "pt_eo_reconstruct": ([_P, _P, _P, _P, _P, _P, _I], _I),
     "pt_eo_clover_blocks": ([_P, _P, _D, _P, _P], _I),
+    "pt_eo_solve": ([_P, _P, _P, _P, _P, _P, _I, _D, _I, _P, _P], _I),
+    "pt_eo_solve_host": ([_I, ctypes.POINTER(_I), _D, _D, _P, _I, _P, _P, _P, _P, _I, _D, _I, _P, _P], _I),
     "pt_clover_blocks_host": ([ctypes.POINTER(_I), _P, _D, _D, _P], _I),
     "pt_clover_blocks": ([_P, _P, _D, _P], _I),
     "pt_site_blocks_apply": ([_P, _I, _P, _P, _D, _P, _I], _I),
@@ -569,6 +571,42 @@ def eo_host(kind, dims, step, in1, in2=None, m2=0.0, kappa=0.0, U=None, antiperi
                             int(step),
                             _np_ptr(in1), _np_ptr(in2) if in2 is not None else None, _np_ptr(out), int(nrhs)))
     return out
+
+
+def eo_solve_host(kind, dims, b, tol=1e-10, maxit=10000, m2=0.0, kappa=0.0, U=None, antiperiodic_t=True,
+                  blocks=None):
+    """pt_eo_solve_host (host only): (x, iters, relres) for numpy b
+    [nrhs, N] (Laplacian) or [nrhs, N, 4, 3] complex (Wilson)."""
+    dt = np.float64 if kind == 0 else np.complex128
+    b = np.ascontiguousarray(np.asarray(b, dtype=dt))
+    nrhs, N = b.shape[0], int(np.prod(dims))
+    x = np.zeros_like(b)
+    iters = np.zeros(nrhs, dtype=np.int32)
+    relres = np.zeros(nrhs, dtype=np.float64)
+    U = None if U is None else np.ascontiguousarray(np.asarray(U, dtype=np.complex128))
+    Aee = Aoo = None
+    if blocks is not None:
+        Aee = np.ascontiguousarray(np.asarray(blocks[0], dtype=np.complex128)).reshape(N // 2, 12, 12)
+        Aoo = np.ascontiguousarray(np.asarray(blocks[1], dtype=np.complex128)).reshape(N // 2, 12, 12)
+    _check(lib().pt_eo_solve_host(int(kind), _ints(dims), float(m2), float(kappa),
+                                  _np_ptr(U) if U is not None else None, 1 if antiperiodic_t else 0,
+                                  _np_ptr(Aee) if Aee is not None else None, _np_ptr(Aoo) if Aoo is not None else None,
+                                  _np_ptr(b), _np_ptr(x), int(nrhs), float(tol), int(maxit), _np_ptr(iters),
+                                  _np_ptr(relres)))
+    return x, iters, relres
+
+
+def eo_solve(op, b, tol=1e-10, maxit=10000, blocks=None):
+    """pt_eo_solve: (x, iters, relres) for full fields b [nrhs, N(, 4, 3)] on the device."""
+    import torch
+    b = _eo_field(op, b, op.N, "b")
+    x = torch.empty_like(b)
+    iters = np.zeros(b.shape[0], dtype=np.int32)
+    relres = np.zeros(b.shape[0], dtype=np.float64)
+    ae, ao = _eo_blocks(op, blocks)
+    _check(lib().pt_eo_solve(op.ctx.handle, op._h, ae, ao, _eo_ptr(b), _eo_ptr(x), int(b.shape[0]), float(tol),
+                             int(maxit), _np_ptr(iters), _np_ptr(relres)))
+    return x, iters, relres
 
 
 def _eo_field(op, x, sites, name):

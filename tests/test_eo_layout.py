@@ -127,3 +127,45 @@ def test_clover_steps_on_the_host_match_the_oracle(ptlib):
     assert np.allclose(xs.reshape(-1), np.linalg.solve(A, b[0].reshape(-1)), atol=1e-11)
     with pytest.raises(ptlib.PtraceError):                       # no site blocks for the Laplacian
         ptlib.eo_host(0, dims, 0, np.zeros((1, N // 2)), m2=0.1, blocks=(Aee, Aoo_inv))
+
+
+def test_even_solve_on_the_host(ptlib):
+    """The building-block solver (host executor): A^{-1} b for the Laplacian,
+    Wilson and clover operators against dense solves; the even Laplacian
+    system needs about half the CG iterations of the full one (cond(S) is
+    about four times smaller) and Wilson fewer BiCGStab iterations; maxit
+    exhaustion is reported; b = 0 gives x = 0 with no iteration."""
+    from oracle import clover as CL
+    from oracle import deflation as D
+    import oracle.estimator as OE
+    from paper_2106_01275_gb300 import inputs
+    rng = np.random.default_rng(9)
+    dims, m2 = [8, 8, 4, 4], 0.05
+    N = int(np.prod(dims))
+    b = rng.standard_normal((2, N))
+    x, its, rel = ptlib.eo_solve_host(0, dims, b, tol=1e-12, m2=m2)
+    opL = OE.Laplacian(dims, m2)
+    for r in range(2):
+        xf, its_full, _ = opL.solve(b[r], 1e-12)
+        assert np.allclose(x[r], np.asarray(xf).reshape(-1), rtol=0, atol=1e-9 * np.abs(xf).max())
+        assert rel[r] <= 1e-12 and its[r] <= 0.7 * its_full, (its[r], its_full)
+    dims = [2, 2, 4, 2]
+    N = int(np.prod(dims))
+    U = inputs.gauge_links(dims, 41, eps=0.7)
+    bw = rng.standard_normal((1, N, 4, 3)) + 1j * rng.standard_normal((1, N, 4, 3))
+    xw, itw, relw = ptlib.eo_solve_host(1, dims, bw, tol=1e-12, kappa=0.12, U=U)
+    A = D.dense_matrix(OE.Wilson(dims, U, 0.12))
+    assert np.allclose(xw[0].reshape(-1), np.linalg.solve(A, bw[0].reshape(-1)), atol=1e-10)
+    _, its_full, _ = OE.Wilson(dims, U, 0.12).solve(bw[0], 1e-12)
+    assert relw[0] <= 1e-12 and itw[0] < its_full, (itw[0], its_full)
+    C = ptlib.clover_blocks_host(dims, U, 0.12, 1.5)
+    ev, od = EO.split(dims)
+    blocks = (np.eye(12)[None] + C[ev], ptlib.site_blocks_invert_host(C[od], 1.0))
+    xc, _, relc = ptlib.eo_solve_host(1, dims, bw, tol=1e-12, kappa=0.12, U=U, blocks=blocks)
+    Ac = D.dense_matrix(CL.WilsonClover(dims, U, 0.12, 1.5))
+    assert relc[0] <= 1e-12 and np.allclose(xc[0].reshape(-1), np.linalg.solve(Ac, bw[0].reshape(-1)), atol=1e-10)
+    with pytest.raises(ptlib.PtraceError) as ei:
+        ptlib.eo_solve_host(0, [4, 4, 4, 4], rng.standard_normal((1, 256)), tol=1e-14, maxit=1, m2=0.01)
+    assert ei.value.code == ptlib.PT_ERR_NOCONV
+    x0, it0, rel0 = ptlib.eo_solve_host(0, [4, 4, 4, 4], np.zeros((1, 256)), m2=0.1)
+    assert np.all(x0 == 0) and it0[0] == 0 and rel0[0] == 0.0
