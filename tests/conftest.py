@@ -1,5 +1,8 @@
 import os
+import shutil
 import sys
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
@@ -21,3 +24,15 @@ def read_golden(name):
             if line and not line.startswith("#"):
                 rows.append(line.split())
     return rows
+
+
+@pytest.fixture(scope="module")
+def ptlib():
+    """The library's binding, built if needed (the host-only entry points need no GPU)."""
+    from paper_2106_01275_gb300 import build
+    if build.needs_build():
+        if not shutil.which(build.NVCC) and not os.path.exists(build.NVCC):
+            pytest.skip("nvcc not available to build libptrace.so")
+        build.build()
+    from paper_2106_01275_gb300 import ptrace
+    return ptrace

@@ -3,23 +3,11 @@ include/ptrace.h declares, and its host-side stencil (Eq. (8)) matches the
 oracle.  No compute call is made (there may be no GPU)."""
 import os
 import re
-import shutil
 
 import numpy as np
 import pytest
 
 from conftest import ROOT
-
-
-@pytest.fixture(scope="module")
-def ptlib():
-    from paper_2106_01275_gb300 import build
-    if build.needs_build():
-        if not shutil.which(build.NVCC) and not os.path.exists(build.NVCC):
-            pytest.skip("nvcc not available to build libptrace.so")
-        build.build()
-    from paper_2106_01275_gb300 import ptrace
-    return ptrace
 
 
 def header_symbols():

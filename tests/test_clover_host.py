@@ -2,25 +2,11 @@
 __host__ __device__ code as its kernels) against the oracle: the blocks
 C(x) for random links, the uniform-flux closed form, and the per-site
 inverses (1 + C(x))^{-1}.  No GPU needed."""
-import os
-import shutil
-
 import numpy as np
 import pytest
 
 from oracle import clover as CL
 from paper_2106_01275_gb300 import inputs
-
-
-@pytest.fixture(scope="module")
-def ptlib():
-    from paper_2106_01275_gb300 import build
-    if build.needs_build():
-        if not shutil.which(build.NVCC) and not os.path.exists(build.NVCC):
-            pytest.skip("nvcc not available to build libptrace.so")
-        build.build()
-    from paper_2106_01275_gb300 import ptrace
-    return ptrace
 
 
 @pytest.mark.parametrize("dims,seed", [([2, 3, 2, 4], 1), ([4, 4, 4, 4], 2), ([3, 1, 5, 2], 3)])

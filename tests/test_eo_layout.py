@@ -1,25 +1,11 @@
 """Even-odd half-field layout of the library (pt_eo_layout, host only; the
 same index functions run in the even-odd kernels) against the oracle's
 even / odd split and its neighbour tables.  No GPU needed."""
-import os
-import shutil
-
 import numpy as np
 import pytest
 
 from oracle import evenodd as EO
 from oracle import operators as ops
-
-
-@pytest.fixture(scope="module")
-def ptlib():
-    from paper_2106_01275_gb300 import build
-    if build.needs_build():
-        if not shutil.which(build.NVCC) and not os.path.exists(build.NVCC):
-            pytest.skip("nvcc not available to build libptrace.so")
-        build.build()
-    from paper_2106_01275_gb300 import ptrace
-    return ptrace
 
 
 @pytest.mark.parametrize("dims", [[2, 2, 2, 2], [4, 2, 6, 2], [6, 4, 2, 8], [2, 4, 4, 6], [8, 8, 8, 16]])

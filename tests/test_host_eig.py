@@ -2,22 +2,8 @@
 (pt_hermitian_eig): eigenvalues against closed forms and numpy's eigvalsh,
 eigenvectors by residual and orthonormality, degenerate clusters, the
 degenerate sizes and the error paths.  No GPU needed."""
-import os
-import shutil
-
 import numpy as np
 import pytest
-
-
-@pytest.fixture(scope="module")
-def ptlib():
-    from paper_2106_01275_gb300 import build
-    if build.needs_build():
-        if not shutil.which(build.NVCC) and not os.path.exists(build.NVCC):
-            pytest.skip("nvcc not available to build libptrace.so")
-        build.build()
-    from paper_2106_01275_gb300 import ptrace
-    return ptrace
 
 
 def _check_pairs(T, w, X, tol):
