@@ -109,3 +109,53 @@ def test_deflation_leg_json_line(monkeypatch, capsys):
     assert d["config"]["workload"].startswith("deflation: 8^4")
     assert d["check_ritz_vs_closed_form_max_rel"] < 1e-6 and d["check_p0_trace_minus_sum_inv_s"] < 1e-9
     assert len(d["var_plain"]) == 5 and all(a > 10 * b for a, b in zip(d["var_plain"], d["var_deflated"]))
+
+
+def test_evenodd_leg_json_line(monkeypatch, capsys):
+    """`bench.py --workload evenodd --case small` end to end on the CPU: the
+    full-system solves come from the oracle, the even-odd ones from the
+    library's host twin of pt_eo_solve; the line reports fewer even-odd
+    iterations and agreeing solutions."""
+    import numpy as np
+    import torch
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle.estimator as OE
+    from paper_2106_01275_gb300 import ptrace as pt
+
+    monkeypatch.setattr(torch.cuda, "set_device", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(torch.Tensor, "cuda", lambda self, *a, **k: self)
+    monkeypatch.setattr(pt, "Context", lambda dev: types.SimpleNamespace(device=dev, set_max_slots=lambda n: None))
+    monkeypatch.setattr(pt, "laplacian", lambda ctx, dims, m2: types.SimpleNamespace(kind=0, dims=dims, m2=m2))
+    monkeypatch.setattr(pt, "wilson", lambda ctx, dims, U, kappa, ap: types.SimpleNamespace(
+        kind=1, dims=dims, U=np.asarray(U), kappa=kappa))
+
+    def oracle_op(op):
+        return OE.Laplacian(op.dims, op.m2) if op.kind == 0 else OE.Wilson(op.dims, op.U, op.kappa)
+
+    def solve(op, b, prec, tol, maxit):
+        bn = b.numpy()
+        xs, its = [], []
+        for r in range(bn.shape[0]):
+            x, it, _ = oracle_op(op).solve(bn[r], tol)
+            xs.append(np.asarray(x).reshape(bn.shape[1:]))
+            its.append(it)
+        return torch.as_tensor(np.stack(xs)), np.array(its), None, {}
+
+    def eo_solve(op, b, tol, maxit):
+        kw = dict(m2=op.m2) if op.kind == 0 else dict(kappa=op.kappa, U=op.U)
+        x, its, rel = pt.eo_solve_host(op.kind, op.dims, b.numpy(), tol=tol, maxit=maxit, **kw)
+        return torch.as_tensor(x), its, rel
+
+    monkeypatch.setattr(pt, "solve", solve)
+    monkeypatch.setattr(pt, "eo_solve", eo_solve)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "evenodd", "--case", "small"])
+    bench.main()
+    lines = [l for l in capsys.readouterr().out.strip().splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["config"]["workload"].startswith("evenodd:") and len(d["cases"]) == 2 and d["value"] > 1.2
+    for c in d["cases"]:
+        assert sum(c["iters_evenodd"]) < sum(c["iters_full"]) and c["max_rel_diff"] < 1e-8, c
