@@ -505,6 +505,30 @@ PT_API int pt_eo_solve_host(int kind, const int dims[4], double m2, double kappa
                             const double *Aee, const double *Aoo_inv, const double *b, double *x, int nrhs,
                             double tol, int maxit, int *iters_out, double *relres_out);
 
+/* Probed estimates of Tr(P_{p_n} A^{-1}) for the shifted Laplacian with the
+ * solves on the even Schur complement: the same tasks, sources, contraction
+ * and output as pt_trace_PAinv (est_out: host complex128 [n_sets][n_p]; the
+ * colouring col_dev on the device), each task solving S x_e = b'_e by FP32 CG
+ * (to delta times its starting residual) inside FP64 defect correction to
+ * ||b'_e - S x_e|| <= tol ||b'_e||, then x_o = (v_o + H_oe x_e) / d where the
+ * contraction reads it.  The tasks of a batch advance in lockstep (batch size
+ * bounded by the memory budget and the slot cap); per-task scalars are
+ * computed on the host after one reduction per step.  Every lattice side
+ * even; 1 <= n_p <= 32.  stats: n_rhs, inner and outer iterations,
+ * site_rhs_applies (inner iterations x N), kernel launches, largest final
+ * relative residual of the even system, n_slots = batch size.
+ * PT_ERR_NOCONV if a task reaches maxit (est_out still written).
+ * Synchronises. */
+PT_API int pt_trace_PAinv_eo(pt_ctx *ctx, const pt_op *op, const int32_t *col_dev, int n_colours, int mu,
+                             const int *p_list, int n_p, int noise, uint64_t seed, int set0, int n_sets, double tol,
+                             int maxit, double delta, double *est_out, pt_stats *stats);
+
+/* The same estimates on the host (no GPU; the same steps; col_host on the
+ * host; all tasks in one batch). */
+PT_API int pt_trace_PAinv_eo_host(const int dims[4], double m2, const int32_t *col_host, int n_colours, int mu,
+                                  const int *p_list, int n_p, int noise, uint64_t seed, int set0, int n_sets,
+                                  double tol, int maxit, double delta, double *est_out, pt_stats *stats);
+
 /* ---------------------------------------------------------------- clover */
 
 /* Clover (Sheikholeslami-Wohlert) site blocks of the Wilson-Dirac operator

@@ -105,6 +105,10 @@ _SIGS = {
     "pt_eo_prepare": ([_P, _P, _P, _P, _P, _I], _I),
     "pt_eo_reconstruct": ([_P, _P, _P, _P, _P, _P, _I], _I),
     "pt_eo_clover_blocks": ([_P, _P, _D, _P, _P], _I),
+    "pt_trace_PAinv_eo": ([_P, _P, _P, _I, _I, ctypes.POINTER(_I), _I, _I, ctypes.c_uint64, _I, _I, _D, _I, _D, _P,
+                           ctypes.POINTER(Stats)], _I),
+    "pt_trace_PAinv_eo_host": ([ctypes.POINTER(_I), _D, _P, _I, _I, ctypes.POINTER(_I), _I, _I, ctypes.c_uint64, _I,
+                                _I, _D, _I, _D, _P, ctypes.POINTER(Stats)], _I),
     "pt_eo_solve": ([_P, _P, _P, _P, _P, _P, _I, _D, _I, _P, _P], _I),
     "pt_eo_solve_host": ([_I, ctypes.POINTER(_I), _D, _D, _P, _I, _P, _P, _P, _P, _I, _D, _I, _P, _P], _I),
     "pt_clover_blocks_host": ([ctypes.POINTER(_I), _P, _D, _D, _P], _I),
@@ -607,6 +611,31 @@ def eo_solve(op, b, tol=1e-10, maxit=10000, blocks=None):
     _check(lib().pt_eo_solve(op.ctx.handle, op._h, ae, ao, _eo_ptr(b), _eo_ptr(x), int(b.shape[0]), float(tol),
                              int(maxit), _np_ptr(iters), _np_ptr(relres)))
     return x, iters, relres
+
+
+def trace_eo(op, col, n_colours, mu, p_list, noise="z2", seed=0, set0=0, n_sets=1, tol=1e-10, maxit=20000,
+             delta=1e-5):
+    """pt_trace_PAinv_eo (Laplacian, even-odd): (est[n_sets, n_p] complex, stats)."""
+    est = np.zeros((n_sets, len(p_list)), dtype=np.complex128)
+    st = Stats()
+    _check(lib().pt_trace_PAinv_eo(op.ctx.handle, op._h, _ptr(col), int(n_colours), int(mu), _ints(p_list),
+                                   len(p_list), NOISE[noise] if isinstance(noise, str) else int(noise), int(seed),
+                                   int(set0), int(n_sets), float(tol), int(maxit), float(delta), _np_ptr(est),
+                                   ctypes.byref(st)))
+    return est, st.as_dict()
+
+
+def trace_eo_host(dims, m2, col, n_colours, mu, p_list, noise="z2", seed=0, set0=0, n_sets=1, tol=1e-10,
+                  maxit=20000, delta=1e-5):
+    """pt_trace_PAinv_eo_host (no GPU): (est[n_sets, n_p] complex, stats)."""
+    col = np.ascontiguousarray(np.asarray(col, dtype=np.int32))
+    est = np.zeros((n_sets, len(p_list)), dtype=np.complex128)
+    st = Stats()
+    _check(lib().pt_trace_PAinv_eo_host(_ints(dims), float(m2), _np_ptr(col), int(n_colours), int(mu), _ints(p_list),
+                                        len(p_list), NOISE[noise] if isinstance(noise, str) else int(noise),
+                                        int(seed), int(set0), int(n_sets), float(tol), int(maxit), float(delta),
+                                        _np_ptr(est), ctypes.byref(st)))
+    return est, st.as_dict()
 
 
 def _eo_field(op, x, sites, name):
