@@ -652,6 +652,25 @@ def run_evenodd(args):
         rows.append({"operator": kind, "lattice": dims, "iters_full": [int(v) for v in itf],
                      "iters_evenodd": [int(v) for v in ite], "seconds_full": t_full, "seconds_evenodd": t_eo,
                      "even_relres": [float(v) for v in rele], "max_rel_diff": diff})
+    # the Laplacian trace on the same probes: the engine on the full system
+    # against the even-odd trace (mixed precision both, tolerance 1e-10)
+    dims = [8, 8, 8, 8] if small else [16, 16, 16, 16]
+    op = pt.laplacian(ctx, dims, 0.01)
+    col, m = pt.colour(ctx, dims, 3, [4], 2, "natural")
+    ps = [0, 1, 2, 3, 4]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    est_f, _, _, st_f = pt.trace(op, col, m, 3, ps, "z2", SEED, 0, 8, True, "mixed_fp32", 1e-10, 20000)
+    torch.cuda.synchronize()
+    t_f = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    est_e, st_e = pt.trace_eo(op, col, m, 3, ps, "z2", SEED, 0, 8, 1e-10, 20000, 1e-5)
+    torch.cuda.synchronize()
+    t_e = time.perf_counter() - t0
+    trace_row = {"lattice": dims, "colours": int(m), "sets": 8, "seconds_engine_full": t_f,
+                 "seconds_evenodd": t_e, "inner_iters_full": int(st_f["inner_iters"]),
+                 "inner_iters_evenodd": int(st_e["inner_iters"]),
+                 "max_rel_diff": float(np.abs(est_e - est_f).max() / np.abs(est_f).max())}
     out = {"metric": "even-odd preconditioning: Krylov iterations and seconds of FP64 solves, full system vs even "
                      "Schur complement", "value": float(np.mean([sum(r["iters_full"]) / sum(r["iters_evenodd"])
                                                                    for r in rows])),
@@ -660,7 +679,7 @@ def run_evenodd(args):
            "config": {"workload": "evenodd: %s, 2 Gaussian right-hand sides each, FP64 to 1e-10, one right-hand "
                                   "side at a time" % "; ".join("%s %s" % (r["operator"], "x".join(map(str, r["lattice"])))
                                                                for r in rows)},
-           "cases": rows}
+           "cases": rows, "trace": trace_row}
     print(json.dumps(out), flush=True)
 
 

@@ -113,9 +113,10 @@ def test_deflation_leg_json_line(monkeypatch, capsys):
 
 def test_evenodd_leg_json_line(monkeypatch, capsys):
     """`bench.py --workload evenodd --case small` end to end on the CPU: the
-    full-system solves come from the oracle, the even-odd ones from the
-    library's host twin of pt_eo_solve; the line reports fewer even-odd
-    iterations and agreeing solutions."""
+    full-system solves and trace estimates come from the oracle, the even-odd
+    ones from the library's host twins of pt_eo_solve and pt_trace_PAinv_eo;
+    the line reports fewer even-odd iterations and agreeing solutions and
+    estimates."""
     import numpy as np
     import torch
     import types
@@ -149,8 +150,20 @@ def test_evenodd_leg_json_line(monkeypatch, capsys):
         x, its, rel = pt.eo_solve_host(op.kind, op.dims, b.numpy(), tol=tol, maxit=maxit, **kw)
         return torch.as_tensor(x), its, rel
 
+    from oracle.colouring import greedy_colour
+
+    def trace(op, col, m, mu, ps, noise, seed, set0, n_sets, dilute, prec, tol, maxit):
+        est = OE.probed_estimates(OE.Laplacian(op.dims, op.m2), col, m, seed, n_sets, 0, mu, ps, 1e-12, set0=set0)
+        return est, None, None, {"inner_iters": 0}
+
+    def trace_eo(op, col, m, mu, ps, noise, seed, set0, n_sets, tol, maxit, delta):
+        return pt.trace_eo_host(op.dims, op.m2, col, m, mu, ps, noise, seed, set0, n_sets, tol, maxit, delta)
+
     monkeypatch.setattr(pt, "solve", solve)
     monkeypatch.setattr(pt, "eo_solve", eo_solve)
+    monkeypatch.setattr(pt, "colour", lambda ctx, dims, mu, ps, k, order: greedy_colour(dims, mu, ps, k, 0))
+    monkeypatch.setattr(pt, "trace", trace)
+    monkeypatch.setattr(pt, "trace_eo", trace_eo)
     monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "evenodd", "--case", "small"])
     bench.main()
     lines = [l for l in capsys.readouterr().out.strip().splitlines() if l.startswith("{")]
@@ -159,3 +172,4 @@ def test_evenodd_leg_json_line(monkeypatch, capsys):
     assert d["config"]["workload"].startswith("evenodd:") and len(d["cases"]) == 2 and d["value"] > 1.2
     for c in d["cases"]:
         assert sum(c["iters_evenodd"]) < sum(c["iters_full"]) and c["max_rel_diff"] < 1e-8, c
+    assert d["trace"]["max_rel_diff"] < 1e-7 and d["trace"]["colours"] >= 2, d["trace"]
