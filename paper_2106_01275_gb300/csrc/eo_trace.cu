@@ -309,9 +309,12 @@ struct ETDev {
             PT_CUDA(cudaGetLastError());
             tot->assign((size_t)R * K, 0.0);
             PT_CUDA(cudaMemcpyAsync(tot->data(), d_tot, (size_t)R * K * 8, cudaMemcpyDeviceToHost, c->stream));
+            PT_CUDA(cudaStreamSynchronize(c->stream));      // the host needs the totals now
         }
-        // the inactive tasks' partials are zero: every block stores its K values
-        PT_CUDA(cudaStreamSynchronize(c->stream));
+        // (steps without a reduction return at once: an upload from pageable
+        // memory is staged before cudaMemcpyAsync returns, so the host vectors may
+        // change; such an upload also waits for the stream first, which pinned
+        // staging buffers would avoid)
         return PT_OK;
     }
 };
