@@ -53,3 +53,16 @@ def test_errors(ptlib):
     with pytest.raises(ptlib.PtraceError) as ei:
         ptlib.trace_eo_host([4, 4, 4, 4], 0.01, np.zeros(256, np.int32), 1, 0, [1], tol=1e-14, maxit=2)
     assert ei.value.code == ptlib.PT_ERR_NOCONV
+
+
+@pytest.mark.parametrize("dims,mu,ps", [
+    ([2, 2, 2, 2], 2, [0, 1, -1]),                 # both neighbours along a side of 2 are one site
+    ([4, 2, 4, 6], 3, [-2, 6, 13]),                # negative and wrapping displacements
+    ([4, 4, 2, 2], 0, list(range(-16, 16))),       # the full 32 outputs per solve
+])
+def test_edge_cases_match_the_oracle(ptlib, dims, mu, ps):
+    m2 = 0.2
+    col, m = greedy_colour(dims, mu, [1], 1, 0)
+    est, _ = ptlib.trace_eo_host(dims, m2, col, m, mu, ps, "z4", 11, 1, 2, tol=1e-11)
+    want = OE.probed_estimates(OE.Laplacian(dims, m2), col, m, 11, 2, 1, mu, ps, 1e-13, set0=1)
+    assert np.allclose(est, want, rtol=1e-8, atol=1e-9 * np.abs(want).max())
