@@ -31,6 +31,7 @@ clearance    clearance of a colouring at other displacements (Thm 3.6, Table 5)
 deflation    deflation of the lowest singular triplets, Eq. (6) (Sec. 2.4)
 evenodd      even-odd (Schur complement) preconditioning of both operators
 clover       clover (Sheikholeslami-Wohlert) term of the Wilson-Dirac operator
+multigrid    two-level aggregation multigrid preconditioner, right-preconditioned GMRES
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against a
 value printed in the paper, a closed form, brute force or an invariant, except
