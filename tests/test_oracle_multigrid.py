@@ -33,6 +33,16 @@ def test_laplacian_galerkin_operator_closed_form(dims):
     assert np.allclose(P.T @ P, np.eye(P.shape[1]))
 
 
+def test_laplacian_galerkin_operator_block_side_4():
+    """Blocks of b^4 sites in general: per block b^4 (8 + m^2) diagonal terms,
+    8 b^3 (b - 1) inner hops, b^3 hops through each face, so
+    P^T A P = (8 / b + m^2) - (1 / b) sum_mu (S_mu + S_mu^{-1}) = (1 / b) A_coarse(b m^2)."""
+    dims, m2, b = [8, 8, 4, 8], 0.2, 4
+    Ac = MG.coarse_operator(_lap(dims, m2), MG.prolongator_constant(dims, b))
+    want = D.dense_matrix(OE.Laplacian([d // b for d in dims], b * m2)) / b
+    assert np.allclose(Ac, want, atol=1e-13)
+
+
 def test_gmres_against_a_direct_solve():
     """Full GMRES ends in n steps at the exact solution; restarted GMRES
     converges when the spectrum stays clear of the origin (and stagnates
