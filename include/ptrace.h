@@ -529,6 +529,32 @@ PT_API int pt_trace_PAinv_eo_host(const int dims[4], double m2, const int32_t *c
                                   const int *p_list, int n_p, int noise, uint64_t seed, int set0, int n_sets,
                                   double tol, int maxit, double delta, double *est_out, pt_stats *stats);
 
+/* ---------------------------------------------------------------- multigrid */
+
+/* Two-level multigrid for the shifted Laplacian as a CG preconditioner (the
+ * paper solves with an adaptive multigrid library, Sec. 4.2, and describes
+ * none of its method; this is the textbook aggregation scheme).  Aggregates:
+ * blocks of block^4 sites (block must divide every side); prolongator: the
+ * normalised block indicators, so the Galerkin coarse operator is
+ * P^T A P = A_coarse(block m2) / block; the cycle M: nu damped-Jacobi sweeps
+ * (weight omega) from zero, the coarse correction (coarse CG to 1e-13), nu
+ * sweeps, symmetric positive definite.  pt_mg_solve: A x = b for nrhs fields
+ * (float64 [nrhs][N], device; x and b must not overlap) by M-preconditioned
+ * CG from x = 0 in FP64 to ||b - A x|| <= tol ||b||, one right-hand side at
+ * a time; iters_out (int32 [nrhs]) and relres_out (float64 [nrhs], the true
+ * relative residual): host, may be NULL.  PT_ERR_NOCONV if a right-hand side
+ * reaches maxit first.  1 <= block, 0 <= nu <= 16, 0 < omega <= 1.
+ * Synchronises. */
+PT_API int pt_mg_solve(pt_ctx *ctx, const pt_op *op, int block, int nu, double omega, const double *b_dev,
+                       double *x_dev, int nrhs, double tol, int maxit, int *iters_out, double *relres_out);
+
+/* The same solve on the host, and one application out = M r of the cycle
+ * (host buffers; the same site arithmetic and steps; no GPU). */
+PT_API int pt_mg_solve_host(const int dims[4], double m2, int block, int nu, double omega, const double *b,
+                            double *x, int nrhs, double tol, int maxit, int *iters_out, double *relres_out);
+PT_API int pt_mg_cycle_host(const int dims[4], double m2, int block, int nu, double omega, const double *r,
+                            double *out);
+
 /* ---------------------------------------------------------------- clover */
 
 /* Clover (Sheikholeslami-Wohlert) site blocks of the Wilson-Dirac operator

@@ -105,6 +105,9 @@ _SIGS = {
     "pt_eo_prepare": ([_P, _P, _P, _P, _P, _I], _I),
     "pt_eo_reconstruct": ([_P, _P, _P, _P, _P, _P, _I], _I),
     "pt_eo_clover_blocks": ([_P, _P, _D, _P, _P], _I),
+    "pt_mg_solve": ([_P, _P, _I, _I, _D, _P, _P, _I, _D, _I, _P, _P], _I),
+    "pt_mg_solve_host": ([ctypes.POINTER(_I), _D, _I, _I, _D, _P, _P, _I, _D, _I, _P, _P], _I),
+    "pt_mg_cycle_host": ([ctypes.POINTER(_I), _D, _I, _I, _D, _P, _P], _I),
     "pt_trace_PAinv_eo": ([_P, _P, _P, _I, _I, ctypes.POINTER(_I), _I, _I, ctypes.c_uint64, _I, _I, _D, _I, _D, _P,
                            ctypes.POINTER(Stats)], _I),
     "pt_trace_PAinv_eo_host": ([ctypes.POINTER(_I), _D, _P, _I, _I, ctypes.POINTER(_I), _I, _I, ctypes.c_uint64, _I,
@@ -636,6 +639,38 @@ def trace_eo_host(dims, m2, col, n_colours, mu, p_list, noise="z2", seed=0, set0
                                         int(seed), int(set0), int(n_sets), float(tol), int(maxit), float(delta),
                                         _np_ptr(est), ctypes.byref(st)))
     return est, st.as_dict()
+
+
+def mg_solve(op, b, block=2, nu=2, omega=0.8, tol=1e-10, maxit=10000):
+    """pt_mg_solve (Laplacian): (x, iters, relres) for b torch float64 [nrhs, N] on the device."""
+    import torch
+    b = _eo_field(op, b, op.N, "b")
+    x = torch.empty_like(b)
+    iters = np.zeros(b.shape[0], dtype=np.int32)
+    relres = np.zeros(b.shape[0], dtype=np.float64)
+    _check(lib().pt_mg_solve(op.ctx.handle, op._h, int(block), int(nu), float(omega), _ptr(b), _ptr(x),
+                             int(b.shape[0]), float(tol), int(maxit), _np_ptr(iters), _np_ptr(relres)))
+    return x, iters, relres
+
+
+def mg_solve_host(dims, m2, b, block=2, nu=2, omega=0.8, tol=1e-10, maxit=10000):
+    """pt_mg_solve_host (no GPU): (x, iters, relres) for numpy b [nrhs, N]."""
+    b = np.ascontiguousarray(np.asarray(b, dtype=np.float64))
+    x = np.zeros_like(b)
+    iters = np.zeros(b.shape[0], dtype=np.int32)
+    relres = np.zeros(b.shape[0], dtype=np.float64)
+    _check(lib().pt_mg_solve_host(_ints(dims), float(m2), int(block), int(nu), float(omega), _np_ptr(b), _np_ptr(x),
+                                  int(b.shape[0]), float(tol), int(maxit), _np_ptr(iters), _np_ptr(relres)))
+    return x, iters, relres
+
+
+def mg_cycle_host(dims, m2, r, block=2, nu=2, omega=0.8):
+    """pt_mg_cycle_host (no GPU): M r for one numpy vector r [N]."""
+    r = np.ascontiguousarray(np.asarray(r, dtype=np.float64).reshape(-1))
+    out = np.zeros_like(r)
+    _check(lib().pt_mg_cycle_host(_ints(dims), float(m2), int(block), int(nu), float(omega), _np_ptr(r),
+                                  _np_ptr(out)))
+    return out
 
 
 def _eo_field(op, x, sites, name):
