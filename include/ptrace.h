@@ -369,6 +369,8 @@ PT_API int pt_trace_PAinv_nested(pt_ctx *ctx, const pt_op *op, int n_lev, const 
                                  uint64_t seed, int set0, int n_sets, int dilute, int prec, double tol,
                                  int maxit, double *est_out, pt_stats *stats);
 
+/* ---------------------------------------------------------------- deflation */
+
 /* Deflation of given triplets (Sec. 2.4, Eq. (6)) for the displaced trace.
  * With U, V (n_ev columns each) and M = (U^H A V)^{-1} (the caller's small
  * matrix; for singular triplets, diag(1 / sigma)):
@@ -587,6 +589,8 @@ PT_API int pt_site_blocks_apply(pt_ctx *ctx, int N, const double *blocks_dev, co
  * device form synchronises the stream. */
 PT_API int pt_site_blocks_invert_host(int n, const double *blocks, double shift, double *inv_out);
 PT_API int pt_site_blocks_invert(pt_ctx *ctx, int N, const double *blocks_dev, double shift, double *inv_dev);
+
+/* ---------------------------------------------------------------- gradient */
 
 /* Adjoint gradient of the probed estimate T = sum_s est[s] for one
  * displacement p (not in the paper): with x = A^{-1} v, y = A^{-+} P^T v,
