@@ -11,6 +11,11 @@ __host__ __device__ __forceinline__ zd zsub(zd a, zd b) { return {a.re - b.re, a
 __host__ __device__ __forceinline__ zd zmulc(zd a, zd b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
 __host__ __device__ __forceinline__ zd zconj(zd a) { return {a.re, -a.im}; }
 __host__ __device__ __forceinline__ zd zscal(zd a, double s) { return {a.re * s, a.im * s}; }
+__host__ __device__ __forceinline__ zd zdiv(zd a, zd b) {
+    const double d = b.re * b.re + b.im * b.im;
+    return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+__host__ __device__ __forceinline__ double zabs(zd a) { return sqrt(a.re * a.re + a.im * a.im); }
 
 // g_mu (4 x 4, row-major) in the chiral Euclidean basis of the library's
 // hopping term: g_k = [[0, -i s_k], [i s_k, 0]] for mu = k - 1 = 0, 1, 2 (s_k
