@@ -570,21 +570,23 @@ PT_API int pt_mg_cycle_host(const int dims[4], double m2, int block, int nu, dou
  * (device); iters_out (int32 [nrhs]) and relres_out (float64 [nrhs], true
  * relative residual): host, may be NULL.  1 <= nv <= 8, 6 block^4 >= nv,
  * 1 <= restart <= 64, 0 <= nu <= 16.  PT_ERR_NOCONV if a right-hand side
- * reaches maxit first.  Synchronises. */
-PT_API int pt_wmg_solve(pt_ctx *ctx, const pt_op *op, int block, int nv, int sweeps, int nu, double omega,
-                        int restart, uint64_t seed, const double *b_dev, double *x_dev, int nrhs, double tol,
-                        int maxit, int *iters_out, double *relres_out);
+ * reaches maxit first.  csw != 0 makes the operator the clover one, A_W + C
+ * (pt_clover_blocks; a temporary stream-ordered copy of the blocks).
+ * Synchronises. */
+PT_API int pt_wmg_solve(pt_ctx *ctx, const pt_op *op, double csw, int block, int nv, int sweeps, int nu,
+                        double omega, int restart, uint64_t seed, const double *b_dev, double *x_dev, int nrhs,
+                        double tol, int maxit, int *iters_out, double *relres_out);
 
 /* The same solve on the host (links U_host in the user layout; no GPU), and
  * the setup alone: P_out complex128 [Nc][2][nv][block^4][6] (coarse site,
  * chirality half, vector, site in the block, spin-colour component in the
  * half) and Ac_out complex128 [Nc][9][2 nv][2 nv] (stencil slot 0 = self,
  * 1 + 2 mu = +mu, 2 + 2 mu = -mu). */
-PT_API int pt_wmg_solve_host(const int dims[4], const double *U_host, double kappa, int antip, int block, int nv,
-                             int sweeps, int nu, double omega, int restart, uint64_t seed, const double *b, double *x,
-                             int nrhs, double tol, int maxit, int *iters_out, double *relres_out);
-PT_API int pt_wmg_setup_host(const int dims[4], const double *U_host, double kappa, int antip, int block, int nv,
-                             int sweeps, double omega, uint64_t seed, double *P_out, double *Ac_out);
+PT_API int pt_wmg_solve_host(const int dims[4], const double *U_host, double kappa, double csw, int antip, int block,
+                             int nv, int sweeps, int nu, double omega, int restart, uint64_t seed, const double *b,
+                             double *x, int nrhs, double tol, int maxit, int *iters_out, double *relres_out);
+PT_API int pt_wmg_setup_host(const int dims[4], const double *U_host, double kappa, double csw, int antip, int block,
+                             int nv, int sweeps, double omega, uint64_t seed, double *P_out, double *Ac_out);
 
 /* ---------------------------------------------------------------- clover */
 

@@ -17,6 +17,8 @@
 //   outer        FGMRES(m) (the coarse solve is inexact, so the cycle is not a
 //                fixed linear map).
 //
+// With c_sw != 0 the operator is the clover one, A = A_W + C (the site blocks
+// of clover.cu in the fine apply, P^H C P in the coarse self blocks).
 // All arithmetic FP64, fields in the user layout (complex128 [N][4][3]).  The
 // per-site arithmetic and the solver are shared by the device entry point and
 // a host-only twin: only the loop over sites differs.
@@ -38,6 +40,7 @@ struct WMG {
     int b, bs, nv;               // block side, sites per block, vectors per aggregate
     double kappa, omega;
     EoOp o;                      // gammas and the time boundary
+    const double *Cb;            // clover site blocks [N][12][12] complex, or NULL (plain Wilson)
     __host__ __device__ int dc() const { return 2 * nv; }   // coarse degrees of freedom per coarse site
 };
 
@@ -91,6 +94,12 @@ __host__ __device__ __forceinline__ void wmg_apply_site(const WMG &m, const User
     else eo_wilson_hop(m.g, U0, m.o, F, 0, i, xc, acc);
     const double *xi = x + (size_t)i * 24;
     for (int c = 0; c < 12; ++c) out[c] = zsub(zd{xi[2 * c], xi[2 * c + 1]}, zscal(acc[c], m.kappa));
+    if (m.Cb) {                                          // + C(x) x(x)
+        const double *Ci = m.Cb + (size_t)i * 288;
+        for (int r = 0; r < 12; ++r)
+            for (int c = 0; c < 12; ++c)
+                out[r] = zadd(out[r], zmulc(zd{Ci[(r * 12 + c) * 2], Ci[(r * 12 + c) * 2 + 1]}, zd{xi[2 * c], xi[2 * c + 1]}));
+    }
 }
 
 // counter-based start vector k: components uniform in [-1, 1) (SplitMix64 outputs)
@@ -244,6 +253,29 @@ __host__ __device__ void wmg_build_site(const WMG &m, const L &U, const double *
                     e[0] += s.re;
                     e[1] += s.im;
                 }
+        // the clover term (site-local): P_row^H C(x) P_col, into the self slot
+        if (m.Cb) {
+            const double *Ci = m.Cb + (size_t)i * 288;
+            for (int ar = 0; ar < 2; ++ar)
+                for (int kr = 0; kr < m.nv; ++kr)
+                    for (int ac = 0; ac < 2; ++ac)
+                        for (int kc = 0; kc < m.nv; ++kc) {
+                            zd s = {0.0, 0.0};
+                            for (int cr = 0; cr < 6; ++cr) {
+                                zd t = {0.0, 0.0};
+                                for (int cc = 0; cc < 6; ++cc) {
+                                    const size_t pc = wmg_pidx(m, B, ac, kc, sl, cc) * 2;
+                                    const size_t ci = ((size_t)(ar * 6 + cr) * 12 + ac * 6 + cc) * 2;
+                                    t = zadd(t, zmulc(zd{Ci[ci], Ci[ci + 1]}, zd{P[pc], P[pc + 1]}));
+                                }
+                                const size_t pr = wmg_pidx(m, B, ar, kr, sl, cr) * 2;
+                                s = zadd(s, zmulc(zd{P[pr], -P[pr + 1]}, t));
+                            }
+                            double *e = A + ((size_t)(ar * m.nv + kr) * dc + ac * m.nv + kc) * 2;
+                            e[0] += s.re;
+                            e[1] += s.im;
+                        }
+        }
         // the hops: inside the block -> slot 0, across a face -> the direction's slot
         for (int mu = 0; mu < 4; ++mu)
             for (int dir = 0; dir < 2; ++dir) {
@@ -600,6 +632,7 @@ static int wmg_geom(const int dims[4], double kappa, int antip, int block, int n
     m->o.kind = 1;
     m->o.antip = antip ? 1 : 0;
     m->o.G = make_gammas();
+    m->Cb = nullptr;
     return PT_OK;
 }
 
@@ -620,9 +653,9 @@ static int wmg_solve_all(X &ex, int sweeps, uint64_t seed, int nu, int restart, 
     return rc ? rc : rc_nc;
 }
 
-extern "C" int pt_wmg_solve(pt_ctx *c, const pt_op *op, int block, int nv, int sweeps, int nu, double omega,
-                            int restart, uint64_t seed, const double *b_dev, double *x_dev, int nrhs, double tol,
-                            int maxit, int *iters_out, double *relres_out) {
+extern "C" int pt_wmg_solve(pt_ctx *c, const pt_op *op, double csw, int block, int nv, int sweeps, int nu,
+                            double omega, int restart, uint64_t seed, const double *b_dev, double *x_dev, int nrhs,
+                            double tol, int maxit, int *iters_out, double *relres_out) {
     PT_CHECK_ARG(c && op && op->ctx == c && op->kind == 1, "pt_wmg_solve: a Wilson operator is required");
     PT_CHECK_ARG(nrhs >= 0 && nrhs <= 65535 && tol > 0.0 && maxit >= 1 && sweeps >= 0 && nu >= 0 && nu <= 16 &&
                      restart >= 1 && restart <= 64,
@@ -637,47 +670,59 @@ extern "C" int pt_wmg_solve(pt_ctx *c, const pt_op *op, int block, int nv, int s
     const size_t np = (size_t)ex.m.g.N * 12 * nv * 2, na = (size_t)ex.m.Nc * 9 * ex.m.dc() * ex.m.dc() * 2;
     ex.P = ex.alloc(np);
     ex.Ac = ex.alloc(na);
-    if (!ex.P || !ex.Ac) {
+    double *cb = csw != 0.0 ? ex.alloc((size_t)ex.m.g.N * 288) : nullptr;
+    if (!ex.P || !ex.Ac || (csw != 0.0 && !cb)) {
         pt_set_error("pt_wmg_solve: device allocation failed");
         rc = PT_ERR_OOM;
     } else {
-        rc = wmg_solve_all(ex, sweeps, seed, nu, restart, b_dev, x_dev, nrhs, tol, maxit, iters_out, relres_out);
+        if (cb) rc = pt_clover_blocks(c, op, csw, cb);
+        ex.m.Cb = cb;
+        if (!rc) rc = wmg_solve_all(ex, sweeps, seed, nu, restart, b_dev, x_dev, nrhs, tol, maxit, iters_out,
+                                    relres_out);
     }
     if (ex.P) ex.release(ex.P);
     if (ex.Ac) ex.release(ex.Ac);
+    if (cb) ex.release(cb);
     const cudaError_t ce = cudaStreamSynchronize(c->stream);
     if (!rc && ce != cudaSuccess) rc = pt_cuda_fail(ce, "pt_wmg_solve", __FILE__, __LINE__);
     return rc;
 }
 
-static int wmg_host_init(WMGHost &ex, const int dims[4], const double *U_host, double kappa, int antip, int block,
-                         int nv, double omega, const char *fn) {
+static int wmg_host_init(WMGHost &ex, const int dims[4], const double *U_host, double kappa, double csw, int antip,
+                         int block, int nv, double omega, const char *fn) {
     PT_CHECK_ARG(U_host, "%s: NULL links", fn);
     int rc = wmg_geom(dims, kappa, antip, block, nv, omega, &ex.m, fn);
     if (rc) return rc;
     ex.U0 = UserLinks{U_host};
     ex.P = ex.alloc((size_t)ex.m.g.N * 12 * nv * 2);
     ex.Ac = ex.alloc((size_t)ex.m.Nc * 9 * ex.m.dc() * ex.m.dc() * 2);
+    if (csw != 0.0) {
+        double *cb = ex.alloc((size_t)ex.m.g.N * 288);
+        if ((rc = pt_clover_blocks_host(dims, U_host, kappa, csw, cb))) return rc;
+        ex.m.Cb = cb;
+    }
     return PT_OK;
 }
 
-extern "C" int pt_wmg_solve_host(const int dims[4], const double *U_host, double kappa, int antip, int block, int nv,
-                                 int sweeps, int nu, double omega, int restart, uint64_t seed, const double *b,
-                                 double *x, int nrhs, double tol, int maxit, int *iters_out, double *relres_out) {
+extern "C" int pt_wmg_solve_host(const int dims[4], const double *U_host, double kappa, double csw, int antip,
+                                 int block, int nv, int sweeps, int nu, double omega, int restart, uint64_t seed,
+                                 const double *b, double *x, int nrhs, double tol, int maxit, int *iters_out,
+                                 double *relres_out) {
     PT_CHECK_ARG(nrhs >= 0 && b && x && tol > 0.0 && maxit >= 1 && sweeps >= 0 && nu >= 0 && nu <= 16 &&
                      restart >= 1 && restart <= 64,
                  "pt_wmg_solve_host: bad argument");
     WMGHost ex;
-    int rc = wmg_host_init(ex, dims, U_host, kappa, antip, block, nv, omega, "pt_wmg_solve_host");
+    int rc = wmg_host_init(ex, dims, U_host, kappa, csw, antip, block, nv, omega, "pt_wmg_solve_host");
     if (rc) return rc;
     return wmg_solve_all(ex, sweeps, seed, nu, restart, b, x, nrhs, tol, maxit, iters_out, relres_out);
 }
 
-extern "C" int pt_wmg_setup_host(const int dims[4], const double *U_host, double kappa, int antip, int block, int nv,
-                                 int sweeps, double omega, uint64_t seed, double *P_out, double *Ac_out) {
+extern "C" int pt_wmg_setup_host(const int dims[4], const double *U_host, double kappa, double csw, int antip,
+                                 int block, int nv, int sweeps, double omega, uint64_t seed, double *P_out,
+                                 double *Ac_out) {
     PT_CHECK_ARG(P_out && Ac_out && sweeps >= 0, "pt_wmg_setup_host: bad argument");
     WMGHost ex;
-    int rc = wmg_host_init(ex, dims, U_host, kappa, antip, block, nv, omega, "pt_wmg_setup_host");
+    int rc = wmg_host_init(ex, dims, U_host, kappa, csw, antip, block, nv, omega, "pt_wmg_setup_host");
     if (rc) return rc;
     if ((rc = wmg_setup(ex, sweeps, seed))) return rc;
     const size_t np = (size_t)ex.m.g.N * 12 * nv * 2, na = (size_t)ex.m.Nc * 9 * ex.m.dc() * ex.m.dc() * 2;

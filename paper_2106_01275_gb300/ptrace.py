@@ -105,10 +105,10 @@ _SIGS = {
     "pt_eo_prepare": ([_P, _P, _P, _P, _P, _I], _I),
     "pt_eo_reconstruct": ([_P, _P, _P, _P, _P, _P, _I], _I),
     "pt_eo_clover_blocks": ([_P, _P, _D, _P, _P], _I),
-    "pt_wmg_solve": ([_P, _P, _I, _I, _I, _I, _D, _I, ctypes.c_uint64, _P, _P, _I, _D, _I, _P, _P], _I),
-    "pt_wmg_solve_host": ([ctypes.POINTER(_I), _P, _D, _I, _I, _I, _I, _I, _D, _I, ctypes.c_uint64, _P, _P, _I, _D,
-                           _I, _P, _P], _I),
-    "pt_wmg_setup_host": ([ctypes.POINTER(_I), _P, _D, _I, _I, _I, _I, _D, ctypes.c_uint64, _P, _P], _I),
+    "pt_wmg_solve": ([_P, _P, _D, _I, _I, _I, _I, _D, _I, ctypes.c_uint64, _P, _P, _I, _D, _I, _P, _P], _I),
+    "pt_wmg_solve_host": ([ctypes.POINTER(_I), _P, _D, _D, _I, _I, _I, _I, _I, _D, _I, ctypes.c_uint64, _P, _P, _I,
+                           _D, _I, _P, _P], _I),
+    "pt_wmg_setup_host": ([ctypes.POINTER(_I), _P, _D, _D, _I, _I, _I, _I, _D, ctypes.c_uint64, _P, _P], _I),
     "pt_mg_solve": ([_P, _P, _I, _I, _D, _P, _P, _I, _D, _I, _P, _P], _I),
     "pt_mg_solve_host": ([ctypes.POINTER(_I), _D, _I, _I, _D, _P, _P, _I, _D, _I, _P, _P], _I),
     "pt_mg_cycle_host": ([ctypes.POINTER(_I), _D, _I, _I, _D, _P, _P], _I),
@@ -645,14 +645,14 @@ def trace_eo_host(dims, m2, col, n_colours, mu, p_list, noise="z2", seed=0, set0
     return est, st.as_dict()
 
 
-def wmg_solve(op, b, block=2, nv=4, sweeps=20, nu=2, omega=0.8, restart=30, seed=0, tol=1e-10, maxit=5000):
+def wmg_solve(op, b, block=2, nv=4, sweeps=20, nu=2, omega=0.8, restart=30, seed=0, tol=1e-10, maxit=5000, csw=0.0):
     """pt_wmg_solve (Wilson): (x, iters, relres) for b torch complex128 [nrhs, N, 4, 3] on the device."""
     import torch
     b = _eo_field(op, b, op.N, "b")
     x = torch.empty_like(b)
     iters = np.zeros(b.shape[0], dtype=np.int32)
     relres = np.zeros(b.shape[0], dtype=np.float64)
-    _check(lib().pt_wmg_solve(op.ctx.handle, op._h, int(block), int(nv), int(sweeps), int(nu), float(omega),
+    _check(lib().pt_wmg_solve(op.ctx.handle, op._h, float(csw), int(block), int(nv), int(sweeps), int(nu), float(omega),
                               int(restart), int(seed), _eo_ptr(b), _eo_ptr(x), int(b.shape[0]), float(tol),
                               int(maxit), _np_ptr(iters), _np_ptr(relres)))
     return x, iters, relres
@@ -666,27 +666,29 @@ def _wmg_links(dims, U):
 
 
 def wmg_solve_host(dims, U, kappa, b, block=2, nv=4, sweeps=20, nu=2, omega=0.8, restart=30, seed=0, tol=1e-10,
-                   maxit=5000, antiperiodic_t=True):
+                   maxit=5000, antiperiodic_t=True, csw=0.0):
     """pt_wmg_solve_host (no GPU): (x, iters, relres) for numpy b [nrhs, N, 4, 3] complex."""
     U = _wmg_links(dims, U)
     b = np.ascontiguousarray(np.asarray(b, dtype=np.complex128))
     x = np.zeros_like(b)
     iters = np.zeros(b.shape[0], dtype=np.int32)
     relres = np.zeros(b.shape[0], dtype=np.float64)
-    _check(lib().pt_wmg_solve_host(_ints(dims), _np_ptr(U), float(kappa), 1 if antiperiodic_t else 0, int(block),
+    _check(lib().pt_wmg_solve_host(_ints(dims), _np_ptr(U), float(kappa), float(csw), 1 if antiperiodic_t else 0,
+                                   int(block),
                                    int(nv), int(sweeps), int(nu), float(omega), int(restart), int(seed), _np_ptr(b),
                                    _np_ptr(x), int(b.shape[0]), float(tol), int(maxit), _np_ptr(iters),
                                    _np_ptr(relres)))
     return x, iters, relres
 
 
-def wmg_setup_host(dims, U, kappa, block=2, nv=4, sweeps=20, omega=0.8, seed=0, antiperiodic_t=True):
+def wmg_setup_host(dims, U, kappa, block=2, nv=4, sweeps=20, omega=0.8, seed=0, antiperiodic_t=True, csw=0.0):
     """pt_wmg_setup_host (no GPU): (P [Nc, 2, nv, block^4, 6], Ac [Nc, 9, 2 nv, 2 nv]) complex."""
     U = _wmg_links(dims, U)
     Nc = int(np.prod([d // block for d in dims]))
     P = np.zeros((Nc, 2, nv, block ** 4, 6), dtype=np.complex128)
     Ac = np.zeros((Nc, 9, 2 * nv, 2 * nv), dtype=np.complex128)
-    _check(lib().pt_wmg_setup_host(_ints(dims), _np_ptr(U), float(kappa), 1 if antiperiodic_t else 0, int(block),
+    _check(lib().pt_wmg_setup_host(_ints(dims), _np_ptr(U), float(kappa), float(csw), 1 if antiperiodic_t else 0,
+                                   int(block),
                                    int(nv), int(sweeps), float(omega), int(seed), _np_ptr(P), _np_ptr(Ac)))
     return P, Ac
 

@@ -99,3 +99,23 @@ def test_errors(ptlib):
         ptlib.wmg_solve_host(dims, U, 0.12, b, 2, 9)                                   # nv > 8
     x, its, rel = ptlib.wmg_solve_host(dims, U, 0.12, b)
     assert np.all(x == 0) and its[0] == 0 and rel[0] == 0.0
+
+
+def test_clover_operator(ptlib):
+    """c_sw != 0: the fine operator is A_W + C; the coarse stencil equals the
+    dense P^H A_c P and the solve reproduces the dense clover solve."""
+    from oracle import clover as CL
+    dims, kappa, csw, b, nv = [2, 2, 4, 4], 0.12, 1.7, 2, 3
+    N = int(np.prod(dims))
+    U = inputs.gauge_links(dims, 21, eps=0.6)
+    P, Ac = ptlib.wmg_setup_host(dims, U, kappa, b, nv, 10, 0.8, 2, csw=csw)
+    Pd = _dense_P(P, dims, b)
+    A = D.dense_matrix(CL.WilsonClover(dims, U, kappa, csw))
+    want = Pd.conj().T @ A @ Pd
+    got = _dense_coarse(Ac, [d // b for d in dims])
+    assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
+    _, Ac0 = ptlib.wmg_setup_host(dims, U, kappa, b, nv, 10, 0.8, 2)
+    assert np.abs(Ac - Ac0).max() > 1e-3                                     # the clover term is there
+    rhs = np.random.default_rng(8).standard_normal((1, N, 4, 3)) + 0j
+    x, its, rel = ptlib.wmg_solve_host(dims, U, kappa, rhs, 2, 4, 20, 2, 0.8, 30, 7, tol=1e-10, csw=csw)
+    assert rel[0] <= 1e-10 and np.allclose(x[0].reshape(-1), np.linalg.solve(A, rhs[0].reshape(-1)), atol=1e-8)
