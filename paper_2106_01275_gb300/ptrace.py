@@ -3,6 +3,9 @@
 Argument marshalling only: every step of the estimator runs in the CUDA
 library.  PyTorch provides device memory and the stream.  There is no CPU
 fallback: if the library is missing or no GPU is present the calls raise.
+The `*_host` functions are separate host-only twins of some device entry
+points (the same site arithmetic and steps, run by host loops) that the
+CPU tests use to check that code; no device entry point ever calls them.
 Field layouts are those of the C ABI (see include/ptrace.h):
   scalar fields  torch.float64    [nrhs, N]
   spinor fields  torch.complex128 [nrhs, N, 4, 3]
