@@ -40,3 +40,32 @@ def test_multigrid_blocks(ptlib, coarse, block, seed):
     want = M(r)
     got = ptlib.mg_cycle_host(dims, m2, r, block, 1, 0.8)
     assert np.abs(got - want).max() <= 1e-9 * max(1.0, np.abs(want).max())
+
+
+@settings(max_examples=12, deadline=None)
+@given(dims=st.lists(st.sampled_from([2, 4]), min_size=4, max_size=4), mu=st.integers(0, 3),
+       ps=st.lists(st.integers(-5, 5), min_size=1, max_size=4), k=st.integers(1, 2), noise=st.integers(0, 1),
+       seed=st.integers(0, 10 ** 6))
+def test_even_odd_trace(ptlib, dims, mu, ps, k, noise, seed):
+    import oracle.estimator as OE
+    from oracle.colouring import greedy_colour
+    col, m = greedy_colour(dims, mu, [abs(p) for p in ps], k, 0)
+    est, _ = ptlib.trace_eo_host(dims, 0.3, col, m, mu, ps, noise, seed, 0, 1, tol=1e-11)
+    want = OE.probed_estimates(OE.Laplacian(dims, 0.3), col, m, seed, 1, noise, mu, ps, 1e-13)
+    assert np.allclose(est, want, rtol=1e-8, atol=1e-9 * max(1.0, np.abs(want).max()))
+
+
+@settings(max_examples=6, deadline=None)
+@given(dims=st.sampled_from([[2, 2, 2, 4], [2, 2, 4, 2], [4, 2, 2, 2], [2, 4, 2, 2]]), nv=st.integers(1, 4),
+       seed=st.integers(0, 1000), ap=st.booleans())
+def test_wilson_coarse_stencil(ptlib, dims, nv, seed, ap):
+    import oracle.estimator as OE
+    from oracle import deflation as D
+    from paper_2106_01275_gb300 import inputs
+    from test_wmg_host import _dense_P, _dense_coarse
+    U = inputs.gauge_links(dims, seed, eps=0.5)
+    P, Ac = ptlib.wmg_setup_host(dims, U, 0.12, 2, nv, 5, 0.8, seed, antiperiodic_t=ap)
+    Pd = _dense_P(P, dims, 2)
+    A = D.dense_matrix(OE.Wilson(dims, U, 0.12, ap))
+    want = Pd.conj().T @ A @ Pd
+    assert np.abs(_dense_coarse(Ac, [d // 2 for d in dims]) - want).max() < 1e-12 * np.abs(want).max()
