@@ -608,20 +608,16 @@ static int wmg_geom(const int dims[4], double kappa, int antip, int block, int n
     PT_CHECK_ARG(dims && block >= 1 && nv >= 1 && nv <= WMG_MAXNV && omega > 0.0 && omega <= 1.0,
                  "%s: block >= 1, 1 <= nv <= %d, 0 < omega <= 1", fn, WMG_MAXNV);
     long N = 1;
-    int s = 1, cs = 1;
+    int cs = 1;
     for (int mu = 0; mu < 4; ++mu) {
         PT_CHECK_ARG(dims[mu] >= 1 && dims[mu] % block == 0, "%s: the block side must divide every lattice side", fn);
-        m->g.D[mu] = dims[mu];
-        m->g.stride[mu] = s;
         m->C[mu] = dims[mu] / block;
         m->cstride[mu] = cs;
-        s *= dims[mu];
         cs *= dims[mu] / block;
         N *= dims[mu];
     }
     PT_CHECK_ARG(N <= (1L << 28), "%s: lattice too large", fn);
-    m->g.N = s;
-    m->g.Nh = s / 2;
+    m->g = make_eo_geom(dims);
     m->Nc = cs;
     m->b = block;
     m->bs = block * block * block * block;
