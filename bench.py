@@ -683,6 +683,66 @@ def run_evenodd(args):
     print(json.dumps(out), flush=True)
 
 
+def run_multigrid(args):
+    """Two-level multigrid against the engine's plain FP64 solves (one slot),
+    same seeded right-hand sides: the Laplacian at m2 = 0.001 on 16^4 (CG
+    against multigrid-preconditioned CG) and Wilson at kappa = 0.124 on
+    16^3 x 32 with and without the clover term (BiCGStab against adaptive
+    multigrid FGMRES).  Reports iterations, seconds and the largest
+    difference of the solutions (relative to their largest entry)."""
+    import torch
+    from paper_2106_01275_gb300 import inputs
+    from paper_2106_01275_gb300 import ptrace as pt
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    ctx = pt.Context(local)
+    small = args.case == "small"
+    rng = np.random.default_rng(SEED)
+    rows = []
+    dl = [8, 8, 8, 8] if small else [16, 16, 16, 16]
+    dw = [4, 4, 4, 4] if small else [16, 16, 16, 32]
+    cases = [("laplacian", dl, 0.001, 0.0), ("wilson", dw, 0.124, 0.0), ("clover", dw, 0.124, 1.0)]
+    for kind, dims, par, csw in cases:
+        N = int(np.prod(dims))
+        if kind == "laplacian":
+            op = pt.laplacian(ctx, dims, par)
+            b = torch.as_tensor(rng.standard_normal((1, N))).cuda()
+        else:
+            op = pt.wilson(ctx, dims, torch.as_tensor(inputs.gauge_links(dims, 1234)).cuda(), par, True)
+            b = torch.as_tensor(rng.standard_normal((1, N, 4, 3)) + 0j).cuda()
+        t_full, it_full, diff = None, None, None
+        if csw == 0.0:
+            ctx.set_max_slots(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            xf, itf, _, _ = pt.solve(op, b, "fp64", 1e-10, 100000)
+            torch.cuda.synchronize()
+            t_full, it_full = time.perf_counter() - t0, int(itf[0])
+            ctx.set_max_slots(0)
+        t0 = time.perf_counter()
+        if kind == "laplacian":
+            xm, itm, relm = pt.mg_solve(op, b, 2, 2, 0.8, 1e-10, 10000)
+        else:
+            xm, itm, relm = pt.wmg_solve(op, b, 2, 4, 20, 2, 0.8, 30, SEED, 1e-10, 5000, csw=csw)
+        torch.cuda.synchronize()
+        t_mg = time.perf_counter() - t0
+        if t_full is not None:
+            diff = float((xf - xm).abs().max() / xm.abs().max())
+        rows.append({"operator": kind, "lattice": dims, "iters_plain": it_full, "iters_multigrid": int(itm[0]),
+                     "seconds_plain": t_full, "seconds_multigrid": t_mg, "relres_multigrid": float(relm[0]),
+                     "max_rel_diff": diff})
+    ratios = [r["iters_plain"] / r["iters_multigrid"] for r in rows if r["iters_plain"]]
+    out = {"metric": "two-level multigrid: Krylov iterations and seconds of FP64 solves, plain vs multigrid",
+           "value": float(np.mean(ratios)), "unit": "x (iterations plain / multigrid, mean over operators)",
+           "higher_is_better": True, "n_gpus": 1, "steps": 1, "warmup": 0, "data": "synthetic",
+           "config": {"workload": "multigrid: %s; one Gaussian right-hand side each, FP64 to 1e-10"
+                                  % "; ".join("%s %s" % (r["operator"], "x".join(map(str, r["lattice"]))) for r in rows)},
+           "cases": rows}
+    print(json.dumps(out), flush=True)
+
+
 def oracle_sample(W, seconds):
     """The oracle as it stands, on a bounded sample of the workload: probes of
     one colouring (set 0, then further sets) solved one by one with its FP64
@@ -774,7 +834,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="lap16", choices=["lap16", "wilson24", "grad32", "colour", "deflation", "evenodd"])
+    ap.add_argument("--workload", default="lap16", choices=["lap16", "wilson24", "grad32", "colour", "deflation", "evenodd",
+                                                        "multigrid"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--skip-baselines", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="use the engine's default parameters")
@@ -793,6 +854,8 @@ def main():
         run_deflation(args)
     elif args.workload == "evenodd":
         run_evenodd(args)
+    elif args.workload == "multigrid":
+        run_multigrid(args)
     else:
         run_ours(args)
 

@@ -173,3 +173,52 @@ def test_evenodd_leg_json_line(monkeypatch, capsys):
     for c in d["cases"]:
         assert sum(c["iters_evenodd"]) < sum(c["iters_full"]) and c["max_rel_diff"] < 1e-8, c
     assert d["trace"]["max_rel_diff"] < 1e-7 and d["trace"]["colours"] >= 2, d["trace"]
+
+
+def test_multigrid_leg_json_line(monkeypatch, capsys):
+    """`bench.py --workload multigrid --case small` on the CPU: plain solves
+    from the oracle, multigrid ones from the library's host twins; fewer
+    multigrid iterations and agreeing solutions."""
+    import numpy as np
+    import torch
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle.estimator as OE
+    from paper_2106_01275_gb300 import ptrace as pt
+
+    monkeypatch.setattr(torch.cuda, "set_device", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(torch.Tensor, "cuda", lambda self, *a, **k: self)
+    monkeypatch.setattr(pt, "Context", lambda dev: types.SimpleNamespace(device=dev, set_max_slots=lambda n: None))
+    monkeypatch.setattr(pt, "laplacian", lambda ctx, dims, m2: types.SimpleNamespace(kind=0, dims=dims, m2=m2))
+    monkeypatch.setattr(pt, "wilson", lambda ctx, dims, U, kappa, ap: types.SimpleNamespace(
+        kind=1, dims=dims, U=np.asarray(U), kappa=kappa))
+
+    def solve(op, b, prec, tol, maxit):
+        o = OE.Laplacian(op.dims, op.m2) if op.kind == 0 else OE.Wilson(op.dims, op.U, op.kappa)
+        x, it, _ = o.solve(b.numpy()[0], tol)
+        return torch.as_tensor(np.asarray(x).reshape(b.shape)), np.array([it]), None, {}
+
+    def mg_solve(op, b, block, nu, omega, tol, maxit):
+        x, its, rel = pt.mg_solve_host(op.dims, op.m2, b.numpy(), block, nu, omega, tol, maxit)
+        return torch.as_tensor(x), its, rel
+
+    def wmg_solve(op, b, block, nv, sweeps, nu, omega, restart, seed, tol, maxit, csw=0.0):
+        x, its, rel = pt.wmg_solve_host(op.dims, op.U, op.kappa, b.numpy(), block, nv, sweeps, nu, omega, restart,
+                                        seed, tol, maxit, csw=csw)
+        return torch.as_tensor(x), its, rel
+
+    monkeypatch.setattr(pt, "solve", solve)
+    monkeypatch.setattr(pt, "mg_solve", mg_solve)
+    monkeypatch.setattr(pt, "wmg_solve", wmg_solve)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "multigrid", "--case", "small"])
+    bench.main()
+    lines = [l for l in capsys.readouterr().out.strip().splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["config"]["workload"].startswith("multigrid:") and len(d["cases"]) == 3 and d["value"] > 1.0
+    for c in d["cases"]:
+        assert c["relres_multigrid"] <= 1e-10, c
+        if c["iters_plain"] is not None:
+            assert c["iters_multigrid"] < c["iters_plain"] and c["max_rel_diff"] < 1e-7, c
