@@ -127,14 +127,15 @@ class ColourDB:
         device, m, tile, hit).  A miss colours the tile on the GPU and stores it."""
         import torch
         from . import ptrace as pt
-        tile = pt.tile_dims(dims, mu, p_list, k)
-        got = self.get(tile, mu, p_list, k, order)
+        ps = canonical_p(p_list)          # the library takes |p|: the neighbourhood is symmetric in p
+        tile = pt.tile_dims(dims, mu, ps, k)
+        got = self.get(tile, mu, ps, k, order)
         hit = got is not None
         if hit:
             tcol, m = got
             tdev = torch.as_tensor(tcol).to("cuda:%d" % ctx.device)
         else:
-            tdev, m = pt.colour(ctx, tile, mu, canonical_p(p_list), k, order)
-            self.put(tile, mu, p_list, k, order, tdev.cpu().numpy(), m)
+            tdev, m = pt.colour(ctx, tile, mu, ps, k, order)
+            self.put(tile, mu, ps, k, order, tdev.cpu().numpy(), m)
         col = pt.tile_replicate(ctx, tile, tdev, dims, out)
         return col, m, tile, hit

@@ -82,10 +82,16 @@ def test_invalid_colourings_are_not_stored(tmp_path):
 def _fake_binding(calls):
     """ptrace stand-in on the CPU: the oracle's tile policy, greedy colouring
     and tile repetition, numpy arrays for device buffers."""
+    def _ps(name, p_list):                    # the library's range check (0 <= p <= 4096)
+        if not 1 <= len(p_list) <= 64 or any(not 0 <= int(p) <= 4096 for p in p_list):
+            raise RuntimeError("%s: displacement out of range" % name)
+
     def tile_dims(dims, mu, p_list, k):
+        _ps("pt_tile_dims", p_list)
         return list(OT.tile_dims(dims, mu, p_list, k))
 
     def colour(ctx, dims, mu, p_list, k, order):
+        _ps("pt_colour", p_list)
         calls.append(("colour", list(dims), list(p_list), k, order))
         import torch
         c, m = greedy_colour(dims, mu, p_list, k, {"natural": 0, "redblack": 1}.get(order, order))
