@@ -235,8 +235,9 @@ PT_API int pt_colour_conflicts(pt_ctx *ctx, const int dims[4], int mu, const int
  * or one running under a fixed device-memory cap).  Same result as
  * pt_colour_conflicts, without a context: it runs on the calling thread's
  * current device and on `stream` (a cudaStream_t; NULL = the default stream).
- * Scratch is a file-scope device array of the library: at most 16384 stencil
- * offsets (larger stencils return PT_ERR_ARG) and one counter, 256 KiB in
+ * Scratch is a file-scope device array of the library: at most 16384 distinct
+ * stencil offsets after repeats from overlapping displacements are merged
+ * (larger stencils return PT_ERR_ARG) and one counter, 256 KiB in
  * total, held by every device that loads the library until the process
  * exits.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.

@@ -60,8 +60,27 @@ __global__ void k_conflicts_noalloc(Geom g, int n_off, const int32_t *__restrict
     if (threadIdx.x == 0 && v[0] > 0.0) atomicAdd(&s->count, (unsigned long long)v[0]);
 }
 
+static bool noalloc_less(const int4 &a, const int4 &b) {
+    if (a.x != b.x) return a.x < b.x;
+    if (a.y != b.y) return a.y < b.y;
+    if (a.z != b.z) return a.z < b.z;
+    return a.w < b.w;
+}
+
+static bool noalloc_same(const int4 &a, const int4 &b) { return a.x == b.x && a.y == b.y && a.z == b.z && a.w == b.w; }
+
+// Sort the first n rows of the staging table and drop repeats; returns the
+// number of distinct rows.
+static int noalloc_compact(int n) {
+    std::sort(g_noalloc_host_off, g_noalloc_host_off + n, noalloc_less);
+    return (int)(std::unique(g_noalloc_host_off, g_noalloc_host_off + n, noalloc_same) - g_noalloc_host_off);
+}
+
 // Stencil of Eq. (8) written into the static staging table (sorted, unique).
-// Returns the number of offsets, or -1 if it exceeds PT_NOALLOC_MAX_OFFSETS.
+// Repeated or overlapping displacements produce the same offset more than
+// once; when the table fills up it is compacted and filling goes on, so the
+// limit applies to the distinct offsets only.  Returns the number of offsets,
+// or -1 if the distinct ones exceed PT_NOALLOC_MAX_OFFSETS.
 static int noalloc_stencil(int mu, const int *p_list, int n_p, int k) {
     int n = 0;
     for (int q = 0; q < n_p; ++q) {
@@ -81,19 +100,14 @@ static int noalloc_stencil(int mu, const int *p_list, int n_p, int k) {
                             dm += abs(o[nu] + c);
                         }
                         if (dp > k && dm > k) continue;
-                        if (n == PT_NOALLOC_MAX_OFFSETS) return -1;
+                        if (n == PT_NOALLOC_MAX_OFFSETS) {
+                            n = noalloc_compact(n);
+                            if (n == PT_NOALLOC_MAX_OFFSETS) return -1;
+                        }
                         g_noalloc_host_off[n++] = make_int4(o[0], o[1], o[2], o[3]);
                     }
     }
-    auto less = [](const int4 &a, const int4 &b) {
-        if (a.x != b.x) return a.x < b.x;
-        if (a.y != b.y) return a.y < b.y;
-        if (a.z != b.z) return a.z < b.z;
-        return a.w < b.w;
-    };
-    auto same = [](const int4 &a, const int4 &b) { return a.x == b.x && a.y == b.y && a.z == b.z && a.w == b.w; };
-    std::sort(g_noalloc_host_off, g_noalloc_host_off + n, less);
-    return (int)(std::unique(g_noalloc_host_off, g_noalloc_host_off + n, same) - g_noalloc_host_off);
+    return noalloc_compact(n);
 }
 
 extern "C" int pt_colour_conflicts_noalloc(void *stream, const int dims[4], int mu, const int *p_list, int n_p,

@@ -50,3 +50,21 @@ def test_noalloc_rejects_oversized_stencil(pt):
     with pytest.raises(pt.PtraceError) as ei:
         pt.conflicts_noalloc([2, 2, 2, 2], 0, [0], 12, col)      # |N(0,0,12)| in 4D exceeds 16384
     assert ei.value.code == pt.PT_ERR_ARG
+
+
+def test_noalloc_overlapping_displacements_fit(pt):
+    """Repeated displacements produce each stencil offset twice: 2 x 11968
+    raw rows for (p = 0, k = 11) listed twice, above the 16384-offset limit,
+    but 11968 distinct ones, which fit.  The result must equal the context
+    version's on an invalid and a partly valid colouring."""
+    import torch
+    ctx = pt.Context(0)
+    dims, mu, k = [6, 5, 7, 4], 3, 11
+    assert pt.stencil(mu, [0], k).shape[0] == 11968
+    N = int(np.prod(dims))
+    rng = np.random.default_rng(7)
+    for colv in (np.zeros(N, np.int32), rng.integers(0, N // 2, N).astype(np.int32)):
+        col = torch.as_tensor(colv).cuda()
+        want = pt.conflicts(ctx, dims, mu, [0], k, col)
+        for p in ([0, 0], [0, 0, 0]):
+            assert pt.conflicts_noalloc(dims, mu, p, k, col) == want
