@@ -519,7 +519,8 @@ PT_API int pt_eo_solve_host(int kind, const int dims[4], double m2, double kappa
  * computed on the host after one reduction per step.  Every lattice side
  * even; 1 <= n_p <= 32.  stats: n_rhs, inner and outer iterations,
  * site_rhs_applies (inner iterations x N), kernel launches, largest final
- * relative residual of the even system, n_slots = batch size.
+ * relative residual of the even system, n_slots = batch size.  noise must be
+ * PT_NOISE_Z2 (the operator is real; PT_ERR_ARG otherwise).
  * PT_ERR_NOCONV if a task reaches maxit (est_out still written).
  * Synchronises. */
 PT_API int pt_trace_PAinv_eo(pt_ctx *ctx, const pt_op *op, const int32_t *col_dev, int n_colours, int mu,

@@ -484,7 +484,10 @@ static int et_params(const int dims[4], double m2, int n_colours, int mu, const 
     PT_CHECK_ARG(N <= (1L << 30), "%s: lattice too large", fn);
     PT_CHECK_ARG(n_colours >= 1 && mu >= 0 && mu < 4 && n_p >= 1 && n_p <= PT_MAX_P, "%s: bad colours, mu or n_p",
                  fn);
-    PT_CHECK_ARG(noise == PT_NOISE_Z2 || noise == PT_NOISE_Z4, "%s: noise must be Z2 or Z4", fn);
+    // the Laplacian is real: its probes are real Z2 vectors (a complex Z4 probe
+    // would be solved through its real part and contracted with its conjugate,
+    // an estimate of half the trace)
+    PT_CHECK_ARG(noise == PT_NOISE_Z2, "%s: the real Laplacian takes Z2 noise", fn);
     PT_CHECK_ARG(set0 >= 0 && n_sets >= 1 && (long)n_sets * n_colours <= (1L << 30), "%s: bad sets", fn);
     PT_CHECK_ARG(tol > 0.0 && maxit >= 1 && delta > 0.0 && delta < 1.0, "%s: bad tol, maxit or delta", fn);
     P->g = make_eo_geom(dims);

@@ -1,6 +1,6 @@
 """Even-odd trace estimation for the Laplacian (pt_trace_PAinv_eo), run by
 its host twin (the same per-site arithmetic and steps; no GPU): the probed
-estimates equal the oracle's (Eqs. (1), (5)) for Z2 and Z4 noise, several
+estimates equal the oracle's (Eqs. (1), (5)) for Z2 noise, several
 displacements, set offsets and colourings; iterations against the full
 system; argument and iteration-limit errors."""
 import numpy as np
@@ -12,7 +12,7 @@ from oracle.colouring import greedy_colour
 
 @pytest.mark.parametrize("dims,m2,mu,ps,k,noise,set0,n_sets", [
     ([4, 4, 4, 4], 0.1, 0, [0, 1, 2], 1, 0, 0, 2),
-    ([6, 4, 2, 8], 0.05, 3, [1, 3], 2, 1, 3, 2),
+    ([6, 4, 2, 8], 0.05, 3, [1, 3], 2, 0, 3, 2),
     ([8, 8, 4, 4], 0.01, 1, [0, 4], 1, 0, 0, 1),
 ])
 def test_estimates_match_the_oracle(ptlib, dims, m2, mu, ps, k, noise, set0, n_sets):
@@ -46,6 +46,8 @@ def test_iterations_against_the_full_system(ptlib):
 
 def test_errors(ptlib):
     col = np.zeros(3 * 4 * 4 * 4, dtype=np.int32)
+    with pytest.raises(ptlib.PtraceError):                                 # complex noise, real operator
+        ptlib.trace_eo_host([4, 4, 4, 4], 0.1, np.zeros(256, np.int32), 1, 0, [1], "z4")
     with pytest.raises(ptlib.PtraceError):
         ptlib.trace_eo_host([3, 4, 4, 4], 0.1, col, 1, 0, [1])              # odd side
     with pytest.raises(ptlib.PtraceError):
@@ -63,6 +65,6 @@ def test_errors(ptlib):
 def test_edge_cases_match_the_oracle(ptlib, dims, mu, ps):
     m2 = 0.2
     col, m = greedy_colour(dims, mu, [1], 1, 0)
-    est, _ = ptlib.trace_eo_host(dims, m2, col, m, mu, ps, "z4", 11, 1, 2, tol=1e-11)
-    want = OE.probed_estimates(OE.Laplacian(dims, m2), col, m, 11, 2, 1, mu, ps, 1e-13, set0=1)
+    est, _ = ptlib.trace_eo_host(dims, m2, col, m, mu, ps, "z2", 11, 1, 2, tol=1e-11)
+    want = OE.probed_estimates(OE.Laplacian(dims, m2), col, m, 11, 2, 0, mu, ps, 1e-13, set0=1)
     assert np.allclose(est, want, rtol=1e-8, atol=1e-9 * np.abs(want).max())
