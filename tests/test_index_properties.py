@@ -44,9 +44,9 @@ def test_multigrid_blocks(ptlib, coarse, block, seed):
 
 @settings(max_examples=12, deadline=None)
 @given(dims=st.lists(st.sampled_from([2, 4]), min_size=4, max_size=4), mu=st.integers(0, 3),
-       ps=st.lists(st.integers(-5, 5), min_size=1, max_size=4), k=st.integers(1, 2), noise=st.integers(0, 1),
-       seed=st.integers(0, 10 ** 6))
-def test_even_odd_trace(ptlib, dims, mu, ps, k, noise, seed):
+       ps=st.lists(st.integers(-5, 5), min_size=1, max_size=4), k=st.integers(1, 2), seed=st.integers(0, 10 ** 6))
+def test_even_odd_trace(ptlib, dims, mu, ps, k, seed):
+    noise = 0                                    # Z2: the Laplacian is real
     import oracle.estimator as OE
     from oracle.colouring import greedy_colour
     col, m = greedy_colour(dims, mu, [abs(p) for p in ps], k, 0)

@@ -333,9 +333,67 @@ def test_table6_speedup_arithmetic():
         assert abs(s - float(r[6])) < 0.005 * float(r[6]), (p, k)
 
 
-def test_eq7_eq8_definitions():
-    assert E.speedup_over_cp(10.0, 4, 2.0, 5) == pytest.approx(4.0)
-    assert E.normalised_relative_error(4.0, 200, 800, 2.0) == pytest.approx(0.5)
+def test_eq16_eq17_mean_what_sec43_says_at_equal_work():
+    """Eqs. (16) and (17) against what they measure (Sec. 4.3): both compare
+    estimators at the same number of solves.  4^4 Laplacian, m^2 = 0.1,
+    p = 1 along dim 0: classical probing with the (0, 1) colouring (H_0,
+    m_0 colours) and displaced probing with the (1, 1) colouring (H_p, m_p).
+    Independent Z2 sets are drawn, each one's estimate z^T (B (.) H H^T) z
+    formed from the dense B = P A^{-1}, and the sets are averaged in groups
+    that cost the same budget of solves.  Eq. (17) must equal the observed
+    standard deviation of a budget-M mean over |tr|, and Eq. (16) the ratio of
+    the observed variances of the classical and displaced means at equal
+    budget.  A missing square root, a transposed m_0 / m_p or m_p / M, or a
+    missing trace each miss by far more than the sampling error."""
+    from oracle import deflation as D
+    dims, m2, mu, p = [4, 4, 4, 4], 0.1, 0, 1
+    B = D.displacement_matrix(dims, mu, p) @ np.linalg.inv(D.dense_matrix(E.Laplacian(dims, m2)))
+    tr = float(np.trace(B))
+    c0, m0 = greedy_colour(dims, mu, [0], 1, 0)
+    cp, mp = greedy_colour(dims, mu, [p], 1, 0)
+    assert m0 != mp
+    M = int(np.lcm(m0, mp)) * 4                        # the common budget of solves
+    rng = np.random.default_rng(2021)
+    trials = 3000
+
+    def budget_means(col, m):
+        Bm = B * (col[:, None] == col[None, :])
+        k = M // m                                      # sets that the budget buys
+        Z = rng.choice([-1.0, 1.0], size=(trials * k, B.shape[0]))
+        T = np.einsum('ni,ni->n', Z @ Bm.T, Z)          # one estimate per set
+        return T.reshape(trials, k).mean(axis=1), float(np.var(T, ddof=1))
+
+    mean0, v0 = budget_means(c0, m0)
+    meanp, vp = budget_means(cp, mp)
+    # the per-set variances are the exact ones (Eq. (2) general form, pinned by enumeration)
+    assert abs(v0 / V.exact_variance(B, c0, 0) - 1) < 0.05
+    assert abs(vp / V.exact_variance(B, cp, 0) - 1) < 0.05
+    nre_p = E.normalised_relative_error(vp, mp, M, tr)
+    assert abs(np.std(meanp, ddof=1) / abs(tr) / nre_p - 1) < 0.06
+    nre_0 = E.normalised_relative_error(v0, m0, M, tr)
+    assert abs(np.std(mean0, ddof=1) / abs(tr) / nre_0 - 1) < 0.06
+    s_cp = E.speedup_over_cp(v0, m0, vp, mp)
+    assert abs(np.var(mean0, ddof=1) / np.var(meanp, ddof=1) / s_cp - 1) < 0.12
+    assert s_cp > 1.0                                   # displaced probing wins for p = 1
+
+
+def test_eq16_against_eq15_on_table6():
+    """Eq. (16) is the ratio of two Eq. (15) speedups over the same Hutchinson
+    variance: for every p of Table 6 and every pair of its colourings, with the
+    printed variances and colour counts (Eq. (15) itself reproduces Table 6's
+    printed speedups, above)."""
+    rows = [r for r in read_golden("table6_speedup.txt")]
+    by_p = {}
+    for r in rows:
+        by_p.setdefault(int(r[0]), []).append((float(r[3]), int(r[4]), float(r[5])))
+    n = 0
+    for p, rs in by_p.items():
+        for (vh, ma, va) in rs:
+            for (_, mb, vb) in rs:
+                want = E.speedup_over_hutchinson(vh, vb, mb) / E.speedup_over_hutchinson(vh, va, ma)
+                assert E.speedup_over_cp(va, ma, vb, mb) == pytest.approx(want, rel=1e-12)
+                n += 1
+    assert n > 500
 
 
 # ---------------------------------------------------------------- gradient
