@@ -112,6 +112,14 @@ PT_API int pt_set_memory_budget(pt_ctx *ctx, size_t bytes);
  * beyond the memory budget).  n = 1 gives the plain one-RHS-at-a-time solve. */
 PT_API int pt_set_max_slots(pt_ctx *ctx, int n);
 
+/* Cap on the CUDA-graph launches of one solver-engine run (a host-side
+ * watchdog for callers with a time budget; 0 = the engine's own bound, which
+ * every run meets: maxit Krylov iterations per right-hand side plus a margin
+ * per outer restart and per retire/refill).  A run that reaches the cap stops
+ * between two graph launches, with nothing left in flight, and returns
+ * PT_ERR_TIMEOUT; the context stays usable. */
+PT_API int pt_set_launch_limit(pt_ctx *ctx, int64_t n);
+
 /* Free parameters of the solver engine (not in the paper).
  *   delta        inner relative tolerance of a mixed-precision Krylov cycle
  *                (0 for FP64: the inner solve runs to the outer tolerance)
@@ -126,6 +134,13 @@ PT_API int pt_set_max_slots(pt_ctx *ctx, int n);
  *                outer steps run as CUDA-graph branches beside the inner
  *                Krylov kernels (they work on disjoint right-hand sides);
  *                0: one kernel after another
+ *   evenodd      Laplacian with every lattice side even: 1 solves each
+ *                right-hand side through the Schur complement on the even
+ *                sites, S = d - H_eo H_oe / d (d = 8 + m2, H the hops), with
+ *                the odd half rebuilt as x_o = (b_o + H_oe x_e) / d; the
+ *                stopping test stays the full system's ||b - A x|| / ||b||.
+ *                0: the full system.  The default is 1 where allowed; it is
+ *                ignored for Wilson, for odd sides and by pt_grad.
  * seconds_per_rhs is an output of pt_autotune (device time per trial RHS). */
 typedef struct pt_tune {
     double delta;
@@ -133,13 +148,15 @@ typedef struct pt_tune {
     int32_t graph_iters;
     int32_t rhs_block;
     int32_t overlap;
+    int32_t evenodd;
     double seconds_per_rhs;
 } pt_tune;
 
 /* Autotuner: solves the same trial right-hand sides (up to trial_rhs probes
  * of one noise set spread over the colours of col_dev) with candidate
- * parameters, by coordinate descent over delta (mixed precision), rhs_block
- * and group (Wilson) and graph_iters (overlap stays as set), keeps the fastest, and stores it in the context
+ * parameters, by coordinate descent over evenodd (Laplacian with even sides),
+ * delta (mixed precision), rhs_block and group (Wilson) and graph_iters
+ * (overlap stays as set), keeps the fastest, and stores it in the context
  * for this operator's (kind, precision, lattice); later solves, traces and
  * gradients with that key use it.  *best (host) receives it.  Synchronises. */
 PT_API int pt_autotune(pt_ctx *ctx, const pt_op *op, const int32_t *col_dev, int n_colours, int mu, int noise,

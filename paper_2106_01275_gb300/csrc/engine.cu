@@ -55,6 +55,8 @@ struct TaskStat {
 struct EP {
     Geom g;
     int kind, nsb, R, gs, vec4;
+    int eo;                    // Laplacian on the even Schur complement (inner vectors on the even sites)
+    int nsite;                 // entries of a slot field: N, or N / 2 in even-odd mode
     int rhs_block;             // Wilson applies: right-hand sides per item (1 or 2)
     int overlap;               // groups run as graph branches: the inner list holds PH_INNER slots only
     // nested trace mode (n_lev > 0): the tasks are the classes of the finest of
@@ -78,7 +80,8 @@ struct EP {
     const double *B_user;      // solve mode: user layout sources
     double *X_user;            // solve mode: user layout solutions
     double *x64;
-    void *e, *r, *pv, *q, *s, *t, *r0, *p1;   // p1: second CG direction buffer
+    double *t64;               // even-odd: H_oe x64 on the odd sites (FP64)
+    void *e, *r, *pv, *q, *s, *t, *r0, *p1;   // p1: second CG direction buffer; even-odd: t = H_oe p (odd sites)
     Slot *slots;
     double *partials;
     int *counters, *lists, *counts, *head, *flags;
@@ -468,7 +471,7 @@ __global__ void k_fin_contract(EP P) {
 template <int KIND, typename S>
 __global__ void __launch_bounds__(PT_BLOCK) k_outer_update(EP P) {
     typedef Fld<KIND, S> F;
-    const int N = P.g.N;
+    const int N = P.nsite;            // field entries per slot (N/2 in even-odd mode)
     ITEM_LOOP(LIST_OUTER)
         const int ph = P.slots[j].phase;
         if (ph != PH_START && ph != PH_OUTER) continue;
@@ -635,7 +638,7 @@ template <typename S>
 __global__ void __launch_bounds__(PT_BLOCK) k_cg_update(EP P) {
     typedef typename ArithT<S>::T R;
     __shared__ double sh[32];
-    const int N = P.g.N;
+    const int N = P.nsite;            // field entries per slot (N/2 in even-odd mode)
     ITEM_LOOP(LIST_INNER)
         const Slot &st = P.slots[j];
         if (st.phase != PH_INNER) continue;
@@ -790,7 +793,7 @@ template <typename S>
 __global__ void __launch_bounds__(PT_BLOCK) k_cg_update_v4(EP P) {
     typedef typename ArithT<S>::T R;
     __shared__ double sh[32];
-    const int N = P.g.N;
+    const int N = P.nsite;            // field entries per slot (N/2 in even-odd mode)
     ITEM_LOOP(LIST_INNER)
         const Slot &st = P.slots[j];
         if (st.phase != PH_INNER) continue;
@@ -816,6 +819,382 @@ __global__ void __launch_bounds__(PT_BLOCK) k_cg_update_v4(EP P) {
             Quad<S>::st(r, idx, rv);
         QUAD_LOOP_END
         item_store_r<1>(P, j, b, vr, sh);
+    ITEM_LOOP_END
+}
+
+// ------------------------------------------------------------------ even-odd CG (Laplacian)
+// With every lattice side even the Laplacian splits by site parity,
+// A = [[d, -H_eo], [-H_oe, d]] with d = 8 + m^2 and H the sum of the eight
+// hops, and A x = b is solved through the Schur complement on the even sites:
+//   S x_e = b'_e,  S = d - H_eo H_oe / d,  b'_e = b_e + H_eo b_o / d,
+//   x_o = (b_o + H_oe x_e) / d.
+// S is about four times better conditioned than A, so CG needs about half
+// the iterations.  The inner vectors e, r, p, q live on the even sites and
+// t = H_oe p on the odd ones.  A half field holds the sites of one parity in
+// storage order: with D_0 even, site i is entry i >> 1 of its parity's field.
+// One inner iteration is three kernels:
+//   k_eo_hop     odd entries:  t = H_oe p_i, with p_i = r + beta p_{i-1} formed
+//                at the eight even neighbours (as in k_cg_apply)
+//   k_eo_apply   even entries: p_i stored, q = S p_i = d p_i - H_eo t / d,
+//                partial p_i . q
+//   k_cg_update  even entries: e += alpha p_i, r -= alpha q, partial |r|^2
+// which moves 6 + 10 + 12 = 28 bytes per lattice site in FP32 (40 on the full
+// system).  The FP64 outer step forms t64 = H_oe x64 on the odd entries, then
+// r = b'_e - S x64 on the even ones, with b'_e regenerated from the noise; its
+// |b|^2 is that of the whole source (both parities), so the stopping test is
+// the full system's ||b - A x|| / ||b|| (r_o = 0 once x_o is rebuilt).  The
+// contraction rebuilds x_o wherever it reads an odd site.
+
+// storage index and coordinates of entry h of the half field of parity par
+__device__ __forceinline__ int half_site(const Geom &g, int par, int h, int x[4]) {
+    const int q0 = fdiv(g.fd[0], 2 * h);            // row of sites 2h and 2h + 1 (D_0 even)
+    const int x0e = 2 * h - q0 * g.D[0];
+    const int q1 = fdiv(g.fd[1], q0);
+    x[1] = q0 - q1 * g.D[1];
+    const int q2 = fdiv(g.fd[2], q1);
+    x[2] = q1 - q2 * g.D[2];
+    x[3] = q2;
+    const int b = (par ^ (x[1] + x[2] + x[3])) & 1;  // x_0 parity that gives the site parity par
+    x[0] = x0e + b;
+    return 2 * h + b;
+}
+
+// sum over the eight neighbours of site i (coordinates x) of f, a half field
+// of the other parity
+template <typename S, typename R>
+__device__ __forceinline__ R half_nbsum(const Geom &g, const S *f, int i, const int x[4]) {
+    R s = R(0);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        s += (R)ld_real(f, (size_t)(nb_fwd(g, i, x, mu) >> 1));
+        s += (R)ld_real(f, (size_t)(nb_bwd(g, i, x, mu) >> 1));
+    }
+    return s;
+}
+
+// coordinates of the neighbour of x one step along mu (s = +1 or -1)
+__device__ __forceinline__ void nb_coords(const Geom &g, const int x[4], int mu, int s, int y[4]) {
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu) y[nu] = x[nu];
+    y[mu] = s > 0 ? (x[mu] == g.D[mu] - 1 ? 0 : x[mu] + 1) : (x[mu] == 0 ? g.D[mu] - 1 : x[mu] - 1);
+}
+
+// t = H_oe p_i at the odd entries (one entry per thread)
+template <typename S>
+__global__ void __launch_bounds__(PT_BLOCK) k_eo_hop(EP P) {
+    typedef typename ArithT<S>::T R;
+    const int N = P.nsite;
+    ITEM_LOOP(LIST_INNER)
+        const Slot &st = P.slots[j];
+        if (st.phase != PH_INNER) continue;
+        const int i = st.inner_it;
+        const R be = (R)st.beta.re;
+        const bool first = (i == 0);
+        const S *r = slot_cptr<S>(P.r, j, P.L);
+        const S *pold = slot_cptr<S>((i & 1) ? P.p1 : P.pv, j, P.L);
+        S *t = slot_ptr<S>(P.t, j, P.L);
+        SITE_LOOP(0)
+            int xc[4];
+            const int s = half_site(P.g, 1, idx, xc);
+            auto pn = [&](int y) -> R {
+                const size_t h = (size_t)(y >> 1);
+                R rv = ld_real(r, h);
+                return first ? rv : rnd<S, R>(rv + be * (R)ld_real(pold, h));
+            };
+            R nb = R(0);
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu) {
+                nb += pn(nb_fwd(P.g, s, xc, mu));
+                nb += pn(nb_bwd(P.g, s, xc, mu));
+            }
+            st_real(t, (size_t)idx, nb);
+        SITE_LOOP_END
+    ITEM_LOOP_END
+}
+
+// p_i = r + beta p_{i-1} and q = S p_i = d p_i - H_eo t / d at the even
+// entries; partial p_i . q
+template <typename S>
+__global__ void __launch_bounds__(PT_BLOCK) k_eo_apply(EP P) {
+    typedef typename ArithT<S>::T R;
+    __shared__ double sh[32];
+    const int N = P.nsite;
+    const R diag = (R)P.diag, inv_d = (R)(1.0 / P.diag);
+    ITEM_LOOP(LIST_INNER)
+        const Slot &st = P.slots[j];
+        if (st.phase != PH_INNER) continue;
+        const int i = st.inner_it;
+        const R be = (R)st.beta.re;
+        const bool first = (i == 0);
+        const S *r = slot_cptr<S>(P.r, j, P.L);
+        const S *pold = slot_cptr<S>((i & 1) ? P.p1 : P.pv, j, P.L);
+        const S *t = slot_cptr<S>(P.t, j, P.L);
+        S *pnew = slot_ptr<S>((i & 1) ? P.pv : P.p1, j, P.L);
+        S *q = slot_ptr<S>(P.q, j, P.L);
+        R vr[1] = {R(0)};
+        SITE_LOOP(0)
+            int xc[4];
+            const int s = half_site(P.g, 0, idx, xc);
+            const R rv = ld_real(r, (size_t)idx);
+            const R pc = first ? rv : rnd<S, R>(rv + be * (R)ld_real(pold, (size_t)idx));
+            const R nb = half_nbsum<S, R>(P.g, t, s, xc);
+            const R qv = rnd<S, R>(diag * pc - nb * inv_d);
+            st_real(pnew, (size_t)idx, pc);
+            st_real(q, (size_t)idx, qv);
+            vr[0] += pc * qv;
+        SITE_LOOP_END
+        item_store_r<1>(P, j, b, vr, sh);
+    ITEM_LOOP_END
+}
+
+// Four half entries per thread (D_0 a multiple of 8, so that the quad
+// h .. h+3, h a multiple of 4, lies in one x row and all four sites share
+// their row parity b): the sites are s, s+2, s+4, s+6.  Their y, z, t
+// neighbours are the aligned quad of the other parity at (neighbour of s) >> 1.
+// With Q the other parity's quad at h, the +x / -x neighbours of entry k are
+// Q[k] / Q[k-1] when b = 0 and Q[k+1] / Q[k] when b = 1; the one entry
+// outside Q is a single load, wrapping within the row.  The neighbours are
+// added in the one-entry kernels' order (x+, x-, y+, y-, z+, z-, t+, t-), so
+// both paths give the same results.
+template <typename S, typename R, typename F1, typename F4>
+__device__ __forceinline__ void eo_nbsum4(const Geom &g, int h, int s, const int xc[4], F1 one, F4 quad,
+                                          R acc[4]) {
+    const int half_row = g.D[0] >> 1;
+    const int c = (xc[0] - (s & 1)) >> 1;           // position of h in its row (multiple of 4)
+    R Q[4], t4[4];
+    quad(h, Q);
+    if ((s & 1) == 0) {
+        const R L = one(c == 0 ? h + half_row - 1 : h - 1);
+        acc[0] = Q[0] + L; acc[1] = Q[1] + Q[0]; acc[2] = Q[2] + Q[1]; acc[3] = Q[3] + Q[2];
+    } else {
+        const R Rt = one(c + 4 == half_row ? h + 4 - half_row : h + 4);
+        acc[0] = Q[1] + Q[0]; acc[1] = Q[2] + Q[1]; acc[2] = Q[3] + Q[2]; acc[3] = Rt + Q[3];
+    }
+#pragma unroll
+    for (int mu = 1; mu < 4; ++mu) {
+        quad(nb_fwd(g, s, xc, mu) >> 1, t4);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k] += t4[k];
+        quad(nb_bwd(g, s, xc, mu) >> 1, t4);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k] += t4[k];
+    }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(PT_BLOCK) k_eo_hop_v4(EP P) {
+    typedef typename ArithT<S>::T R;
+    const int N = P.nsite;
+    ITEM_LOOP(LIST_INNER)
+        const Slot &st = P.slots[j];
+        if (st.phase != PH_INNER) continue;
+        const int i = st.inner_it;
+        const R be = (R)st.beta.re;
+        const bool first = (i == 0);
+        const S *r = slot_cptr<S>(P.r, j, P.L);
+        const S *pold = slot_cptr<S>((i & 1) ? P.p1 : P.pv, j, P.L);
+        S *t = slot_ptr<S>(P.t, j, P.L);
+        QUAD_LOOP
+            int xc[4];
+            const int s = half_site(P.g, 1, idx, xc);
+            auto pquad = [&](int h, R out[4]) {
+                Quad<S>::ld(r, h, out);
+                if (!first) {
+                    R pp[4];
+                    Quad<S>::ld(pold, h, pp);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) out[k] = rnd<S, R>(out[k] + be * pp[k]);
+                }
+            };
+            auto pone = [&](int h) -> R {
+                R rv = ld_real(r, (size_t)h);
+                return first ? rv : rnd<S, R>(rv + be * (R)ld_real(pold, (size_t)h));
+            };
+            R acc[4];
+            eo_nbsum4<S, R>(P.g, idx, s, xc, pone, pquad, acc);
+            Quad<S>::st(t, idx, acc);
+        QUAD_LOOP_END
+    ITEM_LOOP_END
+}
+
+template <typename S>
+__global__ void __launch_bounds__(PT_BLOCK) k_eo_apply_v4(EP P) {
+    typedef typename ArithT<S>::T R;
+    __shared__ double sh[32];
+    const int N = P.nsite;
+    const R diag = (R)P.diag, inv_d = (R)(1.0 / P.diag);
+    ITEM_LOOP(LIST_INNER)
+        const Slot &st = P.slots[j];
+        if (st.phase != PH_INNER) continue;
+        const int i = st.inner_it;
+        const R be = (R)st.beta.re;
+        const bool first = (i == 0);
+        const S *r = slot_cptr<S>(P.r, j, P.L);
+        const S *pold = slot_cptr<S>((i & 1) ? P.p1 : P.pv, j, P.L);
+        const S *t = slot_cptr<S>(P.t, j, P.L);
+        S *pnew = slot_ptr<S>((i & 1) ? P.pv : P.p1, j, P.L);
+        S *q = slot_ptr<S>(P.q, j, P.L);
+        R vr[1] = {R(0)};
+        QUAD_LOOP
+            int xc[4];
+            const int s = half_site(P.g, 0, idx, xc);
+            R pc[4], acc[4], qv[4];
+            Quad<S>::ld(r, idx, pc);
+            if (!first) {
+                R pp[4];
+                Quad<S>::ld(pold, idx, pp);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) pc[k] = rnd<S, R>(pc[k] + be * pp[k]);
+            }
+            auto tone = [&](int h) -> R { return ld_real(t, (size_t)h); };
+            auto tquad = [&](int h, R out[4]) { Quad<S>::ld(t, h, out); };
+            eo_nbsum4<S, R>(P.g, idx, s, xc, tone, tquad, acc);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                qv[k] = rnd<S, R>(diag * pc[k] - acc[k] * inv_d);
+                vr[0] += pc[k] * qv[k];
+            }
+            Quad<S>::st(pnew, idx, pc);
+            Quad<S>::st(q, idx, qv);
+        QUAD_LOOP_END
+        item_store_r<1>(P, j, b, vr, sh);
+    ITEM_LOOP_END
+}
+
+// outer step, part 1: t64 = H_oe x64 at the odd entries (FP64)
+__global__ void __launch_bounds__(PT_BLOCK) k_eo_outer_hop(EP P) {
+    const int N = P.nsite;
+    ITEM_LOOP(LIST_OUTER)
+        const int ph = P.slots[j].phase;
+        if (ph != PH_START && ph != PH_OUTER) continue;
+        const double *x = P.x64 + (size_t)j * P.L;
+        double *t = P.t64 + (size_t)j * P.L;
+        SITE_LOOP(0)
+            int xc[4];
+            const int s = half_site(P.g, 1, idx, xc);
+            t[idx] = half_nbsum<double, double>(P.g, x, s, xc);
+        SITE_LOOP_END
+    ITEM_LOOP_END
+}
+
+// outer step, part 2, at the even entries: r64 = b'_e - S x64 in FP64 with
+// b'_e = b_e + H_eo b_o / d regenerated from the source; r = (S) r64 starts
+// the inner solve (e = 0).  Partials: |r64|^2, |b|^2 of both sites of the
+// entry (even and odd), |r|^2 of the rounded r.
+template <typename S>
+__global__ void __launch_bounds__(PT_BLOCK) k_eo_outer_residual(EP P) {
+    typedef typename ArithT<S>::T R;
+    __shared__ double sh[32 * 3];
+    const int N = P.nsite;
+    const double d = P.diag, inv_d = 1.0 / P.diag;
+    ITEM_LOOP(LIST_OUTER)
+        const Slot &st = P.slots[j];
+        const int ph = st.phase;
+        if (ph != PH_START && ph != PH_OUTER) continue;
+        const Task tk = P.tasks[st.task];
+        const uint64_t key = (P.mode == MODE_SOLVE) ? 0 : pt_set_key(P.seed, tk.set);
+        S *r = slot_ptr<S>(P.r, j, P.L);
+        S *e = slot_ptr<S>(P.e, j, P.L);
+        const double *x = P.x64 + (size_t)j * P.L;
+        const double *t = P.t64 + (size_t)j * P.L;
+        double v[3] = {0.0, 0.0, 0.0};
+        SITE_LOOP(0)
+            int xc[4], y4[4];
+            const int s = half_site(P.g, 0, idx, xc);
+            const double b_e = source_val<0>(P, tk, key, s, xc, 0).re;
+            double b_nb = 0.0;
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu) {
+                nb_coords(P.g, xc, mu, 1, y4);
+                b_nb += source_val<0>(P, tk, key, nb_fwd(P.g, s, xc, mu), y4, 0).re;
+                nb_coords(P.g, xc, mu, -1, y4);
+                b_nb += source_val<0>(P, tk, key, nb_bwd(P.g, s, xc, mu), y4, 0).re;
+            }
+#pragma unroll
+            for (int nu = 0; nu < 4; ++nu) y4[nu] = xc[nu];
+            y4[0] ^= 1;                                  // the odd site of the same entry
+            const double b_o = source_val<0>(P, tk, key, s ^ 1, y4, 0).re;
+            const double bp = b_e + b_nb * inv_d;
+            const double sx = d * x[idx] - half_nbsum<double, double>(P.g, t, s, xc) * inv_d;
+            const double rv = bp - sx;
+            v[0] += rv * rv;
+            v[1] += b_e * b_e + b_o * b_o;
+            const R rs = rnd<S, R>((R)rv);
+            st_real(r, (size_t)idx, rs);
+            st_real(e, (size_t)idx, R(0));
+            v[2] += (double)rs * (double)rs;
+        SITE_LOOP_END
+        item_store<3>(P, j, b, v, sh);
+    ITEM_LOOP_END
+}
+
+// x at storage site y (coordinates xy): its even entry, or on an odd site
+// x_o = (b_o + H_oe x_e) / d rebuilt from the source and the even neighbours
+__device__ __forceinline__ double eo_x_at(const EP &P, const Task &tk, uint64_t key, const double *x, int y,
+                                          const int xy[4]) {
+    if (((xy[0] + xy[1] + xy[2] + xy[3]) & 1) == 0) return x[y >> 1];
+    const double b_o = source_val<0>(P, tk, key, y, xy, 0).re;
+    return (b_o + half_nbsum<double, double>(P.g, x, y, xy)) / P.diag;
+}
+
+// the contraction (trace mode) or the copy-out (solve mode) of k_contract for
+// even-odd slots: entry h covers the sites 2h and 2h + 1
+template <int MAXQ>
+__global__ void __launch_bounds__(PT_BLOCK) k_eo_contract(EP P) {
+    __shared__ double sh[32 * 2 * PT_MAX_P];
+    const int N = P.nsite, NF = P.g.N;
+    ITEM_LOOP(LIST_CONTRACT)
+        const Slot &st = P.slots[j];
+        if (st.phase != PH_CONTRACT) continue;
+        const Task tk = P.tasks[st.task];
+        const double *x = P.x64 + (size_t)j * P.L;
+        const uint64_t key = (P.mode == MODE_SOLVE) ? 0 : pt_set_key(P.seed, tk.set);
+        if (P.mode == MODE_SOLVE) {
+            SITE_LOOP(0)
+                for (int w = 0; w < 2; ++w) {
+                    const int sw = 2 * idx + w;
+                    int xs[4];
+                    site_coords(P.g, sw, xs);
+                    P.X_user[(size_t)tk.set * NF + sw] = eo_x_at(P, tk, key, x, sw, xs);
+                }
+            SITE_LOOP_END
+            continue;
+        }
+        double acc[2 * MAXQ];
+#pragma unroll
+        for (int n = 0; n < 2 * MAXQ; ++n) acc[n] = 0.0;
+        const int32_t *col = P.col + (size_t)tk.cidx * NF;
+        SITE_LOOP(0)
+            for (int w = 0; w < 2; ++w) {
+                const int sw = 2 * idx + w;
+                if (P.n_lev) {                 // the coarsest ancestor class holds every finer one
+                    if (P.lev_cols[sw] != P.lev_anc[tk.colour]) continue;
+                } else if (col[sw] != tk.colour) {
+                    continue;
+                }
+                int xs[4], xy[4];
+                site_coords(P.g, sw, xs);
+                const Cx<double> z = pt_noise(key, (uint64_t)sw, P.noise);
+#pragma unroll
+                for (int n = 0; n < MAXQ; ++n) {
+                    if (n >= P.n_p) break;
+                    if (P.n_lev) {
+                        const int l = n / P.n_pr;
+                        if (l > 0 && P.lev_cols[(size_t)l * NF + sw] != P.lev_anc[(size_t)l * P.m_fin + tk.colour])
+                            continue;
+                    }
+                    const int y = shift_site(P.g, sw, xs, P.mu, P.p[n]);
+#pragma unroll
+                    for (int nu = 0; nu < 4; ++nu) xy[nu] = xs[nu];
+                    int cm = (xs[P.mu] + P.p[n]) % P.g.D[P.mu];
+                    xy[P.mu] = cm < 0 ? cm + P.g.D[P.mu] : cm;
+                    const double xv = eo_x_at(P, tk, key, x, y, xy);
+                    acc[2 * n] += z.re * xv;                // conj(z) x
+                    acc[2 * n + 1] -= z.im * xv;
+                }
+            }
+        SITE_LOOP_END
+        item_store_contract<MAXQ>(P, j, b, acc, 2 * P.n_p, sh);
     ITEM_LOOP_END
 }
 
@@ -1171,6 +1550,7 @@ struct EngineRun {
     // persistent grid of each item kernel: SMs x its own resident CTAs per SM
     int g_contract, g_oupd, g_ores, g_apply1, g_apply2, g_upd, g_s, g_dir;
     int g_apply1_x2, g_apply2_x2, g_contract32;
+    int g_hop, g_ohop;                 // even-odd: the odd-site hop of the inner and of the outer step
     double *part_con, *part_outer;   // partial-sum regions of the contraction and outer kernel groups
 };
 
@@ -1217,18 +1597,39 @@ static void enqueue_iteration(const EngineRun &E, cudaStream_t st, const cudaEve
         s_con = side[0];
         s_out = side[1];
     }
-    if (P.n_p <= 16) k_contract<KIND, 16><<<E.g_contract, PT_BLOCK, 0, s_con>>>(Pc);
-    else k_contract<KIND, PT_MAX_P><<<E.g_contract32, PT_BLOCK, 0, s_con>>>(Pc);
+    if (KIND == 0 && P.eo) {
+        if (P.n_p <= 16) k_eo_contract<16><<<E.g_contract, PT_BLOCK, 0, s_con>>>(Pc);
+        else k_eo_contract<PT_MAX_P><<<E.g_contract32, PT_BLOCK, 0, s_con>>>(Pc);
+    } else {
+        if (P.n_p <= 16) k_contract<KIND, 16><<<E.g_contract, PT_BLOCK, 0, s_con>>>(Pc);
+        else k_contract<KIND, PT_MAX_P><<<E.g_contract32, PT_BLOCK, 0, s_con>>>(Pc);
+    }
     k_fin_contract<<<W, 256, 0, s_con>>>(Pc);
     ev_rec(ev, 5, s_out);
     k_outer_update<KIND, S><<<E.g_oupd, PT_BLOCK, 0, s_out>>>(Po);
-    k_outer_residual<KIND, S><<<E.g_ores, PT_BLOCK, 0, s_out>>>(Po);
+    if (KIND == 0 && P.eo) {
+        k_eo_outer_hop<<<E.g_ohop, PT_BLOCK, 0, s_out>>>(Po);
+        k_eo_outer_residual<S><<<E.g_ores, PT_BLOCK, 0, s_out>>>(Po);
+    } else {
+        k_outer_residual<KIND, S><<<E.g_ores, PT_BLOCK, 0, s_out>>>(Po);
+    }
     k_fin_outer<<<W, 256, 0, s_out>>>(Po);
     ev_rec(ev, 6, s_out);
     if constexpr (KIND == 0) {
         ev_rec(ev, 0, st);
-        if (P.vec4) k_cg_apply_v4<S><<<E.g_apply1, PT_BLOCK, 0, st>>>(P);
-        else k_cg_apply<S><<<E.g_apply1, PT_BLOCK, 0, st>>>(P);
+        if (P.eo) {
+            if (P.vec4) {
+                k_eo_hop_v4<S><<<E.g_hop, PT_BLOCK, 0, st>>>(P);
+                k_eo_apply_v4<S><<<E.g_apply1, PT_BLOCK, 0, st>>>(P);
+            } else {
+                k_eo_hop<S><<<E.g_hop, PT_BLOCK, 0, st>>>(P);
+                k_eo_apply<S><<<E.g_apply1, PT_BLOCK, 0, st>>>(P);
+            }
+        } else if (P.vec4) {
+            k_cg_apply_v4<S><<<E.g_apply1, PT_BLOCK, 0, st>>>(P);
+        } else {
+            k_cg_apply<S><<<E.g_apply1, PT_BLOCK, 0, st>>>(P);
+        }
         ev_rec(ev, 1, st);
         k_fin_cg_alpha<<<W, 256, 0, st>>>(P);
         if (P.vec4) k_cg_update_v4<S><<<E.g_upd, PT_BLOCK, 0, st>>>(P);
@@ -1301,6 +1702,13 @@ struct EngineRequest {
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// the even-odd split needs every side even (each hop then joins opposite parities)
+static bool pt_evenodd_ok(const int dims[4]) {
+    for (int mu = 0; mu < 4; ++mu)
+        if (dims[mu] < 2 || dims[mu] % 2) return false;
+    return true;
+}
+
 // Engine parameters for (operator kind, precision, lattice): the autotuner's
 // candidate while it runs, else a stored tuning, else the defaults.
 static pt_ctx::Tune engine_tuning(const pt_ctx *c, const pt_op *op, int prec) {
@@ -1319,6 +1727,7 @@ static pt_ctx::Tune engine_tuning(const pt_ctx *c, const pt_op *op, int prec) {
     d.graph_iters = 8;
     d.rhs_block = 1;
     d.overlap = 0;
+    d.evenodd = (op->kind == 0 && pt_evenodd_ok(op->dims)) ? 1 : 0;
     return d;
 }
 
@@ -1326,19 +1735,25 @@ template <int KIND, typename S, typename LS>
 static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     pt_ctx *c = op->ctx;
     const Geom g = op->g;
-    const int64_t L = pt_field_reals(op);
-    const int nvec = KIND ? 7 : 5;
-    const size_t per_slot = (size_t)L * (sizeof(double) + nvec * sizeof(S));
+    const pt_ctx::Tune tn = engine_tuning(c, op, rq.prec);
+    // even-odd for the Laplacian (every side even) unless switched off; the
+    // gradient works on full-lattice solutions and keeps the full system
+    const bool eo = KIND == 0 && tn.evenodd && rq.mode != MODE_GRAD && pt_evenodd_ok(op->dims);
+    const int nsite = eo ? g.N / 2 : g.N;
+    const int64_t L = eo ? (int64_t)nsite : pt_field_reals(op);
+    const int nvec = KIND ? 7 : (eo ? 6 : 5);
+    const size_t per_slot = (size_t)L * ((eo ? 2 : 1) * sizeof(double) + nvec * sizeof(S));
     int R = rq.R_force > 0 ? rq.R_force : (int)std::min<size_t>((size_t)rq.n_tasks, c->mem_budget / per_slot);
     if (rq.R_force <= 0 && c->max_slots > 0) R = std::min(R, c->max_slots);
     if (R < 1) R = 1;
     if (rq.R_force <= 0) R = std::min(R, 4096);
-    const int nsb = (g.N + Tile<KIND>::SITES - 1) / Tile<KIND>::SITES;
+    const int nsb = (nsite + Tile<KIND>::SITES - 1) / Tile<KIND>::SITES;
     const int K_MAX = 2 * PT_MAX_P;
     // layout of the work space
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
     size_t o_x64 = take((size_t)R * L * sizeof(double));
+    size_t o_t64 = eo ? take((size_t)R * L * sizeof(double)) : 0;
     size_t o_vec[7];
     for (int v = 0; v < nvec; ++v) o_vec[v] = take((size_t)R * L * sizeof(S));
     size_t o_slots = take((size_t)R * sizeof(Slot));
@@ -1366,11 +1781,13 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     P.kind = KIND;
     P.nsb = nsb;
     P.R = R;
-    const pt_ctx::Tune tn = engine_tuning(c, op, rq.prec);
+    P.eo = eo ? 1 : 0;
+    P.nsite = nsite;
     P.gs = tn.group;
     P.rhs_block = (KIND == 1 && !std::is_same<S, double>::value && tn.rhs_block == 2) ? 2 : 1;
     P.overlap = tn.overlap ? 1 : 0;
-    P.vec4 = (KIND == 0 && g.D[0] % 4 == 0) ? 1 : 0;
+    // four sites (even-odd: four half entries of one x row) per thread
+    P.vec4 = (KIND == 0 && g.D[0] % (eo ? 8 : 4) == 0) ? 1 : 0;
     P.L = L;
     P.diag = 8.0 + op->m2;
     P.kappa = op->kappa;
@@ -1399,8 +1816,9 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     P.B_user = rq.B_user;
     P.X_user = rq.X_user;
     P.x64 = (double *)(base + o_x64);
+    P.t64 = eo ? (double *)(base + o_t64) : nullptr;
     void **vp[7] = {&P.e, &P.r, &P.pv, &P.q, &P.s, &P.t, &P.r0};
-    if constexpr (KIND == 0) vp[4] = &P.p1;     // CG: e, r, p (two buffers), q
+    if constexpr (KIND == 0) vp[4] = &P.p1;     // CG: e, r, p (two buffers), q; even-odd adds t
     for (int v = 0; v < nvec; ++v) *vp[v] = base + o_vec[v];
     P.slots = (Slot *)(base + o_slots);
     P.partials = (double *)(base + o_part_inner);
@@ -1444,8 +1862,20 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     E.g_contract32 = persistent_grid(k_contract<KIND, PT_MAX_P>, ns);
     E.g_oupd = persistent_grid(k_outer_update<KIND, S>, ns);
     E.g_ores = persistent_grid(k_outer_residual<KIND, S>, ns);
+    E.g_hop = E.g_ohop = 0;
     if constexpr (KIND == 0) {
-        E.g_apply1 = E.g_apply2 = P.vec4 ? persistent_grid(k_cg_apply_v4<S>, ns) : persistent_grid(k_cg_apply<S>, ns);
+        if (eo) {
+            E.g_contract = persistent_grid(k_eo_contract<16>, ns);
+            E.g_contract32 = persistent_grid(k_eo_contract<PT_MAX_P>, ns);
+            E.g_ores = persistent_grid(k_eo_outer_residual<S>, ns);
+            E.g_ohop = persistent_grid(k_eo_outer_hop, ns);
+            E.g_apply1 = E.g_apply2 = P.vec4 ? persistent_grid(k_eo_apply_v4<S>, ns)
+                                             : persistent_grid(k_eo_apply<S>, ns);
+            E.g_hop = P.vec4 ? persistent_grid(k_eo_hop_v4<S>, ns) : persistent_grid(k_eo_hop<S>, ns);
+        } else {
+            E.g_apply1 = E.g_apply2 = P.vec4 ? persistent_grid(k_cg_apply_v4<S>, ns)
+                                             : persistent_grid(k_cg_apply<S>, ns);
+        }
         E.g_upd = P.vec4 ? persistent_grid(k_cg_update_v4<S>, ns) : persistent_grid(k_cg_update<S>, ns);
         E.g_s = E.g_dir = E.g_upd;
     } else {
@@ -1462,7 +1892,7 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
         E.g_dir = persistent_grid(k_bicg_dir<S>, ns);
     }
     E.grid_warps = std::max(1, std::min((R + 7) / 8, c->num_sms * 4));
-    E.kernels_per_iter = KIND ? 14 : 10;
+    E.kernels_per_iter = KIND ? 14 : (eo ? 12 : 10);
 
     // capture ITERS engine iterations into one graph
     const int ITERS = tn.graph_iters;
@@ -1485,7 +1915,8 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     // bounded host loop: every RHS stops within maxit Krylov iterations, plus a
     // few engine iterations per outer restart and per retire/refill
     const int64_t waves = (rq.n_tasks + R - 1) / R + 1;
-    const int64_t max_launches = waves * ((int64_t)rq.maxit * 2 + 400) / ITERS + 64;
+    int64_t max_launches = waves * ((int64_t)rq.maxit * 2 + 400) / ITERS + 64;
+    if (c->launch_limit > 0) max_launches = std::min(max_launches, c->launch_limit);
     int64_t launches = 0;
     int rc_loop = PT_OK;
     int *hf = c->h_flags;
@@ -2016,9 +2447,10 @@ extern "C" int pt_grad(pt_ctx *c, const pt_op *op, const int32_t *col_dev, int n
 
 // ------------------------------------------------------------------ autotuner
 // Coordinate descent over the engine's free parameters on a trial subset of
-// the probes: the inner relative tolerance delta (mixed precision only), the
-// slot group of the item order (Wilson only) and the engine iterations per
-// CUDA graph.  Each candidate solves the same trial right-hand sides; the
+// the probes: even-odd or full system (Laplacian with even sides), the inner
+// relative tolerance delta (mixed precision only), the right-hand sides per
+// item and the slot group of the item order (Wilson only) and the engine
+// iterations per CUDA graph.  Each candidate solves the same trial right-hand sides; the
 // fastest (device time, synchronised) wins and is stored for the operator's
 // (kind, precision, lattice).
 static int store_tuning(pt_ctx *c, const pt_op *op, int prec, const pt_tune *t) {
@@ -2040,6 +2472,7 @@ static int store_tuning(pt_ctx *c, const pt_op *op, int prec, const pt_tune *t) 
     e.graph_iters = t->graph_iters;
     e.rhs_block = t->rhs_block == 2 ? 2 : 1;
     e.overlap = t->overlap ? 1 : 0;
+    e.evenodd = t->evenodd ? 1 : 0;
     return PT_OK;
 }
 
@@ -2053,6 +2486,7 @@ extern "C" int pt_set_tuning(pt_ctx *c, const pt_op *op, int prec, const pt_tune
         PT_CHECK_ARG(t->graph_iters >= 1 && t->graph_iters <= 64, "pt_set_tuning: graph_iters must be in [1, 64]");
         PT_CHECK_ARG(t->rhs_block >= 0 && t->rhs_block <= 2, "pt_set_tuning: rhs_block must be 0, 1 or 2");
         PT_CHECK_ARG(t->overlap == 0 || t->overlap == 1, "pt_set_tuning: overlap must be 0 or 1");
+        PT_CHECK_ARG(t->evenodd == 0 || t->evenodd == 1, "pt_set_tuning: evenodd must be 0 or 1");
     }
     return store_tuning(c, op, prec, t);
 }
@@ -2065,6 +2499,7 @@ extern "C" int pt_get_tuning(pt_ctx *c, const pt_op *op, int prec, pt_tune *t) {
     t->graph_iters = e.graph_iters;
     t->rhs_block = e.rhs_block;
     t->overlap = e.overlap;
+    t->evenodd = e.evenodd;
     t->seconds_per_rhs = 0.0;
     return PT_OK;
 }
@@ -2128,18 +2563,21 @@ extern "C" int pt_autotune(pt_ctx *c, const pt_op *op, const int32_t *col_dev, i
     const std::vector<int> iters = {4, 8, 16};
     std::vector<int> blocks;
     if (op->kind == 1 && prec != PT_PREC_FP64) blocks = {1, 2};
+    std::vector<int> evenodds;
+    if (op->kind == 0 && pt_evenodd_ok(op->dims)) evenodds = {0, 1};
     // serial versus branched iterations (overlap) is left out: within 1 % either way, and the
     // branches blur the per-kernel event timing
     const std::vector<int> overlaps = {};
-    for (int pass = 0; pass < 5 && !rc; ++pass) {
-        const size_t nc = pass == 0 ? deltas.size() : pass == 1 ? blocks.size() : pass == 2 ? groups.size()
-                          : pass == 3 ? iters.size() : overlaps.size();
+    for (int pass = 0; pass < 6 && !rc; ++pass) {
+        const size_t nc = pass == 0 ? evenodds.size() : pass == 1 ? deltas.size() : pass == 2 ? blocks.size()
+                          : pass == 3 ? groups.size() : pass == 4 ? iters.size() : overlaps.size();
         for (size_t i = 0; i < nc && !rc; ++i) {
             pt_ctx::Tune cand = cur;
-            if (pass == 0) cand.delta = deltas[i];
-            else if (pass == 1) cand.rhs_block = blocks[i];
-            else if (pass == 2) cand.group = groups[i];
-            else if (pass == 3) cand.graph_iters = iters[i];
+            if (pass == 0) cand.evenodd = evenodds[i];
+            else if (pass == 1) cand.delta = deltas[i];
+            else if (pass == 2) cand.rhs_block = blocks[i];
+            else if (pass == 3) cand.group = groups[i];
+            else if (pass == 4) cand.graph_iters = iters[i];
             else cand.overlap = overlaps[i];
             if (!memcmp(&cand, &cur, sizeof(cand))) continue;
             double t = 0.0;
@@ -2156,6 +2594,7 @@ extern "C" int pt_autotune(pt_ctx *c, const pt_op *op, const int32_t *col_dev, i
     best->graph_iters = cur.graph_iters;
     best->rhs_block = cur.rhs_block;
     best->overlap = cur.overlap;
+    best->evenodd = cur.evenodd;
     best->seconds_per_rhs = t_best / trial.size();
     return store_tuning(c, op, prec, best);
 }

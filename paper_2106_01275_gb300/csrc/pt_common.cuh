@@ -482,13 +482,14 @@ struct pt_ctx {
     int num_sms;
     size_t mem_budget;
     int max_slots;           // 0: no cap on the right-hand sides in flight
+    int64_t launch_limit;    // 0: the engine's own bound on graph launches per run
     // solver-engine parameters chosen by pt_autotune / pt_set_tuning, per
     // (operator kind, precision, lattice); `trial` overrides them while the
     // autotuner times a candidate
     struct Tune {
         int used, kind, prec, dims[4];
         double delta;
-        int group, graph_iters, rhs_block, overlap;
+        int group, graph_iters, rhs_block, overlap, evenodd;
     } tune[16], trial;
     int in_trial;
     // grow-only work space

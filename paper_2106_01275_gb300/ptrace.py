@@ -48,11 +48,13 @@ class Stats(ctypes.Structure):
 
 class Tune(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("group", ctypes.c_int32), ("graph_iters", ctypes.c_int32),
-                ("rhs_block", ctypes.c_int32), ("overlap", ctypes.c_int32), ("seconds_per_rhs", ctypes.c_double)]
+                ("rhs_block", ctypes.c_int32), ("overlap", ctypes.c_int32), ("evenodd", ctypes.c_int32),
+                ("seconds_per_rhs", ctypes.c_double)]
 
     def as_dict(self):
         return {"delta": self.delta, "group": self.group, "graph_iters": self.graph_iters,
-                "rhs_block": self.rhs_block, "overlap": self.overlap, "seconds_per_rhs": self.seconds_per_rhs}
+                "rhs_block": self.rhs_block, "overlap": self.overlap, "evenodd": self.evenodd,
+                "seconds_per_rhs": self.seconds_per_rhs}
 
 
 _lib = None
@@ -67,6 +69,7 @@ _SIGS = {
     "pt_synchronize": ([_P], _I),
     "pt_set_memory_budget": ([_P, ctypes.c_size_t], _I),
     "pt_set_max_slots": ([_P, _I], _I),
+    "pt_set_launch_limit": ([_P, ctypes.c_int64], _I),
     "pt_autotune": ([_P, _P, _P, _I, _I, _I, ctypes.c_uint64, _I, _D, _I, _I, ctypes.POINTER(Tune)], _I),
     "pt_set_tuning": ([_P, _P, _I, ctypes.POINTER(Tune)], _I),
     "pt_get_tuning": ([_P, _P, _I, ctypes.POINTER(Tune)], _I),
@@ -241,6 +244,9 @@ class Context:
 
     def set_max_slots(self, n):
         _check(lib().pt_set_max_slots(self._h, int(n)))
+
+    def set_launch_limit(self, n):
+        _check(lib().pt_set_launch_limit(self._h, int(n)))
 
     def profile(self, on=True):
         _check(lib().pt_profile_enable(self._h, 1 if on else 0))
@@ -455,7 +461,8 @@ def autotune(op, col, n_colours, mu, noise="z2", seed=0, prec="mixed_fp32", tol=
     return t.as_dict()
 
 
-def set_tuning(op, prec, delta=None, group=None, graph_iters=None, rhs_block=None, overlap=None, reset=False):
+def set_tuning(op, prec, delta=None, group=None, graph_iters=None, rhs_block=None, overlap=None, evenodd=None,
+               reset=False):
     if reset:
         _check(lib().pt_set_tuning(op.ctx.handle, op._h, PREC[prec], None))
         return
@@ -463,7 +470,8 @@ def set_tuning(op, prec, delta=None, group=None, graph_iters=None, rhs_block=Non
     t = Tune(cur["delta"] if delta is None else float(delta), cur["group"] if group is None else int(group),
              cur["graph_iters"] if graph_iters is None else int(graph_iters),
              cur["rhs_block"] if rhs_block is None else int(rhs_block),
-             cur["overlap"] if overlap is None else int(overlap), 0.0)
+             cur["overlap"] if overlap is None else int(overlap),
+             cur["evenodd"] if evenodd is None else int(evenodd), 0.0)
     _check(lib().pt_set_tuning(op.ctx.handle, op._h, PREC[prec], ctypes.byref(t)))
 
 

@@ -1,0 +1,140 @@
+"""GPU parity for the batched engine on the even Schur complement of the
+Laplacian (tuning knob evenodd = 1, the default when every side is even):
+traces (Eqs. (1), (5)) against the oracle at 1e-8 and against the same
+engine on the full system, in FP64, FP32 and BF16 inner storage, on lattices
+that take the four-entry kernels (D_0 a multiple of 8) and the one-entry
+ones; solves checked through the oracle's operator; nested and 32-output
+contractions; the iteration count against the full system."""
+import numpy as np
+import pytest
+
+import oracle.estimator as OE
+import oracle.operators as OO
+from oracle.colouring import greedy_colour, nested_colour
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pt():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_01275_gb300 import build
+    build.build()
+    from paper_2106_01275_gb300 import ptrace
+    return ptrace
+
+
+@pytest.fixture(scope="module")
+def ctx(pt):
+    return pt.Context(0)
+
+
+def _t(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a)).cuda()
+
+
+PRECS = ("fp64", "mixed_fp32", "mixed_bf16")
+
+
+@pytest.mark.parametrize("dims", [
+    [8, 8, 8, 8],          # four entries per thread
+    [16, 2, 2, 2],         # four entries per thread; sides of 2 (both neighbours one site)
+    [8, 4, 6, 2],          # four entries per thread, ragged volume
+    [6, 4, 2, 8],          # one entry per thread (D_0 / 2 odd)
+    [4, 4, 4, 6],          # one entry per thread (D_0 not a multiple of 8)
+    [2, 2, 2, 2],
+])
+def test_trace_matches_oracle_and_full_system(pt, ctx, dims):
+    mu, m2 = 3, 0.1
+    ps = [0, 1, 2]
+    col, m = greedy_colour(dims, mu, [1], 1, 0)
+    op = pt.laplacian(ctx, dims, m2)
+    want = OE.probed_estimates(OE.Laplacian(dims, m2), col, m, 21, 2, 0, mu, ps, 1e-13)
+    for prec in PRECS:
+        assert pt.get_tuning(op, prec)["evenodd"] == 1
+        est, _, _, st = pt.trace(op, _t(col), m, mu, ps, "z2", 21, 0, 2, True, prec, 1e-10, 5000)
+        assert np.allclose(est, want, rtol=1e-8, atol=1e-9 * np.abs(want).max()), prec
+        assert st["max_relres"] <= 1e-10 and st["n_noconv"] == 0
+        pt.set_tuning(op, prec, evenodd=0)
+        full, _, _, st_f = pt.trace(op, _t(col), m, mu, ps, "z2", 21, 0, 2, True, prec, 1e-10, 5000)
+        pt.set_tuning(op, prec, reset=True)
+        assert np.allclose(est, full, rtol=1e-8, atol=1e-9 * np.abs(want).max()), prec
+
+
+def test_iterations_halve_on_16to4(pt, ctx):
+    """16^4, m^2 = 0.01, the (4, 1) colouring along dim 3, one Z2 set: the
+    even-odd engine reaches the same estimates (oracle, 1e-8) in about half
+    the inner CG iterations of the full system."""
+    dims, m2, mu = [16, 16, 16, 16], 0.01, 3
+    col, m = greedy_colour(dims, mu, [4], 1, 0)
+    op = pt.laplacian(ctx, dims, m2)
+    want = OE.probed_estimates(OE.Laplacian(dims, m2), col, m, 1000, 1, 0, mu, [0, 4], 1e-12)
+    est, _, _, st = pt.trace(op, _t(col), m, mu, [0, 4], "z2", 1000, 0, 1, True, "mixed_fp32", 1e-10, 20000)
+    assert np.allclose(est, want, rtol=1e-8, atol=1e-8)
+    pt.set_tuning(op, "mixed_fp32", evenodd=0)
+    _, _, _, st_f = pt.trace(op, _t(col), m, mu, [0, 4], "z2", 1000, 0, 1, True, "mixed_fp32", 1e-10, 20000)
+    pt.set_tuning(op, "mixed_fp32", reset=True)
+    assert st["inner_iters"] <= 0.65 * st_f["inner_iters"], (st["inner_iters"], st_f["inner_iters"])
+
+
+@pytest.mark.parametrize("dims", [[8, 4, 4, 8], [6, 2, 4, 4]])
+def test_solve_through_the_oracle_operator(pt, ctx, dims):
+    """pt_solve with the even-odd engine: the full solution (odd half rebuilt)
+    has a true FP64 residual below the tolerance, and equals the full-system
+    engine's solution."""
+    import torch
+    N, m2 = int(np.prod(dims)), 0.05
+    op = pt.laplacian(ctx, dims, m2)
+    B = np.random.default_rng(3).standard_normal((3, N))
+    for prec in PRECS:
+        X, iters, relres, _ = pt.solve(op, _t(B), prec, 1e-10, 5000)
+        Xn = X.cpu().numpy()
+        for j in range(3):
+            r = B[j] - OO.laplacian_apply(Xn[j], dims, m2)
+            assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(B[j]), prec
+            assert relres[j] <= 1e-10
+        pt.set_tuning(op, prec, evenodd=0)
+        Xf, _, _, _ = pt.solve(op, _t(B), prec, 1e-10, 5000)
+        pt.set_tuning(op, prec, reset=True)
+        assert torch.allclose(X, Xf, rtol=1e-8, atol=1e-9 * Xf.abs().max().item()), prec
+    Z, it0, _, _ = pt.solve(op, _t(np.zeros((1, N))), "mixed_fp32", 1e-10, 100)
+    assert torch.count_nonzero(Z).item() == 0 and it0[0] == 0
+
+
+def test_many_displacements_and_nested_levels(pt, ctx):
+    """20 displacements (the 32-output contraction) and a nested colouring
+    (every level's estimate from the finest level's solves), even-odd against
+    the oracle."""
+    import torch
+    dims, m2, mu = [8, 8, 4, 4], 0.2, 0
+    col, m = greedy_colour(dims, mu, [1], 1, 0)
+    ps = list(range(-10, 10))
+    op = pt.laplacian(ctx, dims, m2)
+    est, _, _, _ = pt.trace(op, _t(col), m, mu, ps, "z2", 5, 0, 2, True, "mixed_fp32", 1e-11, 5000)
+    want = OE.probed_estimates(OE.Laplacian(dims, m2), col, m, 5, 2, 0, mu, ps, 1e-13)
+    assert np.allclose(est, want, rtol=1e-8, atol=1e-9 * np.abs(want).max())
+    c1, m1 = greedy_colour(dims, mu, [1], 1, 0)
+    c2, m2n = nested_colour(dims, mu, [1], 2, c1, 0)
+    cols = torch.as_tensor(np.stack([c1, c2]).astype(np.int32)).cuda().contiguous()
+    est_n, _ = pt.trace_nested(op, cols, [m1, m2n], mu, [0, 1], "z2", 9, 0, 2, True, "mixed_fp32", 1e-11, 5000)
+    lap = OE.Laplacian(dims, m2)
+    for lev, (c, mm) in enumerate([(c1, m1), (c2, m2n)]):
+        w = OE.probed_estimates(lap, c, mm, 9, 2, 0, mu, [0, 1], 1e-13)
+        assert np.allclose(est_n[lev], w, rtol=1e-8, atol=1e-9 * np.abs(w).max()), lev
+
+
+def test_autotuner_chooses_between_full_and_evenodd(pt, ctx):
+    dims, m2, p = [8, 8, 8, 8], 0.05, 1
+    col, m = greedy_colour(dims, 0, [p], 2, 0)
+    op = pt.laplacian(ctx, dims, m2)
+    best = pt.autotune(op, _t(col), m, 0, "z2", 3, "mixed_fp32", 1e-10, 5000, 16)
+    assert best["evenodd"] in (0, 1) and pt.get_tuning(op, "mixed_fp32")["evenodd"] == best["evenodd"]
+    est, _, _, _ = pt.trace(op, _t(col), m, 0, [p], "z2", 3, 0, 2, True, "mixed_fp32", 1e-10, 5000)
+    want = OE.probed_estimates(OE.Laplacian(dims, m2), col, m, 3, 2, 0, 0, [p], 1e-12)
+    assert np.allclose(est, want, rtol=1e-8, atol=1e-9)
+    pt.set_tuning(op, "mixed_fp32", reset=True)
+    odd = pt.laplacian(ctx, [5, 4, 4, 4], m2)
+    assert pt.get_tuning(odd, "mixed_fp32")["evenodd"] == 0          # an odd side: full system
