@@ -134,13 +134,22 @@ PT_API int pt_set_launch_limit(pt_ctx *ctx, int64_t n);
  *                outer steps run as CUDA-graph branches beside the inner
  *                Krylov kernels (they work on disjoint right-hand sides);
  *                0: one kernel after another
- *   evenodd      Laplacian with every lattice side even: 1 solves each
- *                right-hand side through the Schur complement on the even
- *                sites, S = d - H_eo H_oe / d (d = 8 + m2, H the hops), with
- *                the odd half rebuilt as x_o = (b_o + H_oe x_e) / d; the
+ *   evenodd      every lattice side even: 1 solves each right-hand side
+ *                through the Schur complement on the even sites, with the
+ *                odd half rebuilt from it (Laplacian S = d - H_eo H_oe / d,
+ *                d = 8 + m2, H the hops, x_o = (b_o + H_oe x_e) / d; Wilson
+ *                S = 1 - kappa^2 D_eo D_oe, x_o = b_o + kappa D_oe x_e); the
  *                stopping test stays the full system's ||b - A x|| / ||b||.
  *                0: the full system.  The default is 1 where allowed; it is
- *                ignored for Wilson, for odd sides and by pt_grad.
+ *                ignored for odd sides and by pt_grad, and it replaces
+ *                rhs_block by 1.
+ *   cta_threads  threads of every work-item kernel's CTA: 64, 128 or 256
+ *                (0 means 256)
+ *   sites_per_thread  Laplacian: lattice sites (even-odd: half-lattice
+ *                entries) per thread of a work item: 4, 8 or 16 (0 means 8);
+ *                a work item is cta_threads x sites_per_thread sites.  The
+ *                Wilson kernels take one site per thread (pt_get_tuning
+ *                reports 1).
  * seconds_per_rhs is an output of pt_autotune (device time per trial RHS). */
 typedef struct pt_tune {
     double delta;
@@ -149,13 +158,16 @@ typedef struct pt_tune {
     int32_t rhs_block;
     int32_t overlap;
     int32_t evenodd;
+    int32_t cta_threads;
+    int32_t sites_per_thread;
     double seconds_per_rhs;
 } pt_tune;
 
 /* Autotuner: solves the same trial right-hand sides (up to trial_rhs probes
  * of one noise set spread over the colours of col_dev) with candidate
- * parameters, by coordinate descent over evenodd (Laplacian with even sides),
- * delta (mixed precision), rhs_block and group (Wilson) and graph_iters
+ * parameters, by coordinate descent over evenodd (every side even),
+ * delta (mixed precision), rhs_block and group (Wilson), the work-item shape
+ * (cta_threads; sites_per_thread for the Laplacian) and graph_iters
  * (overlap stays as set), keeps the fastest, and stores it in the context
  * for this operator's (kind, precision, lattice); later solves, traces and
  * gradients with that key use it.  *best (host) receives it.  Synchronises. */
@@ -197,6 +209,10 @@ PT_API int pt_op_wilson(pt_ctx *ctx, const int dims[4], const double *U_dev, dou
 /* Degrees of freedom per site of the operator (1 or 12), or a negative error. */
 PT_API int pt_op_dof(const pt_op *op);
 
+/* Free an operator (its packed links).  Waits for the device.  It does not
+ * use the context, so it may be called before or after pt_destroy of the
+ * context the operator was made with (e.g. by a garbage collector that
+ * finalises both in no particular order). */
 PT_API int pt_op_destroy(pt_op *op);
 
 /* y = A x for nrhs fields in the user layout (device).  prec: PT_PREC_FP64

@@ -97,6 +97,12 @@ extern "C" int pt_set_max_slots(pt_ctx *c, int n) {
     return PT_OK;
 }
 
+extern "C" int pt_set_launch_limit(pt_ctx *c, int64_t n) {
+    PT_CHECK_ARG(c && n >= 0, "pt_set_launch_limit: need n >= 0");
+    c->launch_limit = n;
+    return PT_OK;
+}
+
 extern "C" int pt_profile_enable(pt_ctx *c, int on) {
     PT_CHECK_ARG(c, "pt_profile_enable: ctx is NULL");
     c->prof = on != 0;
@@ -162,6 +168,7 @@ extern "C" int pt_op_laplacian(pt_ctx *c, const int dims[4], double m2, pt_op **
     pt_op *op = (pt_op *)calloc(1, sizeof(pt_op));
     if (!op) { pt_set_error("host allocation failed"); return PT_ERR_OOM; }
     op->ctx = c;
+    op->device = c->device;
     op->kind = 0;
     memcpy(op->dims, dims, 4 * sizeof(int));
     op->g = make_geom(dims);
@@ -179,6 +186,7 @@ extern "C" int pt_op_wilson(pt_ctx *c, const int dims[4], const double *U_dev, d
     pt_op *op = (pt_op *)calloc(1, sizeof(pt_op));
     if (!op) { pt_set_error("host allocation failed"); return PT_ERR_OOM; }
     op->ctx = c;
+    op->device = c->device;
     op->kind = 1;
     memcpy(op->dims, dims, 4 * sizeof(int));
     op->g = make_geom(dims);
@@ -212,11 +220,13 @@ extern "C" int pt_op_wilson(pt_ctx *c, const int dims[4], const double *U_dev, d
 
 extern "C" int pt_op_dof(const pt_op *op) { return op ? op->dof : PT_ERR_ARG; }
 
+// Does not read the context: an operator may outlive it (a garbage collector
+// finalises objects of a reference cycle in no particular order).  cudaFree
+// waits for the device, so no work that still reads the links is cut short.
 extern "C" int pt_op_destroy(pt_op *op) {
     if (!op) return PT_OK;
     if (op->kind == 1) {
-        cudaSetDevice(op->ctx->device);
-        cudaStreamSynchronize(op->ctx->stream);
+        cudaSetDevice(op->device);
         cudaFree(op->U64); cudaFree(op->U32); cudaFree(op->U16);
     }
     free(op);

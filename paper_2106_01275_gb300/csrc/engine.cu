@@ -55,6 +55,7 @@ struct TaskStat {
 struct EP {
     Geom g;
     int kind, nsb, R, gs, vec4;
+    int bs, spt;               // threads of an item kernel's CTA; sites per thread (an item is bs x spt sites)
     int eo;                    // Laplacian on the even Schur complement (inner vectors on the even sites)
     int nsite;                 // entries of a slot field: N, or N / 2 in even-odd mode
     int rhs_block;             // Wilson applies: right-hand sides per item (1 or 2)
@@ -80,7 +81,8 @@ struct EP {
     const double *B_user;      // solve mode: user layout sources
     double *X_user;            // solve mode: user layout solutions
     double *x64;
-    double *t64;               // even-odd: H_oe x64 on the odd sites (FP64)
+    double *t64;               // even-odd: H_oe x64 (Laplacian) / D_oe x64 (Wilson) on the odd sites (FP64)
+    double *b64;               // even-odd: b'_e of the slot's task (FP64; b_e + H_eo b_o / d, resp. + kappa D_eo b_o)
     void *e, *r, *pv, *q, *s, *t, *r0, *p1;   // p1: second CG direction buffer; even-odd: t = H_oe p (odd sites)
     Slot *slots;
     double *partials;
@@ -166,8 +168,9 @@ __device__ __forceinline__ Cx<double> source_val(const EP &P, const Task &tk, ui
 }
 
 // ------------------------------------------------------------------ work items and reductions
-// An item is one slot's block of Tile<KIND>::SITES consecutive sites, processed
-// by one CTA of PT_BLOCK threads (SPT sites per thread).  A reduction stores one
+// An item is one slot's block of bs x spt consecutive sites, processed by one
+// CTA of bs threads (spt sites per thread; by default PT_BLOCK threads and
+// Tile<KIND>::SPT sites, the autotuner may choose others).  A reduction stores one
 // partial sum per item (plain stores: the kernel boundary orders them); a
 // finalize kernel with one warp per slot adds the slot's nsb partials in a
 // fixed order (deterministic) and advances the slot's state machine.
@@ -196,8 +199,8 @@ struct Tile {
 #define ITEM_LOOP_END }
 
 #define SITE_LOOP(KIND)                                                         \
-    for (int k_ = 0; k_ < Tile<KIND>::SPT; ++k_) {                              \
-        const int idx = b * Tile<KIND>::SITES + k_ * PT_BLOCK + (int)threadIdx.x; \
+    for (int k_ = 0; k_ < ((KIND) ? 1 : P.spt); ++k_) {                         \
+        const int idx = b * (((KIND) ? 1 : P.spt) * P.bs) + k_ * P.bs + (int)threadIdx.x; \
         if (idx >= N) continue;
 #define SITE_LOOP_END }
 
@@ -722,8 +725,8 @@ template <> struct Quad<__nv_bfloat16> {
 };
 
 #define QUAD_LOOP                                                               \
-    for (int k_ = 0; k_ < Tile<0>::SPT / 4; ++k_) {                             \
-        const int idx = 4 * (b * (Tile<0>::SITES / 4) + k_ * PT_BLOCK + (int)threadIdx.x); \
+    for (int k_ = 0; k_ < P.spt / 4; ++k_) {                                    \
+        const int idx = 4 * (b * (P.spt / 4 * P.bs) + k_ * P.bs + (int)threadIdx.x); \
         if (idx >= N) continue;
 #define QUAD_LOOP_END }
 
@@ -840,10 +843,13 @@ __global__ void __launch_bounds__(PT_BLOCK) k_cg_update_v4(EP P) {
 //   k_cg_update  even entries: e += alpha p_i, r -= alpha q, partial |r|^2
 // which moves 6 + 10 + 12 = 28 bytes per lattice site in FP32 (40 on the full
 // system).  The FP64 outer step forms t64 = H_oe x64 on the odd entries, then
-// r = b'_e - S x64 on the even ones, with b'_e regenerated from the noise; its
+// r = b'_e - S x64 on the even ones, with b'_e formed from the regenerated
+// noise when the task starts and kept in FP64; its
 // |b|^2 is that of the whole source (both parities), so the stopping test is
 // the full system's ||b - A x|| / ||b|| (r_o = 0 once x_o is rebuilt).  The
-// contraction rebuilds x_o wherever it reads an odd site.
+// contraction reads x_o = (b_o + t64) / d wherever it reads an odd site
+// (t64 = H_oe x64 of the final x64: a slot converges right after the outer
+// step that formed it).
 
 // storage index and coordinates of entry h of the half field of parity par
 __device__ __forceinline__ int half_site(const Geom &g, int par, int h, int x[4]) {
@@ -1077,10 +1083,12 @@ __global__ void __launch_bounds__(PT_BLOCK) k_eo_outer_hop(EP P) {
     ITEM_LOOP_END
 }
 
-// outer step, part 2, at the even entries: r64 = b'_e - S x64 in FP64 with
-// b'_e = b_e + H_eo b_o / d regenerated from the source; r = (S) r64 starts
-// the inner solve (e = 0).  Partials: |r64|^2, |b|^2 of both sites of the
-// entry (even and odd), |r|^2 of the rounded r.
+// outer step, part 2, at the even entries: r64 = b'_e - S x64 in FP64, with
+// b'_e = b_e + H_eo b_o / d formed from the regenerated source when the task
+// starts (x = 0, so r64 = b'_e) and kept in FP64 for its later outer steps;
+// r = (S) r64 starts the inner solve (e = 0).  Partials: |r64|^2, |b|^2 of
+// both sites of the entry (even and odd; used when the task starts), |r|^2
+// of the rounded r.
 template <typename S>
 __global__ void __launch_bounds__(PT_BLOCK) k_eo_outer_residual(EP P) {
     typedef typename ArithT<S>::T R;
@@ -1097,44 +1105,73 @@ __global__ void __launch_bounds__(PT_BLOCK) k_eo_outer_residual(EP P) {
         S *e = slot_ptr<S>(P.e, j, P.L);
         const double *x = P.x64 + (size_t)j * P.L;
         const double *t = P.t64 + (size_t)j * P.L;
-        double v[3] = {0.0, 0.0, 0.0};
+        double *bp = P.b64 + (size_t)j * P.L;
+        // A probe's entries are 0 or +-1: their neighbour sum and |b|^2 are
+        // exact in FP32 (user sources in solve mode stay FP64); |r|^2 of the
+        // rounded r is summed in the inner solve's arithmetic.
+        const bool probe = P.mode != MODE_SOLVE;
+        double v0 = 0.0, v1d = 0.0;
+        float v1f = 0.f;
+        R v2r = R(0);
         SITE_LOOP(0)
-            int xc[4], y4[4];
-            const int s = half_site(P.g, 0, idx, xc);
-            const double b_e = source_val<0>(P, tk, key, s, xc, 0).re;
-            double b_nb = 0.0;
+            double rv;
+            if (ph == PH_START) {
+                int xc[4], y4[4];
+                const int s = half_site(P.g, 0, idx, xc);
 #pragma unroll
-            for (int mu = 0; mu < 4; ++mu) {
-                nb_coords(P.g, xc, mu, 1, y4);
-                b_nb += source_val<0>(P, tk, key, nb_fwd(P.g, s, xc, mu), y4, 0).re;
-                nb_coords(P.g, xc, mu, -1, y4);
-                b_nb += source_val<0>(P, tk, key, nb_bwd(P.g, s, xc, mu), y4, 0).re;
+                for (int nu = 0; nu < 4; ++nu) y4[nu] = xc[nu];
+                y4[0] ^= 1;                                  // the odd site of the same entry
+                const Cx<double> be = source_val<0>(P, tk, key, s, xc, 0);
+                const Cx<double> bo = source_val<0>(P, tk, key, s ^ 1, y4, 0);
+                double b_nb;
+                if (probe) {
+                    float f = 0.f;
+#pragma unroll
+                    for (int mu = 0; mu < 4; ++mu) {
+                        nb_coords(P.g, xc, mu, 1, y4);
+                        f += (float)source_val<0>(P, tk, key, nb_fwd(P.g, s, xc, mu), y4, 0).re;
+                        nb_coords(P.g, xc, mu, -1, y4);
+                        f += (float)source_val<0>(P, tk, key, nb_bwd(P.g, s, xc, mu), y4, 0).re;
+                    }
+                    b_nb = (double)f;
+                    v1f += (float)(be.re * be.re) + (float)(bo.re * bo.re);
+                } else {
+                    b_nb = 0.0;
+#pragma unroll
+                    for (int mu = 0; mu < 4; ++mu) {
+                        nb_coords(P.g, xc, mu, 1, y4);
+                        b_nb += source_val<0>(P, tk, key, nb_fwd(P.g, s, xc, mu), y4, 0).re;
+                        nb_coords(P.g, xc, mu, -1, y4);
+                        b_nb += source_val<0>(P, tk, key, nb_bwd(P.g, s, xc, mu), y4, 0).re;
+                    }
+                    v1d += be.re * be.re + bo.re * bo.re;
+                }
+                rv = be.re + b_nb * inv_d;                   // x = 0
+                bp[idx] = rv;
+            } else {
+                int xc[4];
+                const int s = half_site(P.g, 0, idx, xc);
+                rv = bp[idx] - (d * x[idx] - half_nbsum<double, double>(P.g, t, s, xc) * inv_d);
             }
-#pragma unroll
-            for (int nu = 0; nu < 4; ++nu) y4[nu] = xc[nu];
-            y4[0] ^= 1;                                  // the odd site of the same entry
-            const double b_o = source_val<0>(P, tk, key, s ^ 1, y4, 0).re;
-            const double bp = b_e + b_nb * inv_d;
-            const double sx = d * x[idx] - half_nbsum<double, double>(P.g, t, s, xc) * inv_d;
-            const double rv = bp - sx;
-            v[0] += rv * rv;
-            v[1] += b_e * b_e + b_o * b_o;
+            v0 += rv * rv;
             const R rs = rnd<S, R>((R)rv);
             st_real(r, (size_t)idx, rs);
             st_real(e, (size_t)idx, R(0));
-            v[2] += (double)rs * (double)rs;
+            v2r += rs * rs;
         SITE_LOOP_END
+        double v[3] = {v0, v1d + (double)v1f, (double)v2r};
         item_store<3>(P, j, b, v, sh);
     ITEM_LOOP_END
 }
 
 // x at storage site y (coordinates xy): its even entry, or on an odd site
-// x_o = (b_o + H_oe x_e) / d rebuilt from the source and the even neighbours
-__device__ __forceinline__ double eo_x_at(const EP &P, const Task &tk, uint64_t key, const double *x, int y,
-                                          const int xy[4]) {
+// x_o = (b_o + H_oe x_e) / d from the source and t64 = H_oe x_e, which the
+// outer step formed for the final x_e (the slot converged right after it)
+__device__ __forceinline__ double eo_x_at(const EP &P, const Task &tk, uint64_t key, const double *x,
+                                          const double *t64, int y, const int xy[4]) {
     if (((xy[0] + xy[1] + xy[2] + xy[3]) & 1) == 0) return x[y >> 1];
     const double b_o = source_val<0>(P, tk, key, y, xy, 0).re;
-    return (b_o + half_nbsum<double, double>(P.g, x, y, xy)) / P.diag;
+    return (b_o + t64[y >> 1]) / P.diag;
 }
 
 // the contraction (trace mode) or the copy-out (solve mode) of k_contract for
@@ -1148,6 +1185,7 @@ __global__ void __launch_bounds__(PT_BLOCK) k_eo_contract(EP P) {
         if (st.phase != PH_CONTRACT) continue;
         const Task tk = P.tasks[st.task];
         const double *x = P.x64 + (size_t)j * P.L;
+        const double *t64 = P.t64 + (size_t)j * P.L;
         const uint64_t key = (P.mode == MODE_SOLVE) ? 0 : pt_set_key(P.seed, tk.set);
         if (P.mode == MODE_SOLVE) {
             SITE_LOOP(0)
@@ -1155,7 +1193,7 @@ __global__ void __launch_bounds__(PT_BLOCK) k_eo_contract(EP P) {
                     const int sw = 2 * idx + w;
                     int xs[4];
                     site_coords(P.g, sw, xs);
-                    P.X_user[(size_t)tk.set * NF + sw] = eo_x_at(P, tk, key, x, sw, xs);
+                    P.X_user[(size_t)tk.set * NF + sw] = eo_x_at(P, tk, key, x, t64, sw, xs);
                 }
             SITE_LOOP_END
             continue;
@@ -1188,7 +1226,7 @@ __global__ void __launch_bounds__(PT_BLOCK) k_eo_contract(EP P) {
                     for (int nu = 0; nu < 4; ++nu) xy[nu] = xs[nu];
                     int cm = (xs[P.mu] + P.p[n]) % P.g.D[P.mu];
                     xy[P.mu] = cm < 0 ? cm + P.g.D[P.mu] : cm;
-                    const double xv = eo_x_at(P, tk, key, x, y, xy);
+                    const double xv = eo_x_at(P, tk, key, x, t64, y, xy);
                     acc[2 * n] += z.re * xv;                // conj(z) x
                     acc[2 * n + 1] -= z.im * xv;
                 }
@@ -1259,7 +1297,7 @@ template <typename S>
 __global__ void __launch_bounds__(PT_BLOCK) k_bicg_s(EP P) {
     typedef Fld<1, S> F;
     typedef typename F::R R;
-    const int N = P.g.N;
+    const int N = P.nsite;            // field entries per slot (N/2 in even-odd mode)
     ITEM_LOOP(LIST_INNER)
         const Slot &st = P.slots[j];
         if (st.phase != PH_INNER) continue;
@@ -1446,7 +1484,7 @@ __global__ void __launch_bounds__(PT_BLOCK) k_bicg_update(EP P) {
     typedef Fld<1, S> F;
     typedef typename F::R R;
     __shared__ double sh[32 * 3];
-    const int N = P.g.N;
+    const int N = P.nsite;            // field entries per slot (N/2 in even-odd mode)
     ITEM_LOOP(LIST_INNER)
         const Slot &st = P.slots[j];
         if (st.phase != PH_INNER) continue;
@@ -1517,7 +1555,7 @@ template <typename S>
 __global__ void __launch_bounds__(PT_BLOCK) k_bicg_dir(EP P) {
     typedef Fld<1, S> F;
     typedef typename F::R R;
-    const int N = P.g.N;
+    const int N = P.nsite;            // field entries per slot (N/2 in even-odd mode)
     ITEM_LOOP(LIST_INNER)
         const Slot &st = P.slots[j];
         if (st.phase != PH_INNER) continue;
@@ -1541,6 +1579,457 @@ __global__ void __launch_bounds__(PT_BLOCK) k_bicg_dir(EP P) {
     ITEM_LOOP_END
 }
 
+// ------------------------------------------------------------------ even-odd BiCGStab (Wilson)
+// With every side even, A = 1 - kappa D has D_ee = D_oo = 0, and A x = b is
+// solved through the Schur complement on the even sites:
+//   S x_e = b'_e,  S = 1 - kappa^2 D_eo D_oe,  b'_e = b_e + kappa D_eo b_o,
+//   x_o = b_o + kappa D_oe x_e.
+// Each application of S is two half-lattice hops: k_weo_hop forms
+// h = D_oe p at the odd entries, k_weo_apply1 / k_weo_apply2 then p - kappa^2
+// D_eo h at the even entries with BiCGStab's dot products.  S is better
+// conditioned than A (about half the iterations) and its vectors are half as
+// long.  The FP64 outer step forms t64 = D_oe x64 at the odd entries, then
+// r = b'_e - S x64 at the even ones; b'_e is formed once per task (its first
+// outer step, from the source regenerated at the site and its eight odd
+// neighbours) and kept in FP64.  The stopping test is the full system's
+// ||b - A x|| / ||b|| with |b|^2 over both parities (r_o = 0 once x_o is
+// rebuilt).  The contraction and the copy-out read x_o = b_o + kappa t64,
+// t64 = D_oe x64 of the final x64, where they read an odd site.
+
+// One hop of the Wilson hopping term into acc at site idx (coordinates x):
+// forward (1 - g_mu) U_mu(x) psi(x + mu) or backward (1 + g_mu)
+// U_mu(x - mu)^dagger psi(x - mu), with psi = ps the neighbour's spinor and
+// the boundary sign of antiperiodic time
+template <typename R, typename LS>
+__device__ __forceinline__ void wilson_hop_dir(const Geom &g, const LS *U, int antip, int idx, const int x[4],
+                                               int mu, bool fwd, const Cx<R> ps[4][3], Cx<R> acc[4][3]) {
+    Cx<R> h[2][3], uh[2][3], u[3][3];
+    if (fwd) {
+        const R eta = (antip && mu == 3 && x[3] == g.D[3] - 1) ? R(-1) : R(1);
+        spin_project<R>(mu, R(-1), ps, h);
+        load_link<R, LS>(U, g.N, mu, idx, u);
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                Cx<R> t = cmul(u[a][0], h[k][0]);
+                t = cadd(t, cmul(u[a][1], h[k][1]));
+                t = cadd(t, cmul(u[a][2], h[k][2]));
+                uh[k][a] = t;
+            }
+        spin_accumulate<R>(mu, R(-1), eta, uh, acc);
+    } else {
+        const R eta = (antip && mu == 3 && x[3] == 0) ? R(-1) : R(1);
+        spin_project<R>(mu, R(1), ps, h);
+        load_link<R, LS>(U, g.N, mu, nb_bwd(g, idx, x, mu), u);
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                Cx<R> t = cconjmul(u[0][a], h[k][0]);
+                t = cadd(t, cconjmul(u[1][a], h[k][1]));
+                t = cadd(t, cconjmul(u[2][a], h[k][2]));
+                uh[k][a] = t;
+            }
+        spin_accumulate<R>(mu, R(1), eta, uh, acc);
+    }
+}
+
+// (H psi)(x) at site idx (coordinates x) as in wilson_hop_site, with the
+// neighbour spinors supplied by fetch(y, mu, dir, ps) (dir +1 forward, -1
+// backward) and the links from the packed full-lattice arrays
+template <typename R, typename LS, typename Fetch>
+__device__ __forceinline__ void wilson_hop_fetch(const Geom &g, Fetch fetch, const LS *U, int antip, int idx,
+                                                 const int x[4], Cx<R> acc[4][3]) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[s][a] = Cx<R>{R(0), R(0)};
+    const int N = g.N;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        {   // forward hop: (1 - g_mu) U_mu(x) psi(x + mu)
+            const int y = nb_fwd(g, idx, x, mu);
+            const R eta = (antip && mu == 3 && x[3] == g.D[3] - 1) ? R(-1) : R(1);
+            Cx<R> ps[4][3], h[2][3], uh[2][3], u[3][3];
+            fetch(y, mu, 1, ps);
+            spin_project<R>(mu, R(-1), ps, h);
+            load_link<R, LS>(U, N, mu, idx, u);
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    Cx<R> t = cmul(u[a][0], h[k][0]);
+                    t = cadd(t, cmul(u[a][1], h[k][1]));
+                    t = cadd(t, cmul(u[a][2], h[k][2]));
+                    uh[k][a] = t;
+                }
+            spin_accumulate<R>(mu, R(-1), eta, uh, acc);
+        }
+        {   // backward hop: (1 + g_mu) U_mu(x - mu)^dagger psi(x - mu)
+            const int y = nb_bwd(g, idx, x, mu);
+            const R eta = (antip && mu == 3 && x[3] == 0) ? R(-1) : R(1);
+            Cx<R> ps[4][3], h[2][3], uh[2][3], u[3][3];
+            fetch(y, mu, -1, ps);
+            spin_project<R>(mu, R(1), ps, h);
+            load_link<R, LS>(U, N, mu, y, u);
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    Cx<R> t = cconjmul(u[0][a], h[k][0]);
+                    t = cadd(t, cconjmul(u[1][a], h[k][1]));
+                    t = cadd(t, cconjmul(u[2][a], h[k][2]));
+                    uh[k][a] = t;
+                }
+            spin_accumulate<R>(mu, R(1), eta, uh, acc);
+        }
+    }
+}
+
+// whether the source of a task can be nonzero at storage site y: a probe
+// lives on its colour class only (user sources in solve mode everywhere)
+__device__ __forceinline__ bool source_may_be_nonzero(const EP &P, const Task &tk, int y) {
+    if (P.mode == MODE_SOLVE || (tk.flags & TASK_ADJ)) return true;
+    return P.col[(size_t)tk.cidx * P.g.N + y] == tk.colour;
+}
+
+// h = D_oe p at the odd entries (WHICH 0: p = pv, the first apply; 1: p = s)
+template <typename S, typename LS, int WHICH>
+__global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 : PT_WIL_MINB) k_weo_hop(EP P) {
+    typedef typename ArithT<S>::T R;
+    const int N = P.nsite;
+    ITEM_LOOP(LIST_INNER)
+        const Slot &st = P.slots[j];
+        if (st.phase != PH_INNER) continue;
+        const S *src = slot_cptr<S>(WHICH ? P.s : P.pv, j, P.L);
+        S *h = slot_ptr<S>(P.p1, j, P.L);
+        SITE_LOOP(1)
+            int xc[4];
+            const int s = half_site(P.g, 1, idx, xc);
+            Cx<R> acc[4][3], o[12];
+            wilson_hop_fetch<R, LS>(
+                P.g, [&](int y, int, int, Cx<R> ps[4][3]) { load_spinor<S, R>(src, N, y >> 1, ps); },
+                (const LS *)P.U, P.antip, s, xc, acc);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) o[c] = Cx<R>{rnd<S, R>(acc[c / 3][c % 3].re), rnd<S, R>(acc[c / 3][c % 3].im)};
+            store_spinor<S, R>(h, N, idx, o);
+        SITE_LOOP_END
+    ITEM_LOOP_END
+}
+
+// v = S p = p - kappa^2 D_eo h at the even entries;  partial (r0, v)
+template <typename S, typename LS>
+__global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 : PT_WIL_MINB) k_weo_apply1(EP P) {
+    typedef typename ArithT<S>::T R;
+    __shared__ double sh[32 * 2];
+    const int N = P.nsite;
+    const R k2 = (R)(P.kappa * P.kappa);
+    ITEM_LOOP(LIST_INNER)
+        const Slot &st = P.slots[j];
+        if (st.phase != PH_INNER) continue;
+        const S *pv = slot_cptr<S>(P.pv, j, P.L);
+        const S *h = slot_cptr<S>(P.p1, j, P.L);
+        const S *r0 = slot_cptr<S>(P.r0, j, P.L);
+        S *q = slot_ptr<S>(P.q, j, P.L);
+        R vr[2] = {R(0), R(0)};
+        SITE_LOOP(1)
+            int xc[4];
+            const int s = half_site(P.g, 0, idx, xc);
+            Cx<R> acc[4][3], ps[4][3], z[4][3], av[12];
+            wilson_hop_fetch<R, LS>(
+                P.g, [&](int y, int, int, Cx<R> f[4][3]) { load_spinor<S, R>(h, N, y >> 1, f); },
+                (const LS *)P.U, P.antip, s, xc, acc);
+            load_spinor<S, R>(pv, N, idx, ps);
+            load_spinor<S, R>(r0, N, idx, z);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                const Cx<R> w = csub(ps[c / 3][c % 3], cscale(acc[c / 3][c % 3], k2));
+                av[c] = Cx<R>{rnd<S, R>(w.re), rnd<S, R>(w.im)};
+                const Cx<R> zc = z[c / 3][c % 3];
+                vr[0] += zc.re * av[c].re + zc.im * av[c].im;
+                vr[1] += zc.re * av[c].im - zc.im * av[c].re;
+            }
+            store_spinor<S, R>(q, N, idx, av);
+        SITE_LOOP_END
+        item_store_r<2>(P, j, b, vr, sh);
+    ITEM_LOOP_END
+}
+
+// t = S s = s - kappa^2 D_eo h at the even entries;  partials (t, s), |t|^2
+template <typename S, typename LS>
+__global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 : PT_WIL_MINB) k_weo_apply2(EP P) {
+    typedef typename ArithT<S>::T R;
+    __shared__ double sh[32 * 3];
+    const int N = P.nsite;
+    const R k2 = (R)(P.kappa * P.kappa);
+    ITEM_LOOP(LIST_INNER)
+        const Slot &st = P.slots[j];
+        if (st.phase != PH_INNER) continue;
+        const S *sv = slot_cptr<S>(P.s, j, P.L);
+        const S *h = slot_cptr<S>(P.p1, j, P.L);
+        S *t = slot_ptr<S>(P.t, j, P.L);
+        R vr[3] = {R(0), R(0), R(0)};
+        SITE_LOOP(1)
+            int xc[4];
+            const int s = half_site(P.g, 0, idx, xc);
+            Cx<R> acc[4][3], sp[4][3], av[12];
+            wilson_hop_fetch<R, LS>(
+                P.g, [&](int y, int, int, Cx<R> f[4][3]) { load_spinor<S, R>(h, N, y >> 1, f); },
+                (const LS *)P.U, P.antip, s, xc, acc);
+            load_spinor<S, R>(sv, N, idx, sp);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                const Cx<R> w = csub(sp[c / 3][c % 3], cscale(acc[c / 3][c % 3], k2));
+                av[c] = Cx<R>{rnd<S, R>(w.re), rnd<S, R>(w.im)};
+            }
+            store_spinor<S, R>(t, N, idx, av);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                const Cx<R> tv = av[c], sc = sp[c / 3][c % 3];
+                vr[0] += tv.re * sc.re + tv.im * sc.im;     // (t, s) = conj(t) s
+                vr[1] += tv.re * sc.im - tv.im * sc.re;
+                vr[2] += tv.re * tv.re + tv.im * tv.im;
+            }
+        SITE_LOOP_END
+        item_store_r<3>(P, j, b, vr, sh);
+    ITEM_LOOP_END
+}
+
+// outer step, part 1: t64 = D_oe x64 at the odd entries (FP64); a new task
+// starts from x = 0, so its t64 is zero (written, not hopped: the
+// contraction reads it if the task converges at once)
+__global__ void __launch_bounds__(PT_BLOCK) k_weo_outer_hop(EP P) {
+    const int N = P.nsite;
+    ITEM_LOOP(LIST_OUTER)
+        const int ph = P.slots[j].phase;
+        if (ph != PH_START && ph != PH_OUTER) continue;
+        const double *x = P.x64 + (size_t)j * P.L;
+        double *t = P.t64 + (size_t)j * P.L;
+        SITE_LOOP(1)
+            Cx<double> o[12];
+            if (ph == PH_START) {
+#pragma unroll
+                for (int c = 0; c < 12; ++c) o[c] = Cx<double>{0.0, 0.0};
+            } else {
+                int xc[4];
+                const int s = half_site(P.g, 1, idx, xc);
+                Cx<double> acc[4][3];
+                wilson_hop_fetch<double, double>(
+                    P.g, [&](int y, int, int, Cx<double> f[4][3]) { load_spinor<double, double>(x, N, y >> 1, f); },
+                    P.U64, P.antip, s, xc, acc);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) o[c] = acc[c / 3][c % 3];
+            }
+            store_spinor<double, double>(t, N, idx, o);
+        SITE_LOOP_END
+    ITEM_LOOP_END
+}
+
+// outer step, part 2 (new tasks only), at the even entries: b'_e = b_e +
+// kappa D_eo b_o from the source regenerated at the site and at those of its
+// eight odd neighbours where it can be nonzero (a skipped neighbour would add
+// exact zeros); kept in FP64 for the task's later outer steps
+__global__ void __launch_bounds__(PT_BLOCK) k_weo_outer_bprime(EP P) {
+    const int N = P.nsite;
+    const double kap = P.kappa;
+    ITEM_LOOP(LIST_OUTER)
+        const Slot &st = P.slots[j];
+        if (st.phase != PH_START) continue;
+        const Task tk = P.tasks[st.task];
+        const uint64_t key = (P.mode == MODE_SOLVE) ? 0 : pt_set_key(P.seed, tk.set);
+        double *bp = P.b64 + (size_t)j * P.L;
+        SITE_LOOP(1)
+            int xc[4];
+            const int s = half_site(P.g, 0, idx, xc);
+            Cx<double> acc[4][3], bv[12];
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) acc[sp][a] = Cx<double>{0.0, 0.0};
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+                for (int dir = 1; dir >= -1; dir -= 2) {
+                    const int y = dir > 0 ? nb_fwd(P.g, s, xc, mu) : nb_bwd(P.g, s, xc, mu);
+                    if (!source_may_be_nonzero(P, tk, y)) continue;
+                    int y4[4];
+                    nb_coords(P.g, xc, mu, dir, y4);
+                    Cx<double> f[4][3];
+#pragma unroll
+                    for (int c = 0; c < 12; ++c) f[c / 3][c % 3] = source_val<1>(P, tk, key, y, y4, c);
+                    wilson_hop_dir<double, double>(P.g, P.U64, P.antip, s, xc, mu, dir > 0, f, acc);
+                }
+#pragma unroll
+            for (int c = 0; c < 12; ++c)
+                bv[c] = cadd(source_val<1>(P, tk, key, s, xc, c), cscale(acc[c / 3][c % 3], kap));
+            store_spinor<double, double>(bp, N, idx, bv);
+        SITE_LOOP_END
+    ITEM_LOOP_END
+}
+
+// outer step, part 3, at the even entries: r64 = b'_e - S x64 in FP64
+// (= b'_e for a new task, x = 0); r = (S) r64 starts the inner solve
+// (p = r0 = r, e = 0).  Partials: |r64|^2, |b|^2 of both sites of the entry
+// (even and odd; used when the task starts), |r|^2 of the rounded r.
+template <typename S>
+__global__ void __launch_bounds__(PT_BLOCK) k_weo_outer_residual(EP P) {
+    typedef typename ArithT<S>::T R;
+    __shared__ double sh[32 * 3];
+    const int N = P.nsite;
+    const double k2 = P.kappa * P.kappa;
+    ITEM_LOOP(LIST_OUTER)
+        const Slot &st = P.slots[j];
+        const int ph = st.phase;
+        if (ph != PH_START && ph != PH_OUTER) continue;
+        const Task tk = P.tasks[st.task];
+        const uint64_t key = (P.mode == MODE_SOLVE) ? 0 : pt_set_key(P.seed, tk.set);
+        S *r = slot_ptr<S>(P.r, j, P.L);
+        S *pv = slot_ptr<S>(P.pv, j, P.L);
+        S *r0 = slot_ptr<S>(P.r0, j, P.L);
+        S *e = slot_ptr<S>(P.e, j, P.L);
+        const double *x = P.x64 + (size_t)j * P.L;
+        const double *t = P.t64 + (size_t)j * P.L;
+        const double *bp = P.b64 + (size_t)j * P.L;
+        double v[3] = {0.0, 0.0, 0.0};
+        SITE_LOOP(1)
+            int xc[4];
+            const int s = half_site(P.g, 0, idx, xc);
+            Cx<double> rv[12];
+            if (ph == PH_START) {
+                int xp[4] = {xc[0] ^ 1, xc[1], xc[2], xc[3]};          // the odd site of the same entry
+                Cx<double> bs[4][3];
+                load_spinor<double, double>(bp, N, idx, bs);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) {
+                    const Cx<double> be = source_val<1>(P, tk, key, s, xc, c);
+                    const Cx<double> bo = source_val<1>(P, tk, key, s ^ 1, xp, c);
+                    v[1] += be.re * be.re + be.im * be.im + bo.re * bo.re + bo.im * bo.im;
+                    rv[c] = bs[c / 3][c % 3];                           // x = 0
+                }
+            } else {
+                Cx<double> acc[4][3];
+                wilson_hop_fetch<double, double>(
+                    P.g, [&](int y, int, int, Cx<double> f[4][3]) { load_spinor<double, double>(t, N, y >> 1, f); },
+                    P.U64, P.antip, s, xc, acc);
+                // r = b' - x + kappa^2 D_eo t64, component by component
+#pragma unroll
+                for (int c = 0; c < 12; ++c) {
+                    const Cx<double> bc = ld_cx<double, double>(bp, N, c, idx);
+                    const Cx<double> xcc = ld_cx<double, double>(x, N, c, idx);
+                    rv[c] = csub(bc, csub(xcc, cscale(acc[c / 3][c % 3], k2)));
+                }
+            }
+            Cx<R> rs[12];
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                v[0] += rv[c].re * rv[c].re + rv[c].im * rv[c].im;
+                rs[c] = Cx<R>{rnd<S, R>((R)rv[c].re), rnd<S, R>((R)rv[c].im)};
+                v[2] += (double)rs[c].re * (double)rs[c].re + (double)rs[c].im * (double)rs[c].im;
+            }
+            store_spinor<S, R>(r, N, idx, rs);
+            store_spinor<S, R>(pv, N, idx, rs);
+            store_spinor<S, R>(r0, N, idx, rs);
+            Cx<R> zero[12];
+#pragma unroll
+            for (int c = 0; c < 12; ++c) zero[c] = Cx<R>{R(0), R(0)};
+            store_spinor<S, R>(e, N, idx, zero);
+        SITE_LOOP_END
+        item_store<3>(P, j, b, v, sh);
+    ITEM_LOOP_END
+}
+
+// x at storage site y (coordinates xy), all 12 components: its even entry,
+// or on an odd site x_o = b_o + kappa D_oe x_e from the source and
+// t64 = D_oe x_e, which the outer step formed for the final x_e (zero for a
+// task that converged at its first step, where x = 0)
+__device__ __forceinline__ void weo_x_at(const EP &P, const Task &tk, uint64_t key, const double *x,
+                                         const double *t64, int y, const int xy[4], Cx<double> out[12]) {
+    const int N = P.nsite;
+    Cx<double> f[4][3];
+    if (((xy[0] + xy[1] + xy[2] + xy[3]) & 1) == 0) {
+        load_spinor<double, double>(x, N, y >> 1, f);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) out[c] = f[c / 3][c % 3];
+        return;
+    }
+    load_spinor<double, double>(t64, N, y >> 1, f);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) out[c] = cadd(source_val<1>(P, tk, key, y, xy, c), cscale(f[c / 3][c % 3], P.kappa));
+}
+
+// the contraction (trace mode) or the copy-out (solve mode) for even-odd
+// Wilson slots: entry h covers the sites 2h and 2h + 1
+template <int MAXQ>
+__global__ void __launch_bounds__(PT_BLOCK) k_weo_contract(EP P) {
+    __shared__ double sh[32 * 2 * PT_MAX_P];
+    const int N = P.nsite, NF = P.g.N;
+    ITEM_LOOP(LIST_CONTRACT)
+        const Slot &st = P.slots[j];
+        if (st.phase != PH_CONTRACT) continue;
+        const Task tk = P.tasks[st.task];
+        const double *x = P.x64 + (size_t)j * P.L;
+        const double *t64 = P.t64 + (size_t)j * P.L;
+        const uint64_t key = (P.mode == MODE_SOLVE) ? 0 : pt_set_key(P.seed, tk.set);
+        if (P.mode == MODE_SOLVE) {
+            SITE_LOOP(1)
+                for (int w = 0; w < 2; ++w) {
+                    const int sw = 2 * idx + w;
+                    int xs[4];
+                    site_coords(P.g, sw, xs);
+                    Cx<double> xv[12];
+                    weo_x_at(P, tk, key, x, t64, sw, xs, xv);
+                    double *dst = P.X_user + ((size_t)tk.set * NF + sw) * 24;
+                    for (int c = 0; c < 12; ++c) {
+                        dst[2 * c] = xv[c].re;
+                        dst[2 * c + 1] = xv[c].im;
+                    }
+                }
+            SITE_LOOP_END
+            continue;
+        }
+        double acc[2 * MAXQ];
+#pragma unroll
+        for (int n = 0; n < 2 * MAXQ; ++n) acc[n] = 0.0;
+        const int32_t *col = P.col + (size_t)tk.cidx * NF;
+        SITE_LOOP(1)
+            for (int w = 0; w < 2; ++w) {
+                const int sw = 2 * idx + w;
+                if (P.n_lev) {                 // the coarsest ancestor class holds every finer one
+                    if (P.lev_cols[sw] != P.lev_anc[tk.colour]) continue;
+                } else if (col[sw] != tk.colour) {
+                    continue;
+                }
+                int xs[4], xy[4];
+                site_coords(P.g, sw, xs);
+                for (int n = 0; n < MAXQ; ++n) {
+                    if (n >= P.n_p) break;
+                    if (P.n_lev) {
+                        const int l = n / P.n_pr;
+                        if (l > 0 && P.lev_cols[(size_t)l * NF + sw] != P.lev_anc[(size_t)l * P.m_fin + tk.colour])
+                            continue;
+                    }
+                    const int y = shift_site(P.g, sw, xs, P.mu, P.p[n]);
+                    for (int nu = 0; nu < 4; ++nu) xy[nu] = xs[nu];
+                    const int cm = (xs[P.mu] + P.p[n]) % P.g.D[P.mu];
+                    xy[P.mu] = cm < 0 ? cm + P.g.D[P.mu] : cm;
+                    Cx<double> xv[12];
+                    weo_x_at(P, tk, key, x, t64, y, xy, xv);
+                    for (int a = 0; a < 12; ++a) {
+                        if (P.dilute && a != tk.comp) continue;
+                        const Cx<double> z = P.dilute ? pt_noise(key, (uint64_t)sw, P.noise)
+                                                      : pt_noise(key, (uint64_t)sw * 12 + a, P.noise);
+                        const Cx<double> q = cconjmul(z, xv[a]);
+                        acc[2 * n] += q.re;
+                        acc[2 * n + 1] += q.im;
+                    }
+                }
+            }
+        SITE_LOOP_END
+        item_store_contract<MAXQ>(P, j, b, acc, 2 * P.n_p, sh);
+    ITEM_LOOP_END
+}
+
 // ------------------------------------------------------------------ host driver
 struct EngineRun {
     EP P;
@@ -1551,13 +2040,14 @@ struct EngineRun {
     int g_contract, g_oupd, g_ores, g_apply1, g_apply2, g_upd, g_s, g_dir;
     int g_apply1_x2, g_apply2_x2, g_contract32;
     int g_hop, g_ohop;                 // even-odd: the odd-site hop of the inner and of the outer step
+    int g_obp;                         // even-odd Wilson: b'_e of new tasks
     double *part_con, *part_outer;   // partial-sum regions of the contraction and outer kernel groups
 };
 
 template <typename K>
-static int persistent_grid(K kernel, int num_sms) {
+static int persistent_grid(K kernel, int num_sms, int block = PT_BLOCK) {
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, PT_BLOCK, 0) != cudaSuccess || occ < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, 0) != cudaSuccess || occ < 1) {
         cudaGetLastError();
         occ = 1;
     }
@@ -1597,21 +2087,32 @@ static void enqueue_iteration(const EngineRun &E, cudaStream_t st, const cudaEve
         s_con = side[0];
         s_out = side[1];
     }
-    if (KIND == 0 && P.eo) {
-        if (P.n_p <= 16) k_eo_contract<16><<<E.g_contract, PT_BLOCK, 0, s_con>>>(Pc);
-        else k_eo_contract<PT_MAX_P><<<E.g_contract32, PT_BLOCK, 0, s_con>>>(Pc);
+    if (P.eo) {
+        if constexpr (KIND == 0) {
+            if (P.n_p <= 16) k_eo_contract<16><<<E.g_contract, P.bs, 0, s_con>>>(Pc);
+            else k_eo_contract<PT_MAX_P><<<E.g_contract32, P.bs, 0, s_con>>>(Pc);
+        } else {
+            if (P.n_p <= 16) k_weo_contract<16><<<E.g_contract, P.bs, 0, s_con>>>(Pc);
+            else k_weo_contract<PT_MAX_P><<<E.g_contract32, P.bs, 0, s_con>>>(Pc);
+        }
     } else {
-        if (P.n_p <= 16) k_contract<KIND, 16><<<E.g_contract, PT_BLOCK, 0, s_con>>>(Pc);
-        else k_contract<KIND, PT_MAX_P><<<E.g_contract32, PT_BLOCK, 0, s_con>>>(Pc);
+        if (P.n_p <= 16) k_contract<KIND, 16><<<E.g_contract, P.bs, 0, s_con>>>(Pc);
+        else k_contract<KIND, PT_MAX_P><<<E.g_contract32, P.bs, 0, s_con>>>(Pc);
     }
     k_fin_contract<<<W, 256, 0, s_con>>>(Pc);
     ev_rec(ev, 5, s_out);
-    k_outer_update<KIND, S><<<E.g_oupd, PT_BLOCK, 0, s_out>>>(Po);
-    if (KIND == 0 && P.eo) {
-        k_eo_outer_hop<<<E.g_ohop, PT_BLOCK, 0, s_out>>>(Po);
-        k_eo_outer_residual<S><<<E.g_ores, PT_BLOCK, 0, s_out>>>(Po);
+    k_outer_update<KIND, S><<<E.g_oupd, P.bs, 0, s_out>>>(Po);
+    if (P.eo) {
+        if constexpr (KIND == 0) {
+            k_eo_outer_hop<<<E.g_ohop, P.bs, 0, s_out>>>(Po);
+            k_eo_outer_residual<S><<<E.g_ores, P.bs, 0, s_out>>>(Po);
+        } else {
+            k_weo_outer_hop<<<E.g_ohop, P.bs, 0, s_out>>>(Po);
+            k_weo_outer_bprime<<<E.g_obp, P.bs, 0, s_out>>>(Po);
+            k_weo_outer_residual<S><<<E.g_ores, P.bs, 0, s_out>>>(Po);
+        }
     } else {
-        k_outer_residual<KIND, S><<<E.g_ores, PT_BLOCK, 0, s_out>>>(Po);
+        k_outer_residual<KIND, S><<<E.g_ores, P.bs, 0, s_out>>>(Po);
     }
     k_fin_outer<<<W, 256, 0, s_out>>>(Po);
     ev_rec(ev, 6, s_out);
@@ -1619,46 +2120,62 @@ static void enqueue_iteration(const EngineRun &E, cudaStream_t st, const cudaEve
         ev_rec(ev, 0, st);
         if (P.eo) {
             if (P.vec4) {
-                k_eo_hop_v4<S><<<E.g_hop, PT_BLOCK, 0, st>>>(P);
-                k_eo_apply_v4<S><<<E.g_apply1, PT_BLOCK, 0, st>>>(P);
+                k_eo_hop_v4<S><<<E.g_hop, P.bs, 0, st>>>(P);
+                k_eo_apply_v4<S><<<E.g_apply1, P.bs, 0, st>>>(P);
             } else {
-                k_eo_hop<S><<<E.g_hop, PT_BLOCK, 0, st>>>(P);
-                k_eo_apply<S><<<E.g_apply1, PT_BLOCK, 0, st>>>(P);
+                k_eo_hop<S><<<E.g_hop, P.bs, 0, st>>>(P);
+                k_eo_apply<S><<<E.g_apply1, P.bs, 0, st>>>(P);
             }
         } else if (P.vec4) {
-            k_cg_apply_v4<S><<<E.g_apply1, PT_BLOCK, 0, st>>>(P);
+            k_cg_apply_v4<S><<<E.g_apply1, P.bs, 0, st>>>(P);
         } else {
-            k_cg_apply<S><<<E.g_apply1, PT_BLOCK, 0, st>>>(P);
+            k_cg_apply<S><<<E.g_apply1, P.bs, 0, st>>>(P);
         }
         ev_rec(ev, 1, st);
         k_fin_cg_alpha<<<W, 256, 0, st>>>(P);
-        if (P.vec4) k_cg_update_v4<S><<<E.g_upd, PT_BLOCK, 0, st>>>(P);
-        else k_cg_update<S><<<E.g_upd, PT_BLOCK, 0, st>>>(P);
+        if (P.vec4) k_cg_update_v4<S><<<E.g_upd, P.bs, 0, st>>>(P);
+        else k_cg_update<S><<<E.g_upd, P.bs, 0, st>>>(P);
         k_fin_cg_beta<<<W, 256, 0, st>>>(P);
         ev_rec(ev, 2, st);
+    } else if (P.eo) {
+        ev_rec(ev, 0, st);
+        k_weo_hop<S, LS, 0><<<E.g_hop, P.bs, 0, st>>>(P);
+        k_weo_apply1<S, LS><<<E.g_apply1, P.bs, 0, st>>>(P);
+        ev_rec(ev, 1, st);
+        k_fin_bicg_alpha<<<W, 256, 0, st>>>(P);
+        k_bicg_s<S><<<E.g_s, P.bs, 0, st>>>(P);
+        ev_rec(ev, 2, st);
+        k_weo_hop<S, LS, 1><<<E.g_hop, P.bs, 0, st>>>(P);
+        k_weo_apply2<S, LS><<<E.g_apply2, P.bs, 0, st>>>(P);
+        ev_rec(ev, 3, st);
+        k_fin_bicg_omega<<<W, 256, 0, st>>>(P);
+        k_bicg_update<S><<<E.g_upd, P.bs, 0, st>>>(P);
+        k_fin_bicg_beta<<<W, 256, 0, st>>>(P);
+        k_bicg_dir<S><<<E.g_dir, P.bs, 0, st>>>(P);
+        ev_rec(ev, 4, st);
     } else {
         ev_rec(ev, 0, st);
         if constexpr (!std::is_same<S, double>::value) {
-            if (P.rhs_block == 2) k_bicg_apply1_x2<S, LS><<<E.g_apply1_x2, PT_BLOCK, 0, st>>>(P);
-            else k_bicg_apply1<S, LS><<<E.g_apply1, PT_BLOCK, 0, st>>>(P);
+            if (P.rhs_block == 2) k_bicg_apply1_x2<S, LS><<<E.g_apply1_x2, P.bs, 0, st>>>(P);
+            else k_bicg_apply1<S, LS><<<E.g_apply1, P.bs, 0, st>>>(P);
         } else {
-            k_bicg_apply1<S, LS><<<E.g_apply1, PT_BLOCK, 0, st>>>(P);
+            k_bicg_apply1<S, LS><<<E.g_apply1, P.bs, 0, st>>>(P);
         }
         ev_rec(ev, 1, st);
         k_fin_bicg_alpha<<<W, 256, 0, st>>>(P);
-        k_bicg_s<S><<<E.g_s, PT_BLOCK, 0, st>>>(P);
+        k_bicg_s<S><<<E.g_s, P.bs, 0, st>>>(P);
         ev_rec(ev, 2, st);
         if constexpr (!std::is_same<S, double>::value) {
-            if (P.rhs_block == 2) k_bicg_apply2_x2<S, LS><<<E.g_apply2_x2, PT_BLOCK, 0, st>>>(P);
-            else k_bicg_apply2<S, LS><<<E.g_apply2, PT_BLOCK, 0, st>>>(P);
+            if (P.rhs_block == 2) k_bicg_apply2_x2<S, LS><<<E.g_apply2_x2, P.bs, 0, st>>>(P);
+            else k_bicg_apply2<S, LS><<<E.g_apply2, P.bs, 0, st>>>(P);
         } else {
-            k_bicg_apply2<S, LS><<<E.g_apply2, PT_BLOCK, 0, st>>>(P);
+            k_bicg_apply2<S, LS><<<E.g_apply2, P.bs, 0, st>>>(P);
         }
         ev_rec(ev, 3, st);
         k_fin_bicg_omega<<<W, 256, 0, st>>>(P);
-        k_bicg_update<S><<<E.g_upd, PT_BLOCK, 0, st>>>(P);
+        k_bicg_update<S><<<E.g_upd, P.bs, 0, st>>>(P);
         k_fin_bicg_beta<<<W, 256, 0, st>>>(P);
-        k_bicg_dir<S><<<E.g_dir, PT_BLOCK, 0, st>>>(P);
+        k_bicg_dir<S><<<E.g_dir, P.bs, 0, st>>>(P);
         ev_rec(ev, 4, st);
     }
     if (side) {
@@ -1727,7 +2244,9 @@ static pt_ctx::Tune engine_tuning(const pt_ctx *c, const pt_op *op, int prec) {
     d.graph_iters = 8;
     d.rhs_block = 1;
     d.overlap = 0;
-    d.evenodd = (op->kind == 0 && pt_evenodd_ok(op->dims)) ? 1 : 0;
+    d.evenodd = pt_evenodd_ok(op->dims) ? 1 : 0;
+    d.cta_threads = 0;
+    d.sites_per_thread = 0;
     return d;
 }
 
@@ -1736,25 +2255,33 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     pt_ctx *c = op->ctx;
     const Geom g = op->g;
     const pt_ctx::Tune tn = engine_tuning(c, op, rq.prec);
-    // even-odd for the Laplacian (every side even) unless switched off; the
-    // gradient works on full-lattice solutions and keeps the full system
-    const bool eo = KIND == 0 && tn.evenodd && rq.mode != MODE_GRAD && pt_evenodd_ok(op->dims);
+    // even-odd (every side even) unless switched off; the gradient works on
+    // full-lattice solutions and keeps the full system
+    const bool eo = tn.evenodd && rq.mode != MODE_GRAD && pt_evenodd_ok(op->dims);
     const int nsite = eo ? g.N / 2 : g.N;
-    const int64_t L = eo ? (int64_t)nsite : pt_field_reals(op);
-    const int nvec = KIND ? 7 : (eo ? 6 : 5);
-    const size_t per_slot = (size_t)L * ((eo ? 2 : 1) * sizeof(double) + nvec * sizeof(S));
+    const int64_t L = eo ? (int64_t)nsite * (KIND ? 24 : 1) : pt_field_reals(op);
+    // inner vectors: CG e, r, p (two buffers), q (+ t on the odd sites); BiCGStab
+    // e, r, p, v, s, t, r0 (+ the odd-site hop buffer); FP64: x (+ t64, + b'_e)
+    const int nvec = KIND ? (eo ? 8 : 7) : (eo ? 6 : 5);
+    const int nf64 = eo ? 3 : 1;
+    const size_t per_slot = (size_t)L * (nf64 * sizeof(double) + nvec * sizeof(S));
     int R = rq.R_force > 0 ? rq.R_force : (int)std::min<size_t>((size_t)rq.n_tasks, c->mem_budget / per_slot);
     if (rq.R_force <= 0 && c->max_slots > 0) R = std::min(R, c->max_slots);
     if (R < 1) R = 1;
     if (rq.R_force <= 0) R = std::min(R, 4096);
-    const int nsb = (nsite + Tile<KIND>::SITES - 1) / Tile<KIND>::SITES;
+    // item geometry: CTA threads and sites per thread (the Laplacian's vector
+    // path needs a multiple of 4 sites per thread)
+    const int bs = tn.cta_threads ? tn.cta_threads : PT_BLOCK;
+    const int spt = KIND ? 1 : (tn.sites_per_thread ? tn.sites_per_thread : Tile<0>::SPT);
+    const int nsb = (int)(((int64_t)nsite + (int64_t)bs * spt - 1) / ((int64_t)bs * spt));
     const int K_MAX = 2 * PT_MAX_P;
     // layout of the work space
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
     size_t o_x64 = take((size_t)R * L * sizeof(double));
     size_t o_t64 = eo ? take((size_t)R * L * sizeof(double)) : 0;
-    size_t o_vec[7];
+    size_t o_b64 = eo ? take((size_t)R * L * sizeof(double)) : 0;
+    size_t o_vec[8];
     for (int v = 0; v < nvec; ++v) o_vec[v] = take((size_t)R * L * sizeof(S));
     size_t o_slots = take((size_t)R * sizeof(Slot));
     // partial sums per (slot, item): one region per kernel group (contraction, outer, inner), so that
@@ -1780,11 +2307,13 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     P.g = g;
     P.kind = KIND;
     P.nsb = nsb;
+    P.bs = bs;
+    P.spt = spt;
     P.R = R;
     P.eo = eo ? 1 : 0;
     P.nsite = nsite;
     P.gs = tn.group;
-    P.rhs_block = (KIND == 1 && !std::is_same<S, double>::value && tn.rhs_block == 2) ? 2 : 1;
+    P.rhs_block = (KIND == 1 && !eo && !std::is_same<S, double>::value && tn.rhs_block == 2) ? 2 : 1;
     P.overlap = tn.overlap ? 1 : 0;
     // four sites (even-odd: four half entries of one x row) per thread
     P.vec4 = (KIND == 0 && g.D[0] % (eo ? 8 : 4) == 0) ? 1 : 0;
@@ -1817,7 +2346,8 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     P.X_user = rq.X_user;
     P.x64 = (double *)(base + o_x64);
     P.t64 = eo ? (double *)(base + o_t64) : nullptr;
-    void **vp[7] = {&P.e, &P.r, &P.pv, &P.q, &P.s, &P.t, &P.r0};
+    P.b64 = eo ? (double *)(base + o_b64) : nullptr;
+    void **vp[8] = {&P.e, &P.r, &P.pv, &P.q, &P.s, &P.t, &P.r0, &P.p1};
     if constexpr (KIND == 0) vp[4] = &P.p1;     // CG: e, r, p (two buffers), q; even-odd adds t
     for (int v = 0; v < nvec; ++v) *vp[v] = base + o_vec[v];
     P.slots = (Slot *)(base + o_slots);
@@ -1851,48 +2381,61 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
 
     int occ = 0;
     if constexpr (KIND == 0) {
-        PT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_apply<S>, PT_BLOCK, 0));
+        PT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_apply<S>, bs, 0));
     } else {
-        PT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bicg_apply1<S, LS>, PT_BLOCK, 0));
+        PT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bicg_apply1<S, LS>, bs, 0));
     }
     occ = std::max(occ, 1);
     E.grid_items = c->num_sms * occ;
     const int ns = c->num_sms;
-    E.g_contract = persistent_grid(k_contract<KIND, 16>, ns);
-    E.g_contract32 = persistent_grid(k_contract<KIND, PT_MAX_P>, ns);
-    E.g_oupd = persistent_grid(k_outer_update<KIND, S>, ns);
-    E.g_ores = persistent_grid(k_outer_residual<KIND, S>, ns);
-    E.g_hop = E.g_ohop = 0;
+    E.g_contract = persistent_grid(k_contract<KIND, 16>, ns, bs);
+    E.g_contract32 = persistent_grid(k_contract<KIND, PT_MAX_P>, ns, bs);
+    E.g_oupd = persistent_grid(k_outer_update<KIND, S>, ns, bs);
+    E.g_ores = persistent_grid(k_outer_residual<KIND, S>, ns, bs);
+    E.g_hop = E.g_ohop = E.g_obp = 0;
     if constexpr (KIND == 0) {
         if (eo) {
-            E.g_contract = persistent_grid(k_eo_contract<16>, ns);
-            E.g_contract32 = persistent_grid(k_eo_contract<PT_MAX_P>, ns);
-            E.g_ores = persistent_grid(k_eo_outer_residual<S>, ns);
-            E.g_ohop = persistent_grid(k_eo_outer_hop, ns);
-            E.g_apply1 = E.g_apply2 = P.vec4 ? persistent_grid(k_eo_apply_v4<S>, ns)
-                                             : persistent_grid(k_eo_apply<S>, ns);
-            E.g_hop = P.vec4 ? persistent_grid(k_eo_hop_v4<S>, ns) : persistent_grid(k_eo_hop<S>, ns);
+            E.g_contract = persistent_grid(k_eo_contract<16>, ns, bs);
+            E.g_contract32 = persistent_grid(k_eo_contract<PT_MAX_P>, ns, bs);
+            E.g_ores = persistent_grid(k_eo_outer_residual<S>, ns, bs);
+            E.g_ohop = persistent_grid(k_eo_outer_hop, ns, bs);
+            E.g_apply1 = E.g_apply2 = P.vec4 ? persistent_grid(k_eo_apply_v4<S>, ns, bs)
+                                             : persistent_grid(k_eo_apply<S>, ns, bs);
+            E.g_hop = P.vec4 ? persistent_grid(k_eo_hop_v4<S>, ns, bs) : persistent_grid(k_eo_hop<S>, ns, bs);
         } else {
-            E.g_apply1 = E.g_apply2 = P.vec4 ? persistent_grid(k_cg_apply_v4<S>, ns)
-                                             : persistent_grid(k_cg_apply<S>, ns);
+            E.g_apply1 = E.g_apply2 = P.vec4 ? persistent_grid(k_cg_apply_v4<S>, ns, bs)
+                                             : persistent_grid(k_cg_apply<S>, ns, bs);
         }
-        E.g_upd = P.vec4 ? persistent_grid(k_cg_update_v4<S>, ns) : persistent_grid(k_cg_update<S>, ns);
+        E.g_upd = P.vec4 ? persistent_grid(k_cg_update_v4<S>, ns, bs) : persistent_grid(k_cg_update<S>, ns, bs);
         E.g_s = E.g_dir = E.g_upd;
+    } else if (eo) {
+        E.g_contract = persistent_grid(k_weo_contract<16>, ns, bs);
+        E.g_contract32 = persistent_grid(k_weo_contract<PT_MAX_P>, ns, bs);
+        E.g_ores = persistent_grid(k_weo_outer_residual<S>, ns, bs);
+        E.g_ohop = persistent_grid(k_weo_outer_hop, ns, bs);
+        E.g_obp = persistent_grid(k_weo_outer_bprime, ns, bs);
+        E.g_hop = persistent_grid(k_weo_hop<S, LS, 0>, ns, bs);
+        E.g_apply1 = persistent_grid(k_weo_apply1<S, LS>, ns, bs);
+        E.g_apply2 = persistent_grid(k_weo_apply2<S, LS>, ns, bs);
+        E.g_apply1_x2 = E.g_apply2_x2 = 0;
+        E.g_upd = persistent_grid(k_bicg_update<S>, ns, bs);
+        E.g_s = persistent_grid(k_bicg_s<S>, ns, bs);
+        E.g_dir = persistent_grid(k_bicg_dir<S>, ns, bs);
     } else {
-        E.g_apply1 = persistent_grid(k_bicg_apply1<S, LS>, ns);
-        E.g_apply2 = persistent_grid(k_bicg_apply2<S, LS>, ns);
+        E.g_apply1 = persistent_grid(k_bicg_apply1<S, LS>, ns, bs);
+        E.g_apply2 = persistent_grid(k_bicg_apply2<S, LS>, ns, bs);
         if constexpr (!std::is_same<S, double>::value) {
-            E.g_apply1_x2 = persistent_grid(k_bicg_apply1_x2<S, LS>, ns);
-            E.g_apply2_x2 = persistent_grid(k_bicg_apply2_x2<S, LS>, ns);
+            E.g_apply1_x2 = persistent_grid(k_bicg_apply1_x2<S, LS>, ns, bs);
+            E.g_apply2_x2 = persistent_grid(k_bicg_apply2_x2<S, LS>, ns, bs);
         } else {
             E.g_apply1_x2 = E.g_apply2_x2 = 0;
         }
-        E.g_upd = persistent_grid(k_bicg_update<S>, ns);
-        E.g_s = persistent_grid(k_bicg_s<S>, ns);
-        E.g_dir = persistent_grid(k_bicg_dir<S>, ns);
+        E.g_upd = persistent_grid(k_bicg_update<S>, ns, bs);
+        E.g_s = persistent_grid(k_bicg_s<S>, ns, bs);
+        E.g_dir = persistent_grid(k_bicg_dir<S>, ns, bs);
     }
     E.grid_warps = std::max(1, std::min((R + 7) / 8, c->num_sms * 4));
-    E.kernels_per_iter = KIND ? 14 : (eo ? 12 : 10);
+    E.kernels_per_iter = KIND ? (eo ? 18 : 14) : (eo ? 12 : 10);
 
     // capture ITERS engine iterations into one graph
     const int ITERS = tn.graph_iters;
@@ -2447,10 +2990,11 @@ extern "C" int pt_grad(pt_ctx *c, const pt_op *op, const int32_t *col_dev, int n
 
 // ------------------------------------------------------------------ autotuner
 // Coordinate descent over the engine's free parameters on a trial subset of
-// the probes: even-odd or full system (Laplacian with even sides), the inner
-// relative tolerance delta (mixed precision only), the right-hand sides per
-// item and the slot group of the item order (Wilson only) and the engine
-// iterations per CUDA graph.  Each candidate solves the same trial right-hand sides; the
+// the probes: even-odd or full system (every side even), the inner relative
+// tolerance delta (mixed precision only), the right-hand sides per item and
+// the slot group of the item order (Wilson only), the item shape (CTA threads;
+// sites per thread for the Laplacian) and the engine iterations per CUDA
+// graph.  Each candidate solves the same trial right-hand sides; the
 // fastest (device time, synchronised) wins and is stored for the operator's
 // (kind, precision, lattice).
 static int store_tuning(pt_ctx *c, const pt_op *op, int prec, const pt_tune *t) {
@@ -2473,6 +3017,8 @@ static int store_tuning(pt_ctx *c, const pt_op *op, int prec, const pt_tune *t) 
     e.rhs_block = t->rhs_block == 2 ? 2 : 1;
     e.overlap = t->overlap ? 1 : 0;
     e.evenodd = t->evenodd ? 1 : 0;
+    e.cta_threads = t->cta_threads;
+    e.sites_per_thread = t->sites_per_thread;
     return PT_OK;
 }
 
@@ -2487,6 +3033,11 @@ extern "C" int pt_set_tuning(pt_ctx *c, const pt_op *op, int prec, const pt_tune
         PT_CHECK_ARG(t->rhs_block >= 0 && t->rhs_block <= 2, "pt_set_tuning: rhs_block must be 0, 1 or 2");
         PT_CHECK_ARG(t->overlap == 0 || t->overlap == 1, "pt_set_tuning: overlap must be 0 or 1");
         PT_CHECK_ARG(t->evenodd == 0 || t->evenodd == 1, "pt_set_tuning: evenodd must be 0 or 1");
+        PT_CHECK_ARG(t->cta_threads == 0 || t->cta_threads == 64 || t->cta_threads == 128 || t->cta_threads == 256,
+                     "pt_set_tuning: cta_threads must be 0 (default), 64, 128 or 256");
+        PT_CHECK_ARG(t->sites_per_thread == 0 || t->sites_per_thread == 4 || t->sites_per_thread == 8 ||
+                         t->sites_per_thread == 16,
+                     "pt_set_tuning: sites_per_thread must be 0 (default), 4, 8 or 16");
     }
     return store_tuning(c, op, prec, t);
 }
@@ -2500,6 +3051,8 @@ extern "C" int pt_get_tuning(pt_ctx *c, const pt_op *op, int prec, pt_tune *t) {
     t->rhs_block = e.rhs_block;
     t->overlap = e.overlap;
     t->evenodd = e.evenodd;
+    t->cta_threads = e.cta_threads ? e.cta_threads : PT_BLOCK;
+    t->sites_per_thread = op->kind ? 1 : (e.sites_per_thread ? e.sites_per_thread : Tile<0>::SPT);
     t->seconds_per_rhs = 0.0;
     return PT_OK;
 }
@@ -2564,20 +3117,27 @@ extern "C" int pt_autotune(pt_ctx *c, const pt_op *op, const int32_t *col_dev, i
     std::vector<int> blocks;
     if (op->kind == 1 && prec != PT_PREC_FP64) blocks = {1, 2};
     std::vector<int> evenodds;
-    if (op->kind == 0 && pt_evenodd_ok(op->dims)) evenodds = {0, 1};
+    if (pt_evenodd_ok(op->dims)) evenodds = {0, 1};
+    // item shape: CTA threads, and (Laplacian) sites per thread
+    const std::vector<int> ctas = {64, 128, 256};
+    std::vector<int> spts;
+    if (op->kind == 0) spts = {4, 8, 16};
     // serial versus branched iterations (overlap) is left out: within 1 % either way, and the
     // branches blur the per-kernel event timing
     const std::vector<int> overlaps = {};
-    for (int pass = 0; pass < 6 && !rc; ++pass) {
+    for (int pass = 0; pass < 8 && !rc; ++pass) {
         const size_t nc = pass == 0 ? evenodds.size() : pass == 1 ? deltas.size() : pass == 2 ? blocks.size()
-                          : pass == 3 ? groups.size() : pass == 4 ? iters.size() : overlaps.size();
+                          : pass == 3 ? groups.size() : pass == 4 ? ctas.size() : pass == 5 ? spts.size()
+                          : pass == 6 ? iters.size() : overlaps.size();
         for (size_t i = 0; i < nc && !rc; ++i) {
             pt_ctx::Tune cand = cur;
             if (pass == 0) cand.evenodd = evenodds[i];
             else if (pass == 1) cand.delta = deltas[i];
             else if (pass == 2) cand.rhs_block = blocks[i];
             else if (pass == 3) cand.group = groups[i];
-            else if (pass == 4) cand.graph_iters = iters[i];
+            else if (pass == 4) cand.cta_threads = ctas[i] == PT_BLOCK && !cur.cta_threads ? 0 : ctas[i];
+            else if (pass == 5) cand.sites_per_thread = spts[i] == Tile<0>::SPT && !cur.sites_per_thread ? 0 : spts[i];
+            else if (pass == 6) cand.graph_iters = iters[i];
             else cand.overlap = overlaps[i];
             if (!memcmp(&cand, &cur, sizeof(cand))) continue;
             double t = 0.0;
@@ -2595,6 +3155,8 @@ extern "C" int pt_autotune(pt_ctx *c, const pt_op *op, const int32_t *col_dev, i
     best->rhs_block = cur.rhs_block;
     best->overlap = cur.overlap;
     best->evenodd = cur.evenodd;
+    best->cta_threads = cur.cta_threads ? cur.cta_threads : PT_BLOCK;
+    best->sites_per_thread = op->kind ? 1 : (cur.sites_per_thread ? cur.sites_per_thread : Tile<0>::SPT);
     best->seconds_per_rhs = t_best / trial.size();
     return store_tuning(c, op, prec, best);
 }

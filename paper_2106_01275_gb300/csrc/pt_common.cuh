@@ -489,7 +489,7 @@ struct pt_ctx {
     struct Tune {
         int used, kind, prec, dims[4];
         double delta;
-        int group, graph_iters, rhs_block, overlap, evenodd;
+        int group, graph_iters, rhs_block, overlap, evenodd, cta_threads, sites_per_thread;
     } tune[16], trial;
     int in_trial;
     // grow-only work space
@@ -503,6 +503,7 @@ struct pt_ctx {
 
 struct pt_op {
     pt_ctx *ctx;
+    int device;              // the context's device, kept so that pt_op_destroy never reads the context
     int kind;                // 0 Laplacian, 1 Wilson
     int dims[4];
     Geom g;

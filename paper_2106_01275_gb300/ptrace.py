@@ -49,11 +49,13 @@ class Stats(ctypes.Structure):
 class Tune(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("group", ctypes.c_int32), ("graph_iters", ctypes.c_int32),
                 ("rhs_block", ctypes.c_int32), ("overlap", ctypes.c_int32), ("evenodd", ctypes.c_int32),
+                ("cta_threads", ctypes.c_int32), ("sites_per_thread", ctypes.c_int32),
                 ("seconds_per_rhs", ctypes.c_double)]
 
     def as_dict(self):
         return {"delta": self.delta, "group": self.group, "graph_iters": self.graph_iters,
                 "rhs_block": self.rhs_block, "overlap": self.overlap, "evenodd": self.evenodd,
+                "cta_threads": self.cta_threads, "sites_per_thread": self.sites_per_thread,
                 "seconds_per_rhs": self.seconds_per_rhs}
 
 
@@ -225,6 +227,11 @@ class Context:
 
     def close(self):
         if self._h:
+            # operators first: one finalised from a reference cycle after its
+            # context must find nothing left to free
+            for o in list(_LIVE.values()):
+                if isinstance(o, Operator) and o.ctx is self:
+                    o.close()
             lib().pt_destroy(self._h)
             self._h = ctypes.c_void_p()
 
@@ -462,16 +469,19 @@ def autotune(op, col, n_colours, mu, noise="z2", seed=0, prec="mixed_fp32", tol=
 
 
 def set_tuning(op, prec, delta=None, group=None, graph_iters=None, rhs_block=None, overlap=None, evenodd=None,
-               reset=False):
+               cta_threads=None, sites_per_thread=None, reset=False):
     if reset:
         _check(lib().pt_set_tuning(op.ctx.handle, op._h, PREC[prec], None))
         return
     cur = get_tuning(op, prec)
+    spt = cur["sites_per_thread"] if sites_per_thread is None else int(sites_per_thread)
     t = Tune(cur["delta"] if delta is None else float(delta), cur["group"] if group is None else int(group),
              cur["graph_iters"] if graph_iters is None else int(graph_iters),
              cur["rhs_block"] if rhs_block is None else int(rhs_block),
              cur["overlap"] if overlap is None else int(overlap),
-             cur["evenodd"] if evenodd is None else int(evenodd), 0.0)
+             cur["evenodd"] if evenodd is None else int(evenodd),
+             cur["cta_threads"] if cta_threads is None else int(cta_threads),
+             0 if op.dof == 12 else spt, 0.0)
     _check(lib().pt_set_tuning(op.ctx.handle, op._h, PREC[prec], ctypes.byref(t)))
 
 

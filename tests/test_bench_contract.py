@@ -209,16 +209,33 @@ def test_multigrid_leg_json_line(monkeypatch, capsys):
                                         seed, tol, maxit, csw=csw)
         return torch.as_tensor(x), its, rel
 
+    def eo_clover_blocks(op, csw):
+        from oracle import evenodd as EO
+        C = pt.clover_blocks_host(op.dims, op.U, op.kappa, csw)
+        ev, od = EO.split(op.dims)
+        return np.eye(12)[None] + C[ev], pt.site_blocks_invert_host(C[od], 1.0)
+
+    def eo_solve(op, b, tol, maxit, blocks=None):
+        x, its, rel = pt.eo_solve_host(1, op.dims, b.numpy(), tol=tol, maxit=maxit, kappa=op.kappa, U=op.U,
+                                       blocks=blocks)
+        return torch.as_tensor(x), its, rel
+
     monkeypatch.setattr(pt, "solve", solve)
     monkeypatch.setattr(pt, "mg_solve", mg_solve)
     monkeypatch.setattr(pt, "wmg_solve", wmg_solve)
+    monkeypatch.setattr(pt, "eo_clover_blocks", eo_clover_blocks)
+    monkeypatch.setattr(pt, "eo_solve", eo_solve)
     monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "multigrid", "--case", "small"])
     bench.main()
     lines = [l for l in capsys.readouterr().out.strip().splitlines() if l.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["config"]["workload"].startswith("multigrid:") and len(d["cases"]) == 3 and d["value"] > 1.0
+    assert d["warmup"] == 1
     for c in d["cases"]:
-        assert c["relres_multigrid"] <= 1e-10, c
-        if c["iters_plain"] is not None:
-            assert c["iters_multigrid"] < c["iters_plain"] and c["max_rel_diff"] < 1e-7, c
+        assert c["relres_multigrid"] <= 1e-10 and c["max_rel_diff"] < 1e-7, c
+        assert c["seconds_multigrid_setup"] >= 0.0 and c["seconds_multigrid_solve"] >= 0.0, c
+        if c["operator"] == "clover":
+            assert c["iters_plain"] is None and c["iters_evenodd_bicgstab"] > 0, c
+        else:
+            assert c["iters_multigrid"] < c["iters_plain"], c

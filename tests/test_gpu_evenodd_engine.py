@@ -138,3 +138,93 @@ def test_autotuner_chooses_between_full_and_evenodd(pt, ctx):
     pt.set_tuning(op, "mixed_fp32", reset=True)
     odd = pt.laplacian(ctx, [5, 4, 4, 4], m2)
     assert pt.get_tuning(odd, "mixed_fp32")["evenodd"] == 0          # an odd side: full system
+
+
+# ------------------------------------------------------------------ Wilson
+@pytest.mark.parametrize("dims,antip", [([4, 4, 4, 8], True), ([2, 4, 6, 4], False), ([6, 2, 2, 4], True)])
+def test_wilson_trace_matches_oracle_and_full_system(pt, ctx, dims, antip):
+    """Wilson-Dirac even-odd BiCGStab (S = 1 - kappa^2 D_eo D_oe) against the
+    oracle and against the same engine on the full system, Z4 noise with
+    12-fold dilution, in every precision."""
+    from paper_2106_01275_gb300 import inputs
+    kappa, mu = 0.12, 2
+    U = inputs.gauge_links(dims, 1234)
+    col, m = greedy_colour(dims, mu, [1], 1, 0)
+    op = pt.wilson(ctx, dims, _t(U), kappa, antip)
+    want = OE.probed_estimates(OE.Wilson(dims, U, kappa, antip), col, m, 1000, 2, 1, mu, [0, 1, 2], 1e-12)
+    for prec in PRECS:
+        assert pt.get_tuning(op, prec)["evenodd"] == 1
+        est, _, _, st = pt.trace(op, _t(col), m, mu, [0, 1, 2], "z4", 1000, 0, 2, True, prec, 1e-10, 5000)
+        assert np.allclose(est, want, rtol=1e-8, atol=1e-7), prec
+        assert st["max_relres"] <= 1e-10 and st["n_noconv"] == 0
+        pt.set_tuning(op, prec, evenodd=0)
+        full, _, _, st_f = pt.trace(op, _t(col), m, mu, [0, 1, 2], "z4", 1000, 0, 2, True, prec, 1e-10, 5000)
+        pt.set_tuning(op, prec, reset=True)
+        assert np.allclose(est, full, rtol=1e-8, atol=1e-7), prec
+        assert st["inner_iters"] < st_f["inner_iters"], (prec, st["inner_iters"], st_f["inner_iters"])
+
+
+def test_wilson_undiluted_many_displacements_and_solve(pt, ctx):
+    """Undiluted Z4 probes, 20 displacements (the 32-output contraction), and
+    pt_solve's copy-out of the rebuilt odd half checked through the oracle's
+    operator."""
+    import torch
+    from paper_2106_01275_gb300 import inputs
+    dims, kappa, mu = [4, 2, 4, 4], 0.11, 2
+    U = inputs.gauge_links(dims, 3)
+    col, m = greedy_colour(dims, mu, [1], 1, 1)
+    op = pt.wilson(ctx, dims, _t(U), kappa, True)
+    ps = list(range(-10, 10))
+    est, _, _, _ = pt.trace(op, _t(col), m, mu, ps, "z4", 5, 0, 2, False, "mixed_fp32", 1e-10, 5000)
+    want = OE.probed_estimates(OE.Wilson(dims, U, kappa), col, m, 5, 2, 1, mu, ps, 1e-12, dilute=False)
+    assert np.allclose(est, want, rtol=1e-8, atol=1e-7)
+    N = int(np.prod(dims))
+    B = np.random.default_rng(4).standard_normal((3, N, 4, 3, 2))
+    for prec in PRECS:
+        X, _, relres, _ = pt.solve(op, _t(B), prec, 1e-10, 5000)
+        Xc = X.cpu().numpy()
+        for j in range(3):
+            b = B[j][..., 0] + 1j * B[j][..., 1]
+            x = Xc[j][..., 0] + 1j * Xc[j][..., 1]
+            r = b - OO.wilson_apply(x, U, kappa, dims, True)
+            assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(b), prec
+            assert relres[j] <= 1e-10
+    Z, it0, _, _ = pt.solve(op, _t(np.zeros((1, N, 4, 3, 2))), "mixed_fp32", 1e-10, 100)
+    assert torch.count_nonzero(Z).item() == 0 and it0[0] == 0
+
+
+# ------------------------------------------------------------------ work-item shape
+@pytest.mark.parametrize("cta,spt", [(64, 4), (128, 16), (256, 4), (64, 16)])
+def test_item_shapes_laplacian(pt, ctx, cta, spt):
+    """Every work-item shape the autotuner may pick (CTA threads x sites per
+    thread) covers every site exactly once: traces against the oracle on a
+    four-entry lattice and a one-entry one, even-odd and full system."""
+    for dims in ([8, 8, 4, 6], [6, 4, 2, 4]):
+        mu, m2 = 2, 0.2
+        col, m = greedy_colour(dims, mu, [1], 1, 0)
+        op = pt.laplacian(ctx, dims, m2)
+        want = OE.probed_estimates(OE.Laplacian(dims, m2), col, m, 4, 2, 0, mu, [0, 1], 1e-13)
+        for eo in (1, 0):
+            pt.set_tuning(op, "mixed_fp32", evenodd=eo, cta_threads=cta, sites_per_thread=spt)
+            t = pt.get_tuning(op, "mixed_fp32")
+            assert (t["cta_threads"], t["sites_per_thread"]) == (cta, spt)
+            est, _, _, st = pt.trace(op, _t(col), m, mu, [0, 1], "z2", 4, 0, 2, True, "mixed_fp32", 1e-10, 5000)
+            assert np.allclose(est, want, rtol=1e-8, atol=1e-9 * np.abs(want).max()), (dims, eo)
+        pt.set_tuning(op, "mixed_fp32", reset=True)
+
+
+@pytest.mark.parametrize("cta", [64, 128])
+def test_item_shapes_wilson(pt, ctx, cta):
+    from paper_2106_01275_gb300 import inputs
+    dims, kappa, mu = [4, 4, 2, 6], 0.12, 2
+    U = inputs.gauge_links(dims, 55)
+    col, m = greedy_colour(dims, mu, [1], 1, 0)
+    op = pt.wilson(ctx, dims, _t(U), kappa, True)
+    want = OE.probed_estimates(OE.Wilson(dims, U, kappa), col, m, 8, 1, 1, mu, [0, 1], 1e-12)
+    for eo in (1, 0):
+        pt.set_tuning(op, "mixed_fp32", evenodd=eo, cta_threads=cta)
+        est, _, _, _ = pt.trace(op, _t(col), m, mu, [0, 1], "z4", 8, 0, 1, True, "mixed_fp32", 1e-10, 5000)
+        assert np.allclose(est, want, rtol=1e-8, atol=1e-7), eo
+    pt.set_tuning(op, "mixed_fp32", reset=True)
+    with pytest.raises(pt.PtraceError):
+        pt.set_tuning(op, "mixed_fp32", cta_threads=512)

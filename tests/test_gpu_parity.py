@@ -398,9 +398,11 @@ def test_autotune_then_parity(pt, ctx):
     bw = pt.autotune(opw, _t(colw), mw, mu, "z4", 5, "mixed_fp32", 1e-10, 5000, 12)
     assert bw["group"] in (1, 2, 4, 8, 16)
     assert bw["rhs_block"] in (1, 2) and bw["overlap"] == 0
-    pt.set_tuning(opw, "mixed_fp32", delta=1e-3, group=2, graph_iters=4, rhs_block=1, overlap=0)
+    pt.set_tuning(opw, "mixed_fp32", delta=1e-3, group=2, graph_iters=4, rhs_block=1, overlap=0, evenodd=1,
+                  cta_threads=256)
     assert pt.get_tuning(opw, "mixed_fp32") == {"delta": 1e-3, "group": 2, "graph_iters": 4, "rhs_block": 1,
-                                                "overlap": 0, "evenodd": 0, "seconds_per_rhs": 0.0}
+                                                "overlap": 0, "evenodd": 1, "cta_threads": 256,
+                                                "sites_per_thread": 1, "seconds_per_rhs": 0.0}
     est, _, _, _ = pt.trace(opw, _t(colw), mw, mu, [1], "z4", 5, 0, 1, True, "mixed_fp32", 1e-10, 5000)
     want = OE.probed_estimates(OE.Wilson(dims, U, kappa), colw, mw, 5, 1, 1, mu, [1], 1e-12)
     assert np.allclose(est, want, rtol=1e-8, atol=1e-7)
