@@ -218,6 +218,11 @@ def run_ours(args):
     big = int(np.argmax(m))
     tuning = pt.autotune(op, cols[big].contiguous(), m[big], W.mu, W.noise, SEED + 7, args.prec, TOL, MAXIT,
                          64 if W.kind == "lap" else 24) if not args.no_tune else pt.get_tuning(op, args.prec)
+    if args.tuning:                  # explicit engine parameters on top of the tuned ones
+        fixed = {k: (float(v) if k == "delta" else int(v))
+                 for k, v in (kv.split("=") for kv in args.tuning.split(","))}
+        pt.set_tuning(op, args.prec, **fixed)
+        tuning = pt.get_tuning(op, args.prec)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -938,6 +943,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--skip-baselines", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="use the engine's default parameters")
+    ap.add_argument("--tuning", default="", help="engine parameters fixed after tuning, e.g. rhs_block=8,cta_threads=256")
     ap.add_argument("--prec", default="mixed_fp32", choices=["mixed_fp32", "mixed_bf16"],
                     help="inner Krylov storage: FP32, or BF16 (FP32 arithmetic); FP64 outer either way")
     ap.add_argument("--case", default="full", choices=["full", "small"],

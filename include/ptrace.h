@@ -127,9 +127,13 @@ PT_API int pt_set_launch_limit(pt_ctx *ctx, int64_t n);
  *                by site block, so that they share the links through L2
  *   graph_iters  engine iterations captured in one CUDA graph (host polls
  *                the completion flag once per graph launch)
- *   rhs_block    right-hand sides per work item of the Wilson applies in
- *                the mixed-precision inner solve: 1, or 2 (each link load
- *                then serves two right-hand sides); 0 means 1
+ *   rhs_block    right-hand sides per work item of the Wilson applies: 1;
+ *                2 on the full system in mixed precision (each link load
+ *                serves two right-hand sides); 8 in even-odd mode with
+ *                256-thread CTAs (a work item covers 256 sites for eight
+ *                slots, one warp each, and stages the links of every 32 sites
+ *                once in shared memory for all eight); other combinations
+ *                fall back to 1; 0 means 1
  *   overlap      1: within an engine iteration the contraction and the FP64
  *                outer steps run as CUDA-graph branches beside the inner
  *                Krylov kernels (they work on disjoint right-hand sides);

@@ -167,6 +167,16 @@ __device__ __forceinline__ Cx<double> source_val(const EP &P, const Task &tk, ui
     return Cx<double>{sg * z.re, sg * z.im};
 }
 
+// site index and coordinate along mu of x + p e_mu for 0 <= p < D_mu (the
+// engine reduces its displacements once on the host): an add and a
+// conditional subtract instead of a modulo
+__device__ __forceinline__ int shift_fwd(const Geom &g, int idx, const int x[4], int mu, int p, int *c_out) {
+    int c = x[mu] + p;
+    if (c >= g.D[mu]) c -= g.D[mu];
+    *c_out = c;
+    return idx + (c - x[mu]) * g.stride[mu];
+}
+
 // ------------------------------------------------------------------ work items and reductions
 // An item is one slot's block of bs x spt consecutive sites, processed by one
 // CTA of bs threads (spt sites per thread; by default PT_BLOCK threads and
@@ -441,7 +451,8 @@ __global__ void __launch_bounds__(PT_BLOCK) k_contract(EP P) {
                         if (l > 0 && P.lev_cols[(size_t)l * N + idx] != P.lev_anc[(size_t)l * P.m_fin + tk.colour])
                             continue;
                     }
-                    int y = shift_site(P.g, idx, xc, P.mu, P.p[n]);
+                    int cm;
+                    const int y = shift_fwd(P.g, idx, xc, P.mu, P.p[n], &cm);
                     Cx<double> q = cconjmul(z, Fld<KIND, double>::ld(x, N, a, y));
                     acc[2 * n] += q.re;
                     acc[2 * n + 1] += q.im;
@@ -1067,7 +1078,9 @@ __global__ void __launch_bounds__(PT_BLOCK) k_eo_apply_v4(EP P) {
     ITEM_LOOP_END
 }
 
-// outer step, part 1: t64 = H_oe x64 at the odd entries (FP64)
+// outer step, part 1: t64 = H_oe x64 at the odd entries (FP64); a new task
+// starts from x = 0, so its t64 is zero (written, not hopped: the
+// contraction reads it if the task converges at once)
 __global__ void __launch_bounds__(PT_BLOCK) k_eo_outer_hop(EP P) {
     const int N = P.nsite;
     ITEM_LOOP(LIST_OUTER)
@@ -1075,6 +1088,12 @@ __global__ void __launch_bounds__(PT_BLOCK) k_eo_outer_hop(EP P) {
         if (ph != PH_START && ph != PH_OUTER) continue;
         const double *x = P.x64 + (size_t)j * P.L;
         double *t = P.t64 + (size_t)j * P.L;
+        if (ph == PH_START) {
+            SITE_LOOP(0)
+                t[idx] = 0.0;
+            SITE_LOOP_END
+            continue;
+        }
         SITE_LOOP(0)
             int xc[4];
             const int s = half_site(P.g, 1, idx, xc);
@@ -1168,10 +1187,10 @@ __global__ void __launch_bounds__(PT_BLOCK) k_eo_outer_residual(EP P) {
 // x_o = (b_o + H_oe x_e) / d from the source and t64 = H_oe x_e, which the
 // outer step formed for the final x_e (the slot converged right after it)
 __device__ __forceinline__ double eo_x_at(const EP &P, const Task &tk, uint64_t key, const double *x,
-                                          const double *t64, int y, const int xy[4]) {
+                                          const double *t64, double inv_d, int y, const int xy[4]) {
     if (((xy[0] + xy[1] + xy[2] + xy[3]) & 1) == 0) return x[y >> 1];
     const double b_o = source_val<0>(P, tk, key, y, xy, 0).re;
-    return (b_o + t64[y >> 1]) / P.diag;
+    return (b_o + t64[y >> 1]) * inv_d;
 }
 
 // the contraction (trace mode) or the copy-out (solve mode) of k_contract for
@@ -1180,6 +1199,7 @@ template <int MAXQ>
 __global__ void __launch_bounds__(PT_BLOCK) k_eo_contract(EP P) {
     __shared__ double sh[32 * 2 * PT_MAX_P];
     const int N = P.nsite, NF = P.g.N;
+    const double inv_d = 1.0 / P.diag;
     ITEM_LOOP(LIST_CONTRACT)
         const Slot &st = P.slots[j];
         if (st.phase != PH_CONTRACT) continue;
@@ -1193,7 +1213,7 @@ __global__ void __launch_bounds__(PT_BLOCK) k_eo_contract(EP P) {
                     const int sw = 2 * idx + w;
                     int xs[4];
                     site_coords(P.g, sw, xs);
-                    P.X_user[(size_t)tk.set * NF + sw] = eo_x_at(P, tk, key, x, t64, sw, xs);
+                    P.X_user[(size_t)tk.set * NF + sw] = eo_x_at(P, tk, key, x, t64, inv_d, sw, xs);
                 }
             SITE_LOOP_END
             continue;
@@ -1221,12 +1241,12 @@ __global__ void __launch_bounds__(PT_BLOCK) k_eo_contract(EP P) {
                         if (l > 0 && P.lev_cols[(size_t)l * NF + sw] != P.lev_anc[(size_t)l * P.m_fin + tk.colour])
                             continue;
                     }
-                    const int y = shift_site(P.g, sw, xs, P.mu, P.p[n]);
+                    int cm;
+                    const int y = shift_fwd(P.g, sw, xs, P.mu, P.p[n], &cm);
 #pragma unroll
                     for (int nu = 0; nu < 4; ++nu) xy[nu] = xs[nu];
-                    int cm = (xs[P.mu] + P.p[n]) % P.g.D[P.mu];
-                    xy[P.mu] = cm < 0 ? cm + P.g.D[P.mu] : cm;
-                    const double xv = eo_x_at(P, tk, key, x, t64, y, xy);
+                    xy[P.mu] = cm;
+                    const double xv = eo_x_at(P, tk, key, x, t64, inv_d, y, xy);
                     acc[2 * n] += z.re * xv;                // conj(z) x
                     acc[2 * n + 1] -= z.im * xv;
                 }
@@ -1579,6 +1599,34 @@ __global__ void __launch_bounds__(PT_BLOCK) k_bicg_dir(EP P) {
     ITEM_LOOP_END
 }
 
+// ------------------------------------------------------------------ even-odd link order
+// A packed link array is chunk-major: chunk c of site s at c * N + s (FP32:
+// five 16-byte chunks per direction; FP64 and BF16: one complex entry per
+// chunk, nine per direction).
+template <typename LS> struct LinkLayout;
+template <> struct LinkLayout<float> { typedef float4 E; static constexpr int CHUNKS = 20; };
+template <> struct LinkLayout<double> { typedef double2 E; static constexpr int CHUNKS = 36; };
+template <> struct LinkLayout<__nv_bfloat16> { typedef uint32_t E; static constexpr int CHUNKS = 36; };
+
+// the even-odd ordered copy: chunk c of site s (parity par) moves to
+// c * N + par * N/2 + s/2; nothing else changes, so a kernel reading the
+// copy at that position gets the same link bits
+template <typename E>
+__global__ void k_links_eo(Geom g, int n_chunk, const E *__restrict__ src, E *__restrict__ dst) {
+    const int N = g.N;
+    const int64_t total = (int64_t)n_chunk * N;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = t / N;
+        const int s = (int)(t - c * N);
+        int r = s, par = 0;
+        for (int d = 0; d < 4; ++d) {
+            par += r % g.D[d];
+            r /= g.D[d];
+        }
+        dst[c * N + (par & 1) * (N >> 1) + (s >> 1)] = src[t];
+    }
+}
+
 // ------------------------------------------------------------------ even-odd BiCGStab (Wilson)
 // With every side even, A = 1 - kappa D has D_ee = D_oo = 0, and A x = b is
 // solved through the Schur complement on the even sites:
@@ -1635,10 +1683,22 @@ __device__ __forceinline__ void wilson_hop_dir(const Geom &g, const LS *U, int a
     }
 }
 
+// position of the links of site s (parity par) in the even-odd ordered link
+// copy of the inner solver: entry par * N/2 + s/2, its half-field entry, so
+// that a warp of consecutive half entries reads consecutive links (in the
+// full-lattice order the sites of one parity are two apart)
+__device__ __forceinline__ int eo_link_pos(int N, int s, int par) { return par * (N >> 1) + (s >> 1); }
+template <int LPAR>
+__device__ __forceinline__ int link_pos(int N, int s, int par) {
+    if constexpr (LPAR < 0) return s;
+    else return eo_link_pos(N, s, par);
+}
+
 // (H psi)(x) at site idx (coordinates x) as in wilson_hop_site, with the
 // neighbour spinors supplied by fetch(y, mu, dir, ps) (dir +1 forward, -1
-// backward) and the links from the packed full-lattice arrays
-template <typename R, typename LS, typename Fetch>
+// backward) and the links from a packed array in the full-lattice order
+// (LPAR = -1) or in the even-odd order with idx of parity LPAR
+template <typename R, typename LS, int LPAR = -1, typename Fetch>
 __device__ __forceinline__ void wilson_hop_fetch(const Geom &g, Fetch fetch, const LS *U, int antip, int idx,
                                                  const int x[4], Cx<R> acc[4][3]) {
 #pragma unroll
@@ -1654,7 +1714,7 @@ __device__ __forceinline__ void wilson_hop_fetch(const Geom &g, Fetch fetch, con
             Cx<R> ps[4][3], h[2][3], uh[2][3], u[3][3];
             fetch(y, mu, 1, ps);
             spin_project<R>(mu, R(-1), ps, h);
-            load_link<R, LS>(U, N, mu, idx, u);
+            load_link<R, LS>(U, N, mu, link_pos<LPAR>(N, idx, LPAR), u);
 #pragma unroll
             for (int k = 0; k < 2; ++k)
 #pragma unroll
@@ -1672,7 +1732,7 @@ __device__ __forceinline__ void wilson_hop_fetch(const Geom &g, Fetch fetch, con
             Cx<R> ps[4][3], h[2][3], uh[2][3], u[3][3];
             fetch(y, mu, -1, ps);
             spin_project<R>(mu, R(1), ps, h);
-            load_link<R, LS>(U, N, mu, y, u);
+            load_link<R, LS>(U, N, mu, link_pos<LPAR>(N, y, 1 - LPAR), u);
 #pragma unroll
             for (int k = 0; k < 2; ++k)
 #pragma unroll
@@ -1708,7 +1768,7 @@ __global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 :
             int xc[4];
             const int s = half_site(P.g, 1, idx, xc);
             Cx<R> acc[4][3], o[12];
-            wilson_hop_fetch<R, LS>(
+            wilson_hop_fetch<R, LS, 1>(
                 P.g, [&](int y, int, int, Cx<R> ps[4][3]) { load_spinor<S, R>(src, N, y >> 1, ps); },
                 (const LS *)P.U, P.antip, s, xc, acc);
 #pragma unroll
@@ -1737,7 +1797,7 @@ __global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 :
             int xc[4];
             const int s = half_site(P.g, 0, idx, xc);
             Cx<R> acc[4][3], ps[4][3], z[4][3], av[12];
-            wilson_hop_fetch<R, LS>(
+            wilson_hop_fetch<R, LS, 0>(
                 P.g, [&](int y, int, int, Cx<R> f[4][3]) { load_spinor<S, R>(h, N, y >> 1, f); },
                 (const LS *)P.U, P.antip, s, xc, acc);
             load_spinor<S, R>(pv, N, idx, ps);
@@ -1774,7 +1834,7 @@ __global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 :
             int xc[4];
             const int s = half_site(P.g, 0, idx, xc);
             Cx<R> acc[4][3], sp[4][3], av[12];
-            wilson_hop_fetch<R, LS>(
+            wilson_hop_fetch<R, LS, 0>(
                 P.g, [&](int y, int, int, Cx<R> f[4][3]) { load_spinor<S, R>(h, N, y >> 1, f); },
                 (const LS *)P.U, P.antip, s, xc, acc);
             load_spinor<S, R>(sv, N, idx, sp);
@@ -2009,10 +2069,10 @@ __global__ void __launch_bounds__(PT_BLOCK) k_weo_contract(EP P) {
                         if (l > 0 && P.lev_cols[(size_t)l * NF + sw] != P.lev_anc[(size_t)l * P.m_fin + tk.colour])
                             continue;
                     }
-                    const int y = shift_site(P.g, sw, xs, P.mu, P.p[n]);
+                    int cm;
+                    const int y = shift_fwd(P.g, sw, xs, P.mu, P.p[n], &cm);
                     for (int nu = 0; nu < 4; ++nu) xy[nu] = xs[nu];
-                    const int cm = (xs[P.mu] + P.p[n]) % P.g.D[P.mu];
-                    xy[P.mu] = cm < 0 ? cm + P.g.D[P.mu] : cm;
+                    xy[P.mu] = cm;
                     Cx<double> xv[12];
                     weo_x_at(P, tk, key, x, t64, y, xy, xv);
                     for (int a = 0; a < 12; ++a) {
@@ -2030,6 +2090,230 @@ __global__ void __launch_bounds__(PT_BLOCK) k_weo_contract(EP P) {
     ITEM_LOOP_END
 }
 
+// ------------------------------------------------------------------ even-odd Wilson, link-sharing groups
+// rhs_block = 8 in even-odd mode: one CTA of 256 threads takes a block of 256
+// consecutive half-field entries for eight slots of the work list, one warp
+// per slot.  The block is processed 32 entries at a time: the CTA first
+// stages the 32 sites' eight links in shared memory (lane index innermost, so
+// that a warp reads consecutive words), then every warp applies the hops of
+// its own slot at those 32 sites with the links from shared memory.  Each
+// link crosses L2 once per eight right-hand sides instead of once per
+// right-hand side (about 850 instead of 1400 bytes of L1/L2 traffic per site
+// and right-hand side), and each warp reduces its own slot's dot products.
+#define WEO_G 8                 // slots per work item (one warp each)
+#define WEO_SUB 32              // entries per shared-memory link stage
+
+#define ITEMG_LOOP(LIST)                                                        \
+    const int cnt = P.counts[LIST];                                             \
+    const int *lst = P.lists + (size_t)(LIST) * P.R;                            \
+    const int ngrp_ = (cnt + WEO_G - 1) / WEO_G;                                \
+    const int64_t n_items = (int64_t)ngrp_ * P.nsb;                             \
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;                  \
+    for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {              \
+        const int grp_ = (int)(it / P.nsb);                                     \
+        const int b = (int)(it - (int64_t)grp_ * P.nsb);                        \
+        const int jw = (grp_ * WEO_G + wid < cnt) ? lst[grp_ * WEO_G + wid] : -1; \
+        const bool act = jw >= 0 && P.slots[jw].phase == PH_INNER;
+#define ITEMG_LOOP_END }
+
+// the eight links of the sites of entries base .. base + 31 (parity par) into
+// sU[k][e][lane], k = 2 mu + (0 forward: U_mu(x), 1 backward: U_mu(x - mu))
+template <typename R, typename LS>
+__device__ __forceinline__ void weo_stage_links(const EP &P, int par, int base, Cx<R> (*sU)[9][WEO_SUB]) {
+    // 32 sites x 8 links = 256 threads; warp k stages link k of the 32 sites,
+    // consecutive entries of the even-odd ordered copy
+    const int i = threadIdx.x & 31, k = threadIdx.x >> 5;
+    const int h = base + i;
+    if (h < P.nsite) {
+        int x[4];
+        const int s = half_site(P.g, par, h, x);
+        const int mu = k >> 1;
+        const int pos = (k & 1) ? eo_link_pos(P.g.N, nb_bwd(P.g, s, x, mu), 1 - par) : eo_link_pos(P.g.N, s, par);
+        Cx<R> u[3][3];
+        load_link<R, LS>((const LS *)P.U, P.g.N, mu, pos, u);
+#pragma unroll
+        for (int e = 0; e < 9; ++e) sU[k][e][i] = u[e / 3][e % 3];
+    }
+}
+
+// (H psi)(x) at site idx (coordinates x) with the neighbour spinors read from
+// the half field f (Nh entries) and the links from the staged sU column `col`
+template <typename R, typename S>
+__device__ __forceinline__ void wilson_hop_staged(const Geom &g, const S *f, int Nh, Cx<R> (*sU)[9][WEO_SUB],
+                                                  int col, int antip, int idx, const int x[4], Cx<R> acc[4][3]) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[s][a] = Cx<R>{R(0), R(0)};
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        {   // forward hop: (1 - g_mu) U_mu(x) psi(x + mu)
+            const int y = nb_fwd(g, idx, x, mu);
+            const R eta = (antip && mu == 3 && x[3] == g.D[3] - 1) ? R(-1) : R(1);
+            Cx<R> ps[4][3], h[2][3], uh[2][3];
+            load_spinor<S, R>(f, Nh, y >> 1, ps);
+            spin_project<R>(mu, R(-1), ps, h);
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    Cx<R> t = cmul(sU[2 * mu][3 * a][col], h[k][0]);
+                    t = cadd(t, cmul(sU[2 * mu][3 * a + 1][col], h[k][1]));
+                    t = cadd(t, cmul(sU[2 * mu][3 * a + 2][col], h[k][2]));
+                    uh[k][a] = t;
+                }
+            spin_accumulate<R>(mu, R(-1), eta, uh, acc);
+        }
+        {   // backward hop: (1 + g_mu) U_mu(x - mu)^dagger psi(x - mu)
+            const int y = nb_bwd(g, idx, x, mu);
+            const R eta = (antip && mu == 3 && x[3] == 0) ? R(-1) : R(1);
+            Cx<R> ps[4][3], h[2][3], uh[2][3];
+            load_spinor<S, R>(f, Nh, y >> 1, ps);
+            spin_project<R>(mu, R(1), ps, h);
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    Cx<R> t = cconjmul(sU[2 * mu + 1][a][col], h[k][0]);
+                    t = cadd(t, cconjmul(sU[2 * mu + 1][3 + a][col], h[k][1]));
+                    t = cadd(t, cconjmul(sU[2 * mu + 1][6 + a][col], h[k][2]));
+                    uh[k][a] = t;
+                }
+            spin_accumulate<R>(mu, R(1), eta, uh, acc);
+        }
+    }
+}
+
+// grouped h = D_oe p (WHICH 0: p = pv; 1: p = s) at the odd entries
+template <typename S, typename LS, int WHICH>
+__global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 : PT_WIL_MINB) k_weo_hop_g(EP P) {
+    typedef typename ArithT<S>::T R;
+    __shared__ Cx<R> sU[8][9][WEO_SUB];
+    const int N = P.nsite;
+    ITEMG_LOOP(LIST_INNER)
+        const S *src = act ? slot_cptr<S>(WHICH ? P.s : P.pv, jw, P.L) : nullptr;
+        S *hf = act ? slot_ptr<S>(P.p1, jw, P.L) : nullptr;
+        for (int sub = 0; sub < PT_BLOCK / WEO_SUB; ++sub) {
+            const int base = b * PT_BLOCK + sub * WEO_SUB;
+            if (base >= N) break;                              // uniform over the CTA
+            __syncthreads();                                   // the previous stage is consumed
+            weo_stage_links<R, LS>(P, 1, base, sU);
+            __syncthreads();
+            const int idx = base + lane;
+            if (act && idx < N) {
+                int xc[4];
+                const int s = half_site(P.g, 1, idx, xc);
+                Cx<R> acc[4][3], o[12];
+                wilson_hop_staged<R, S>(P.g, src, N, sU, lane, P.antip, s, xc, acc);
+#pragma unroll
+                for (int c = 0; c < 12; ++c)
+                    o[c] = Cx<R>{rnd<S, R>(acc[c / 3][c % 3].re), rnd<S, R>(acc[c / 3][c % 3].im)};
+                store_spinor<S, R>(hf, N, idx, o);
+            }
+        }
+    ITEMG_LOOP_END
+}
+
+// warp sums of K values, written by lane 0 as the partials of (slot jw, block b)
+template <int K, typename R>
+__device__ __forceinline__ void weo_warp_store(const EP &P, int jw, int b, R vr[K]) {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) vr[k] += __shfl_down_sync(0xffffffffu, vr[k], o);
+    if ((threadIdx.x & 31) == 0) {
+        double *dst = P.partials + ((size_t)jw * P.nsb + b) * K;
+#pragma unroll
+        for (int k = 0; k < K; ++k) dst[k] = (double)vr[k];
+    }
+}
+
+// grouped v = S p = p - kappa^2 D_eo h at the even entries;  partial (r0, v)
+template <typename S, typename LS>
+__global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 : PT_WIL_MINB) k_weo_apply1_g(EP P) {
+    typedef typename ArithT<S>::T R;
+    __shared__ Cx<R> sU[8][9][WEO_SUB];
+    const int N = P.nsite;
+    const R k2 = (R)(P.kappa * P.kappa);
+    ITEMG_LOOP(LIST_INNER)
+        const S *pv = act ? slot_cptr<S>(P.pv, jw, P.L) : nullptr;
+        const S *h = act ? slot_cptr<S>(P.p1, jw, P.L) : nullptr;
+        const S *r0 = act ? slot_cptr<S>(P.r0, jw, P.L) : nullptr;
+        S *q = act ? slot_ptr<S>(P.q, jw, P.L) : nullptr;
+        R vr[2] = {R(0), R(0)};
+        for (int sub = 0; sub < PT_BLOCK / WEO_SUB; ++sub) {
+            const int base = b * PT_BLOCK + sub * WEO_SUB;
+            if (base >= N) break;
+            __syncthreads();
+            weo_stage_links<R, LS>(P, 0, base, sU);
+            __syncthreads();
+            const int idx = base + lane;
+            if (act && idx < N) {
+                int xc[4];
+                const int s = half_site(P.g, 0, idx, xc);
+                Cx<R> acc[4][3], ps[4][3], z[4][3], av[12];
+                wilson_hop_staged<R, S>(P.g, h, N, sU, lane, P.antip, s, xc, acc);
+                load_spinor<S, R>(pv, N, idx, ps);
+                load_spinor<S, R>(r0, N, idx, z);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) {
+                    const Cx<R> w = csub(ps[c / 3][c % 3], cscale(acc[c / 3][c % 3], k2));
+                    av[c] = Cx<R>{rnd<S, R>(w.re), rnd<S, R>(w.im)};
+                    const Cx<R> zc = z[c / 3][c % 3];
+                    vr[0] += zc.re * av[c].re + zc.im * av[c].im;
+                    vr[1] += zc.re * av[c].im - zc.im * av[c].re;
+                }
+                store_spinor<S, R>(q, N, idx, av);
+            }
+        }
+        if (act) weo_warp_store<2, R>(P, jw, b, vr);
+    ITEMG_LOOP_END
+}
+
+// grouped t = S s = s - kappa^2 D_eo h at the even entries;  partials (t, s), |t|^2
+template <typename S, typename LS>
+__global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 : PT_WIL_MINB) k_weo_apply2_g(EP P) {
+    typedef typename ArithT<S>::T R;
+    __shared__ Cx<R> sU[8][9][WEO_SUB];
+    const int N = P.nsite;
+    const R k2 = (R)(P.kappa * P.kappa);
+    ITEMG_LOOP(LIST_INNER)
+        const S *sv = act ? slot_cptr<S>(P.s, jw, P.L) : nullptr;
+        const S *h = act ? slot_cptr<S>(P.p1, jw, P.L) : nullptr;
+        S *t = act ? slot_ptr<S>(P.t, jw, P.L) : nullptr;
+        R vr[3] = {R(0), R(0), R(0)};
+        for (int sub = 0; sub < PT_BLOCK / WEO_SUB; ++sub) {
+            const int base = b * PT_BLOCK + sub * WEO_SUB;
+            if (base >= N) break;
+            __syncthreads();
+            weo_stage_links<R, LS>(P, 0, base, sU);
+            __syncthreads();
+            const int idx = base + lane;
+            if (act && idx < N) {
+                int xc[4];
+                const int s = half_site(P.g, 0, idx, xc);
+                Cx<R> acc[4][3], sp[4][3], av[12];
+                wilson_hop_staged<R, S>(P.g, h, N, sU, lane, P.antip, s, xc, acc);
+                load_spinor<S, R>(sv, N, idx, sp);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) {
+                    const Cx<R> w = csub(sp[c / 3][c % 3], cscale(acc[c / 3][c % 3], k2));
+                    av[c] = Cx<R>{rnd<S, R>(w.re), rnd<S, R>(w.im)};
+                }
+                store_spinor<S, R>(t, N, idx, av);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) {
+                    const Cx<R> tv = av[c], sc = sp[c / 3][c % 3];
+                    vr[0] += tv.re * sc.re + tv.im * sc.im;
+                    vr[1] += tv.re * sc.im - tv.im * sc.re;
+                    vr[2] += tv.re * tv.re + tv.im * tv.im;
+                }
+            }
+        }
+        if (act) weo_warp_store<3, R>(P, jw, b, vr);
+    ITEMG_LOOP_END
+}
+
 // ------------------------------------------------------------------ host driver
 struct EngineRun {
     EP P;
@@ -2041,6 +2325,7 @@ struct EngineRun {
     int g_apply1_x2, g_apply2_x2, g_contract32;
     int g_hop, g_ohop;                 // even-odd: the odd-site hop of the inner and of the outer step
     int g_obp;                         // even-odd Wilson: b'_e of new tasks
+    int g_hop_g, g_apply1_g, g_apply2_g;   // even-odd Wilson, link-sharing groups of slots
     double *part_con, *part_outer;   // partial-sum regions of the contraction and outer kernel groups
 };
 
@@ -2139,14 +2424,24 @@ static void enqueue_iteration(const EngineRun &E, cudaStream_t st, const cudaEve
         ev_rec(ev, 2, st);
     } else if (P.eo) {
         ev_rec(ev, 0, st);
-        k_weo_hop<S, LS, 0><<<E.g_hop, P.bs, 0, st>>>(P);
-        k_weo_apply1<S, LS><<<E.g_apply1, P.bs, 0, st>>>(P);
+        if (P.rhs_block == WEO_G) {
+            k_weo_hop_g<S, LS, 0><<<E.g_hop_g, PT_BLOCK, 0, st>>>(P);
+            k_weo_apply1_g<S, LS><<<E.g_apply1_g, PT_BLOCK, 0, st>>>(P);
+        } else {
+            k_weo_hop<S, LS, 0><<<E.g_hop, P.bs, 0, st>>>(P);
+            k_weo_apply1<S, LS><<<E.g_apply1, P.bs, 0, st>>>(P);
+        }
         ev_rec(ev, 1, st);
         k_fin_bicg_alpha<<<W, 256, 0, st>>>(P);
         k_bicg_s<S><<<E.g_s, P.bs, 0, st>>>(P);
         ev_rec(ev, 2, st);
-        k_weo_hop<S, LS, 1><<<E.g_hop, P.bs, 0, st>>>(P);
-        k_weo_apply2<S, LS><<<E.g_apply2, P.bs, 0, st>>>(P);
+        if (P.rhs_block == WEO_G) {
+            k_weo_hop_g<S, LS, 1><<<E.g_hop_g, PT_BLOCK, 0, st>>>(P);
+            k_weo_apply2_g<S, LS><<<E.g_apply2_g, PT_BLOCK, 0, st>>>(P);
+        } else {
+            k_weo_hop<S, LS, 1><<<E.g_hop, P.bs, 0, st>>>(P);
+            k_weo_apply2<S, LS><<<E.g_apply2, P.bs, 0, st>>>(P);
+        }
         ev_rec(ev, 3, st);
         k_fin_bicg_omega<<<W, 256, 0, st>>>(P);
         k_bicg_update<S><<<E.g_upd, P.bs, 0, st>>>(P);
@@ -2265,7 +2560,11 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     const int nvec = KIND ? (eo ? 8 : 7) : (eo ? 6 : 5);
     const int nf64 = eo ? 3 : 1;
     const size_t per_slot = (size_t)L * (nf64 * sizeof(double) + nvec * sizeof(S));
-    int R = rq.R_force > 0 ? rq.R_force : (int)std::min<size_t>((size_t)rq.n_tasks, c->mem_budget / per_slot);
+    // even-odd Wilson: the inner kernels read a copy of their links in the
+    // even-odd order (LinkLayout<LS>::CHUNKS chunks per site)
+    const size_t ueo_bytes = (KIND == 1 && eo) ? (size_t)g.N * LinkLayout<LS>::CHUNKS * sizeof(typename LinkLayout<LS>::E) : 0;
+    const size_t budget = c->mem_budget > 2 * ueo_bytes ? c->mem_budget - ueo_bytes : c->mem_budget / 2;
+    int R = rq.R_force > 0 ? rq.R_force : (int)std::min<size_t>((size_t)rq.n_tasks, budget / per_slot);
     if (rq.R_force <= 0 && c->max_slots > 0) R = std::min(R, c->max_slots);
     if (R < 1) R = 1;
     if (rq.R_force <= 0) R = std::min(R, 4096);
@@ -2297,6 +2596,7 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     size_t o_tasks = take((size_t)rq.n_tasks * sizeof(Task));
     size_t o_tstat = take((size_t)rq.n_tasks * sizeof(TaskStat));
     size_t o_tout = take((size_t)rq.n_tasks * std::max(rq.n_p, 1) * 2 * sizeof(double));
+    size_t o_ueo = ueo_bytes ? take(ueo_bytes) : 0;
     void *ws;
     int rc = pt_workspace(c, off, &ws);
     if (rc) return rc;
@@ -2313,7 +2613,12 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     P.eo = eo ? 1 : 0;
     P.nsite = nsite;
     P.gs = tn.group;
-    P.rhs_block = (KIND == 1 && !eo && !std::is_same<S, double>::value && tn.rhs_block == 2) ? 2 : 1;
+    // right-hand sides per Wilson work item: 2 on the full system (mixed
+    // precision), a group of WEO_G slots (one warp each, links staged once in
+    // shared memory) in even-odd mode with 256-thread CTAs
+    P.rhs_block = 1;
+    if (KIND == 1 && !eo && !std::is_same<S, double>::value && tn.rhs_block == 2) P.rhs_block = 2;
+    if (KIND == 1 && eo && tn.rhs_block == WEO_G && bs == PT_BLOCK) P.rhs_block = WEO_G;
     P.overlap = tn.overlap ? 1 : 0;
     // four sites (even-odd: four half entries of one x row) per thread
     P.vec4 = (KIND == 0 && g.D[0] % (eo ? 8 : 4) == 0) ? 1 : 0;
@@ -2339,7 +2644,12 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     P.lev_anc = rq.lev_anc;
     P.dilute = rq.dilute;
     P.pshift = rq.pshift;
-    for (int n = 0; n < rq.n_p && n < PT_MAX_P; ++n) P.p[n] = rq.p_list[n];
+    // displacements reduced to [0, D_mu) once here (the contractions add and
+    // conditionally subtract instead of taking a modulo per site)
+    for (int n = 0; n < rq.n_p && n < PT_MAX_P; ++n) {
+        const int D = g.D[rq.mu];
+        P.p[n] = ((rq.p_list[n] % D) + D) % D;
+    }
     P.tasks = (const Task *)(base + o_tasks);
     P.n_tasks = rq.n_tasks;
     P.B_user = rq.B_user;
@@ -2378,6 +2688,15 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     PT_CUDA(cudaMemsetAsync(P.task_out, 0, (size_t)rq.n_tasks * std::max(rq.n_p, 1) * 2 * sizeof(double), st));
     // zero the vectors once so that no slot ever reads uninitialised memory
     PT_CUDA(cudaMemsetAsync(base + o_x64, 0, o_slots - o_x64, st));
+    if constexpr (KIND == 1) {
+        if (ueo_bytes) {
+            typedef typename LinkLayout<LS>::E E;
+            E *ueo = (E *)(base + o_ueo);
+            k_links_eo<E><<<c->num_sms * 8, 256, 0, st>>>(g, LinkLayout<LS>::CHUNKS, (const E *)P.U, ueo);
+            PT_CUDA(cudaGetLastError());
+            P.U = ueo;
+        }
+    }
 
     int occ = 0;
     if constexpr (KIND == 0) {
@@ -2393,6 +2712,7 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     E.g_oupd = persistent_grid(k_outer_update<KIND, S>, ns, bs);
     E.g_ores = persistent_grid(k_outer_residual<KIND, S>, ns, bs);
     E.g_hop = E.g_ohop = E.g_obp = 0;
+    E.g_hop_g = E.g_apply1_g = E.g_apply2_g = 0;
     if constexpr (KIND == 0) {
         if (eo) {
             E.g_contract = persistent_grid(k_eo_contract<16>, ns, bs);
@@ -2418,6 +2738,9 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
         E.g_apply1 = persistent_grid(k_weo_apply1<S, LS>, ns, bs);
         E.g_apply2 = persistent_grid(k_weo_apply2<S, LS>, ns, bs);
         E.g_apply1_x2 = E.g_apply2_x2 = 0;
+        E.g_hop_g = persistent_grid(k_weo_hop_g<S, LS, 0>, ns, PT_BLOCK);
+        E.g_apply1_g = persistent_grid(k_weo_apply1_g<S, LS>, ns, PT_BLOCK);
+        E.g_apply2_g = persistent_grid(k_weo_apply2_g<S, LS>, ns, PT_BLOCK);
         E.g_upd = persistent_grid(k_bicg_update<S>, ns, bs);
         E.g_s = persistent_grid(k_bicg_s<S>, ns, bs);
         E.g_dir = persistent_grid(k_bicg_dir<S>, ns, bs);
@@ -3014,7 +3337,7 @@ static int store_tuning(pt_ctx *c, const pt_op *op, int prec, const pt_tune *t) 
     e.delta = t->delta;
     e.group = t->group;
     e.graph_iters = t->graph_iters;
-    e.rhs_block = t->rhs_block == 2 ? 2 : 1;
+    e.rhs_block = (t->rhs_block == 2 || t->rhs_block == WEO_G) ? t->rhs_block : 1;
     e.overlap = t->overlap ? 1 : 0;
     e.evenodd = t->evenodd ? 1 : 0;
     e.cta_threads = t->cta_threads;
@@ -3030,7 +3353,8 @@ extern "C" int pt_set_tuning(pt_ctx *c, const pt_op *op, int prec, const pt_tune
         PT_CHECK_ARG(t->delta >= 0.0 && t->delta < 1.0, "pt_set_tuning: delta must be in [0, 1)");
         PT_CHECK_ARG(t->group >= 1 && t->group <= 64, "pt_set_tuning: group must be in [1, 64]");
         PT_CHECK_ARG(t->graph_iters >= 1 && t->graph_iters <= 64, "pt_set_tuning: graph_iters must be in [1, 64]");
-        PT_CHECK_ARG(t->rhs_block >= 0 && t->rhs_block <= 2, "pt_set_tuning: rhs_block must be 0, 1 or 2");
+        PT_CHECK_ARG((t->rhs_block >= 0 && t->rhs_block <= 2) || t->rhs_block == WEO_G,
+                     "pt_set_tuning: rhs_block must be 0, 1, 2 or %d", WEO_G);
         PT_CHECK_ARG(t->overlap == 0 || t->overlap == 1, "pt_set_tuning: overlap must be 0 or 1");
         PT_CHECK_ARG(t->evenodd == 0 || t->evenodd == 1, "pt_set_tuning: evenodd must be 0 or 1");
         PT_CHECK_ARG(t->cta_threads == 0 || t->cta_threads == 64 || t->cta_threads == 128 || t->cta_threads == 256,
@@ -3115,7 +3439,7 @@ extern "C" int pt_autotune(pt_ctx *c, const pt_op *op, const int32_t *col_dev, i
     if (op->kind == 1) groups = {1, 2, 4, 8, 16};
     const std::vector<int> iters = {4, 8, 16};
     std::vector<int> blocks;
-    if (op->kind == 1 && prec != PT_PREC_FP64) blocks = {1, 2};
+    if (op->kind == 1 && prec != PT_PREC_FP64) blocks = {1, 2, WEO_G};
     std::vector<int> evenodds;
     if (pt_evenodd_ok(op->dims)) evenodds = {0, 1};
     // item shape: CTA threads, and (Laplacian) sites per thread

@@ -277,12 +277,22 @@ __device__ __forceinline__ void spin_project(int mu, R sg, const Cx<R> ps[4][3],
     }
 }
 
-// acc += eta * (rebuilt 4-spinor from the colour-rotated half spinor uh)
+// v, or -v when n: the sign bit flipped on the integer pipe, the same bits as
+// v * -1 without a floating-point multiply (FP64 issue slots are scarce)
+__device__ __forceinline__ float neg_if(float v, bool n) { return __uint_as_float(__float_as_uint(v) ^ ((unsigned)n << 31)); }
+__device__ __forceinline__ double neg_if(double v, bool n) {
+    return __longlong_as_double(__double_as_longlong(v) ^ (long long)((unsigned long long)n << 63));
+}
+
+// acc += eta * (rebuilt 4-spinor from the colour-rotated half spinor uh),
+// eta = +1 or -1 (the boundary sign)
 template <typename R>
 __device__ __forceinline__ void spin_accumulate(int mu, R sg, R eta, const Cx<R> uh[2][3], Cx<R> acc[4][3]) {
+    const bool neg = eta < R(0);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        Cx<R> h0 = cscale(uh[0][a], eta), h1 = cscale(uh[1][a], eta);
+        const Cx<R> h0 = Cx<R>{neg_if(uh[0][a].re, neg), neg_if(uh[0][a].im, neg)};
+        const Cx<R> h1 = Cx<R>{neg_if(uh[1][a].re, neg), neg_if(uh[1][a].im, neg)};
         acc[0][a] = cadd(acc[0][a], h0);
         acc[1][a] = cadd(acc[1][a], h1);
         if (mu == 0) {

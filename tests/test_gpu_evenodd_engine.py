@@ -228,3 +228,35 @@ def test_item_shapes_wilson(pt, ctx, cta):
     pt.set_tuning(op, "mixed_fp32", reset=True)
     with pytest.raises(pt.PtraceError):
         pt.set_tuning(op, "mixed_fp32", cta_threads=512)
+
+
+@pytest.mark.parametrize("dims", [[4, 4, 2, 6], [6, 2, 4, 8], [8, 8, 8, 8]])
+def test_wilson_link_sharing_groups(pt, ctx, dims):
+    """rhs_block = 8 in even-odd mode: eight slots per work item, one warp
+    each, the links of every 32 sites staged once in shared memory.  Traces
+    against the oracle in every precision on lattices whose half volume is
+    not a multiple of the 256-entry block, with work lists that are not a
+    multiple of eight; solves of three sources (one group with five idle
+    warps) against the ungrouped engine."""
+    import torch
+    from paper_2106_01275_gb300 import inputs
+    kappa, mu = 0.12, 2
+    U = inputs.gauge_links(dims, 99)
+    col, m = greedy_colour(dims, mu, [1], 1, 0)
+    op = pt.wilson(ctx, dims, _t(U), kappa, True)
+    want = OE.probed_estimates(OE.Wilson(dims, U, kappa), col, m, 7, 1, 1, mu, [0, 1], 1e-12)
+    for prec in PRECS:
+        pt.set_tuning(op, prec, evenodd=1, rhs_block=8, cta_threads=256)
+        assert pt.get_tuning(op, prec)["rhs_block"] == 8
+        est, _, _, st = pt.trace(op, _t(col), m, mu, [0, 1], "z4", 7, 0, 1, True, prec, 1e-10, 5000)
+        assert np.allclose(est, want, rtol=1e-8, atol=1e-7), prec
+        assert st["max_relres"] <= 1e-10
+    N = int(np.prod(dims))
+    B = torch.as_tensor(np.random.default_rng(5).standard_normal((3, N, 4, 3, 2))).cuda().contiguous()
+    X8, _, r8, _ = pt.solve(op, B, "mixed_fp32", 1e-10, 5000)
+    pt.set_tuning(op, "mixed_fp32", rhs_block=1)
+    X1, _, r1, _ = pt.solve(op, B, "mixed_fp32", 1e-10, 5000)
+    for prec in PRECS:
+        pt.set_tuning(op, prec, reset=True)
+    assert max(r8) <= 1e-10 and max(r1) <= 1e-10
+    assert torch.allclose(X8, X1, rtol=1e-8, atol=1e-9 * X1.abs().max().item())
