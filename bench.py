@@ -268,9 +268,14 @@ def run_ours(args):
     if W.kind == "lap":
         kernel = ("k_eo_hop_v4 + k_eo_apply_v4 <float> (S p = d p - H_eo H_oe p / d on the even sites, p update, "
                   "p.q)" if eo else "k_cg_apply_v4<float> (p update + stencil + p.q)")
+    elif eo and tuning.get("rhs_block", 1) == 8 and tuning.get("cta_threads", 0) in (0, 256):
+        kernel = ("k_weo_hop_g + k_weo_apply1/2_g <float,float> (eight slots per item, links staged in shared "
+                  "memory; S = 1 - kappa^2 D_eo D_oe on the even sites + BiCGStab dots)")
     elif eo:
         kernel = ("k_weo_hop + k_weo_apply1/2 <float,float> (S = 1 - kappa^2 D_eo D_oe on the even sites + "
                   "BiCGStab dots)")
+    elif tuning.get("rhs_block", 1) == 2:
+        kernel = "k_bicg_apply1/2_x2<float,float> (Wilson apply for two right-hand sides per item + dots)"
     else:
         kernel = "k_bicg_apply1/2<float,float> (Wilson apply + dots)"
     roofline = {"bound": "hbm", "kernel": kernel,
