@@ -15,6 +15,10 @@ exp(i 0.3 H) from seed 1234; displacements p = 0, 2, 4, 8 along z with their
 (p, 2) colourings, Z4 noise with 12x spin-colour dilution, 4 noise sets;
 mixed FP32 BiCGStab inside FP64 defect correction to 1e-10.
 
+"clover24": the same with the clover term, c_sw = 1.0 (the operator class of
+the paper's production runs, on synthetic links), solved on the even Schur
+complement S = A_ee - kappa^2 D_eo A_oo^{-1} D_oe.
+
 Reported value: operator applications x sites per second over the whole step
 (site*RHS/s).  Also reported: the time to the standard deviation of the noise
 sets of one step (= the step time), the same for the plain FP64
@@ -49,8 +53,9 @@ SEED = 1000
 
 class Workload:
     def __init__(self, name, kind, dims, mu, pk, p_contract, n_sets, noise, desc, m2=None, kappa=None,
-                 link_seed=None, plain_subset=None):
+                 link_seed=None, plain_subset=None, csw=0.0):
         self.name, self.kind, self.dims, self.mu, self.pk = name, kind, list(dims), mu, list(pk)
+        self.csw = float(csw)                # clover coefficient (Wilson; 0: none)
         self.p_contract, self.n_sets, self.noise, self.desc = list(p_contract), n_sets, noise, desc
         self.m2, self.kappa, self.link_seed = m2, kappa, link_seed
         self.plain_subset = plain_subset     # colourings used for the plain FP64 timing (None = all)
@@ -70,8 +75,10 @@ class Workload:
             return 240.0, 288.0
         # even-odd, per lattice site: the odd-site hop reads p (or s) at the even sites and
         # writes h at the odd ones (96 B); v = S p then reads h, p, r0 and writes v (192 B),
-        # t = S s reads h, s and writes t (144 B); every link is read by both kernels
-        return 264.0, 576.0
+        # t = S s reads h, s and writes t (144 B); every link is read by both kernels; with the
+        # clover term the hop also reads A_oo^{-1} (288 B per odd site) and the apply A_ee
+        # (288 B per even site)
+        return 264.0, 576.0 + (288.0 if self.csw else 0.0)
 
 
 def workloads(case):
@@ -90,7 +97,14 @@ def workloads(case):
         "Z4 x 12 spin-colour dilution, 4 sets (1584 RHS), mixed FP32 BiCGStab + FP64 defect correction to 1e-10"
         if not small else "wilson24 small: 16^3x32, (p,k)=(4,2), 1 Z4 set, 12x dilution",
         kappa=0.124, link_seed=1234, plain_subset=[3])
-    return {"lap16": lap, "wilson24": wil}
+    clv = Workload(
+        "clover24", "wil", wil.dims, 2, wil.pk, wil.p_contract, wil.n_sets, "z4",
+        ("clover24: clover Wilson-Dirac c_sw=1.0 24^3x48 kappa=0.124 antiperiodic t, p=0,2,4,8 along z with "
+         "(p,2)-colourings, Z4 x 12 spin-colour dilution, 4 sets (1584 RHS), mixed FP32 BiCGStab on the even "
+         "Schur complement + FP64 defect correction to 1e-10")
+        if not small else "clover24 small: 16^3x32 c_sw=1.0, (p,k)=(4,2), 1 Z4 set, 12x dilution",
+        kappa=0.124, link_seed=1234, plain_subset=[3], csw=1.0)
+    return {"lap16": lap, "wilson24": wil, "clover24": clv}
 
 
 def peaks():
@@ -176,7 +190,10 @@ def make_operator(pt, ctx, W):
         return pt.laplacian(ctx, W.dims, W.m2)
     from paper_2106_01275_gb300 import inputs
     U = torch.as_tensor(inputs.gauge_links(W.dims, W.link_seed)).cuda()
-    return pt.wilson(ctx, W.dims, U, W.kappa, True)
+    op = pt.wilson(ctx, W.dims, U, W.kappa, True)
+    if W.csw:
+        pt.set_clover(op, W.csw)
+    return op
 
 
 def dist_backend():
@@ -268,6 +285,9 @@ def run_ours(args):
     if W.kind == "lap":
         kernel = ("k_eo_hop_v4 + k_eo_apply_v4 <float> (S p = d p - H_eo H_oe p / d on the even sites, p update, "
                   "p.q)" if eo else "k_cg_apply_v4<float> (p update + stencil + p.q)")
+    elif eo and W.csw:
+        kernel = ("k_weo_hop + k_weo_apply1/2 <float,float,clover> (S = A_ee - kappa^2 D_eo A_oo^{-1} D_oe on the "
+                  "even sites + BiCGStab dots)")
     elif eo and tuning.get("rhs_block", 1) == 8 and tuning.get("cta_threads", 0) in (0, 256):
         kernel = ("k_weo_hop_g + k_weo_apply1/2_g <float,float> (eight slots per item, links staged in shared "
                   "memory; S = 1 - kappa^2 D_eo D_oe on the even sites + BiCGStab dots)")
@@ -295,7 +315,9 @@ def run_ours(args):
                                   "writes p_i, q (10 B)")
     elif eo:
         roofline["bytes_note"] = ("per S application and lattice site: k_weo_hop 96 B, k_weo_apply1 192 B / "
-                                  "k_weo_apply2 144 B (averaged: 264 B), links 2 x 288 B per site per application")
+                                  "k_weo_apply2 144 B (averaged: 264 B), links 2 x 288 B per site per application"
+                                  + (", clover blocks 288 B per site per application (A_oo^{-1} on the odd "
+                                     "sites, A_ee on the even ones)" if W.csw else ""))
     if W.kind == "lap":
         n_vec, vec_sites = (6, N // 2) if eo else (5, N)
     else:
@@ -409,7 +431,9 @@ def run_ours(args):
         rel = np.max(np.abs(est64 - ref) / np.maximum(np.abs(est64), 1e-300))
         out["fp64_plain"] = {"time_to_sigma_s": t_plain_step, "measured_rhs": int(st64["n_rhs"]),
                              "measured_s": t_plain, "scaled_by_rhs_fraction": frac,
-                             "solver": "FP64 CG / BiCGStab on the full system, one right-hand side at a time",
+                             "solver": ("FP64 BiCGStab on the even Schur complement (the clover operator has no "
+                                        "full-system path), one right-hand side at a time" if W.csw else
+                                        "FP64 CG / BiCGStab on the full system, one right-hand side at a time"),
                              "site_rhs_per_s": st64["site_rhs_applies"] / t_plain,
                              "max_rel_diff_vs_mixed": float(rel)}
         out["speedup_vs_fp64_plain"] = t_plain_step / step_s
@@ -812,7 +836,11 @@ def oracle_sample(W, seconds, worker=0, n_workers=1):
         kind, comps, applies = 0, [0], 1
     else:
         from paper_2106_01275_gb300 import inputs
-        op = OE.Wilson(W.dims, inputs.gauge_links(W.dims, W.link_seed), W.kappa, True)
+        if W.csw:
+            import oracle.clover as CL
+            op = CL.WilsonClover(W.dims, inputs.gauge_links(W.dims, W.link_seed), W.kappa, W.csw, True)
+        else:
+            op = OE.Wilson(W.dims, inputs.gauge_links(W.dims, W.link_seed), W.kappa, True)
         kind, comps, applies = 1, list(range(12)), 2
     t0 = time.perf_counter()
     site_rhs, n_rhs = 0, 0
@@ -894,7 +922,8 @@ def cpu_baseline(W, seconds):
     finally:
         pool.close()
     what = ("%d RHS of one colouring of %s, FP64 CG to 1e-10 with contraction" % (n_rhs, W.name)
-            if W.kind == "lap" else "%d FP64 Wilson operator applications on %s" % (n_rhs, W.name))
+            if W.kind == "lap" else "%d FP64 %s operator applications on %s"
+            % (n_rhs, "clover Wilson" if W.csw else "Wilson", W.name))
     return {"value": site / dt, "unit": "site*RHS/s", "cores": pool.n, "kind": "oracle", "cpu_model": cpu_model(),
             "nproc": os.cpu_count(),
             "sample": "%s, %.1f s wall on %d processes (one per core)" % (what, dt, pool.n)}
@@ -943,7 +972,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="lap16", choices=["lap16", "wilson24", "grad32", "colour", "deflation", "evenodd",
+    ap.add_argument("--workload", default="lap16", choices=["lap16", "wilson24", "clover24", "grad32", "colour", "deflation", "evenodd",
                                                         "multigrid"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--skip-baselines", action="store_true")

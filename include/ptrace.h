@@ -647,6 +647,28 @@ PT_API int pt_clover_blocks_host(const int dims[4], const double *U_host, double
                                  double *blocks_out);
 PT_API int pt_clover_blocks(pt_ctx *ctx, const pt_op *op, double csw, double *blocks_dev);
 
+/* The clover Wilson operator A_c = A_W + C (C as in pt_clover_blocks, Sec. 4.2)
+ * in the batched engine: pt_op_set_clover(op, csw) gives the Wilson operator
+ * op the clover term with coefficient csw (csw = 0 removes it).  It computes
+ * the site blocks 1 + C(x) and their inverses (FP64, on the device), checks
+ * that each is two Hermitian 6 x 6 chiral blocks, and keeps them packed with
+ * the operator (FP64, plus an FP32 copy for the inner solves): about
+ * 1.7 KB + 0.6 KB per even-odd site pair.  From then on pt_apply applies
+ * A_W + C (the term added in FP64), and pt_solve, pt_trace_PAinv and
+ * pt_trace_multi solve with A_c on the even Schur complement
+ * S = A_ee - kappa^2 D_eo A_oo^{-1} D_oe (b'_e = b_e + kappa D_eo A_oo^{-1} b_o,
+ * x_o = A_oo^{-1} (b_o + kappa D_oe x_e)) with the stopping test of the full
+ * system; the engine's even-odd mode is then always on and the link-sharing
+ * groups (rhs_block 8) are not used.  Errors: PT_ERR_ARG if op is not a
+ * Wilson operator or a side of the lattice is odd (the engine also refuses
+ * pt_grad on a clover operator); PT_ERR_NUMERIC if a block 1 + C(x) is
+ * singular or not of the chiral Hermitian form (the operator keeps its
+ * previous term); PT_ERR_OOM.  Synchronises; temporary device buffers of
+ * 2 x 2.3 KB per site while it runs.  The building-block entry points
+ * (pt_eo_*, pt_wmg_solve) take their clover blocks or c_sw explicitly and do
+ * not use the operator's term. */
+PT_API int pt_op_set_clover(pt_op *op, double csw);
+
 /* y[r][x] = beta y[r][x] + B(x) x[r][x] for nrhs spinor fields (user layout,
  * device; x and y must not overlap) and blocks B [N][12][12] (device).  With
  * beta = 1 and y = A_W x (pt_apply) this is the clover operator. */

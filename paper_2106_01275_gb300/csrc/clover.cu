@@ -14,6 +14,7 @@
 // kernels and the host-only entry points (which tests run without a GPU) call
 // the same code.
 #include <algorithm>
+#include <cmath>
 
 #include "hd_complex.cuh"
 #include "pt_common.cuh"
@@ -323,4 +324,149 @@ extern "C" int pt_site_blocks_invert(pt_ctx *c, int N, const double *blocks_dev,
     } while (0);
     cudaFreeAsync(bad, c->stream);
     return rc;
+}
+
+// ---------------------------------------------------------------- clover term of the batched engine
+// 1 + C(x) commutes with g5 = diag(1, 1, -1, -1) (sigma_{mu nu} does) and is
+// Hermitian (sigma_{mu nu} and F_{mu nu} are), so in the chiral basis it is
+// two Hermitian 6 x 6 blocks, components 6q .. 6q + 5 for chirality q; so is
+// its inverse.  Each block is packed as 36 reals: the six real diagonal
+// entries, then the upper entries u_ij (i < j, row-major) as re, im.  Half
+// entry h of parity par is the site 2h + b, b fixing the parity (D_0 even).
+// Arrays, chunk-major by half entry: CL64 double2 [3][36][N/2] (1 + C on
+// the even sites, (1 + C)^{-1} on the odd ones, 1 + C on the odd ones),
+// CL32 float4 [2][18][N/2] (the first two).  bad counts blocks that are not
+// of that form (an entry outside the chiral blocks, or an asymmetry, above
+// 1e-9 of the block's largest entry).
+__global__ void k_clover_pack(CloverGeom g, const double *C, const double *Cinv, double2 *CL64, float4 *CL32,
+                              int *bad) {
+    const int Nh = g.N / 2;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 3 * Nh; t += gridDim.x * blockDim.x) {
+        const int a = t / Nh, h = t - a * Nh;
+        const int par = a == 0 ? 0 : 1;
+        int r = 2 * h, ysum = 0;
+        r /= g.D[0];
+        for (int mu = 1; mu < 4; ++mu) {
+            ysum += r % g.D[mu];
+            r /= g.D[mu];
+        }
+        const int s = 2 * h + ((par ^ ysum) & 1);       // x_0 parity that gives the site parity par
+        const double *M = (a == 1 ? Cinv : C) + (size_t)s * 288;
+        auto ent = [&](int i, int j, double &re, double &im) {
+            re = M[(i * 12 + j) * 2] + (a != 1 && i == j ? 1.0 : 0.0);
+            im = M[(i * 12 + j) * 2 + 1];
+        };
+        double big = 0.0;
+        for (int e = 0; e < 144; ++e) big = fmax(big, fabs(M[2 * e]) + fabs(M[2 * e + 1]));
+        big = fmax(big, 1.0);
+        bool ok = true;
+        double w[72];
+        for (int q = 0; q < 2; ++q) {
+            double *wq = w + 36 * q;
+            int k = 6;
+            for (int i = 0; i < 6; ++i) {
+                double re, im;
+                ent(6 * q + i, 6 * q + i, re, im);
+                wq[i] = re;
+                ok = ok && fabs(im) <= 1e-9 * big;
+                for (int j = 0; j < 6; ++j) {          // the other chirality's columns vanish
+                    double ore, oim;
+                    ent(6 * q + i, 6 * (1 - q) + j, ore, oim);
+                    ok = ok && fabs(ore) + fabs(oim) <= 1e-9 * big;
+                }
+                for (int j = i + 1; j < 6; ++j) {
+                    double ure, uim, lre, lim;
+                    ent(6 * q + i, 6 * q + j, ure, uim);
+                    ent(6 * q + j, 6 * q + i, lre, lim);
+                    ok = ok && fabs(ure - lre) + fabs(uim + lim) <= 1e-9 * big;
+                    wq[k] = ure;
+                    wq[k + 1] = uim;
+                    k += 2;
+                }
+            }
+        }
+        if (!ok) atomicAdd(bad, 1);
+        for (int k = 0; k < 36; ++k) CL64[((size_t)a * 36 + k) * Nh + h] = make_double2(w[2 * k], w[2 * k + 1]);
+        if (a < 2)
+            for (int k = 0; k < 18; ++k)
+                CL32[((size_t)a * 18 + k) * Nh + h] =
+                    make_float4((float)w[4 * k], (float)w[4 * k + 1], (float)w[4 * k + 2], (float)w[4 * k + 3]);
+    }
+}
+
+extern "C" int pt_op_set_clover(pt_op *op, double csw) {
+    PT_CHECK_ARG(op && op->kind == 1, "pt_op_set_clover: a Wilson-Dirac operator is required");
+    PT_CHECK_ARG(std::isfinite(csw), "pt_op_set_clover: c_sw must be finite");
+    pt_ctx *c = op->ctx;
+    PT_CUDA(cudaSetDevice(op->device));
+    if (csw == 0.0) {
+        PT_CUDA(cudaStreamSynchronize(c->stream));
+        cudaFree(op->CL64);
+        cudaFree(op->CL32);
+        op->CL64 = nullptr;
+        op->CL32 = nullptr;
+        op->csw = 0.0;
+        return PT_OK;
+    }
+    for (int mu = 0; mu < 4; ++mu)
+        PT_CHECK_ARG(op->dims[mu] >= 2 && op->dims[mu] % 2 == 0,
+                     "pt_op_set_clover: the clover operator runs on the even-odd engine: every side must be even");
+    CloverGeom g;
+    int rc = clover_geom(op->dims, &g);
+    if (rc) return rc;
+    const size_t Nh = (size_t)g.N / 2, nb = (size_t)g.N * 288 * sizeof(double);
+    double *C = nullptr, *Cinv = nullptr;
+    double2 *CL64 = nullptr;
+    float4 *CL32 = nullptr;
+    int *bad = nullptr;
+    cudaError_t e = cudaMalloc((void **)&C, nb);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&Cinv, nb);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&CL64, Nh * 3 * 36 * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&CL32, Nh * 2 * 18 * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&bad, sizeof(int));
+    auto release = [&](bool keep) {
+        cudaFree(C);
+        cudaFree(Cinv);
+        cudaFree(bad);
+        if (!keep) {
+            cudaFree(CL64);
+            cudaFree(CL32);
+        }
+    };
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        release(false);
+        pt_set_error("pt_op_set_clover: device allocation failed (%s)", cudaGetErrorString(e));
+        return PT_ERR_OOM;
+    }
+    rc = pt_clover_blocks(c, op, csw, C);
+    if (rc == PT_OK) rc = pt_site_blocks_invert(c, g.N, C, 1.0, Cinv);      // synchronises
+    int h_bad = 0;
+    if (rc == PT_OK) {
+        e = cudaMemsetAsync(bad, 0, sizeof(int), c->stream);
+        const int grid = std::max(1, std::min((int)((3 * Nh + 127) / 128), 16 * c->num_sms));
+        if (e == cudaSuccess) {
+            k_clover_pack<<<grid, 128, 0, c->stream>>>(g, C, Cinv, CL64, CL32, bad);
+            ++pt_kernel_launch_count;
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) rc = pt_cuda_fail(e, "k_clover_pack", __FILE__, __LINE__);
+        else if (h_bad) {
+            pt_set_error("pt_op_set_clover: %d site blocks are not Hermitian chiral blocks", h_bad);
+            rc = PT_ERR_NUMERIC;
+        }
+    }
+    if (rc != PT_OK) {
+        release(false);
+        return rc;
+    }
+    release(true);
+    cudaFree(op->CL64);
+    cudaFree(op->CL32);
+    op->CL64 = (double *)CL64;
+    op->CL32 = (float *)CL32;
+    op->csw = csw;
+    return PT_OK;
 }

@@ -4,6 +4,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "pt_common.cuh"
 
 thread_local int64_t pt_kernel_launch_count = 0;
@@ -228,6 +230,7 @@ extern "C" int pt_op_destroy(pt_op *op) {
     if (op->kind == 1) {
         cudaSetDevice(op->device);
         cudaFree(op->U64); cudaFree(op->U32); cudaFree(op->U16);
+        cudaFree(op->CL64); cudaFree(op->CL32);
     }
     free(op);
     return PT_OK;
@@ -338,19 +341,50 @@ template int launch_internal_to_user<float>(pt_ctx *, int, int, int, const float
 template int launch_user_to_internal<__nv_bfloat16>(pt_ctx *, int, int, int, const double *, __nv_bfloat16 *);
 template int launch_internal_to_user<__nv_bfloat16>(pt_ctx *, int, int, int, const __nv_bfloat16 *, double *);
 
+// y += C x for a clover operator (user layout, FP64): C = (1 + C) - 1 with
+// the packed blocks 1 + C (even sites: array 0, odd sites: array 2)
+__global__ void k_clover_add(Geom g, const double2 *CL64, const double *x, double *y, int nrhs) {
+    const int N = g.N;
+    const int64_t total = (int64_t)nrhs * N;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int s = (int)(t % N);
+        int xc[4];
+        site_coords(g, s, xc);
+        const int par = (xc[0] + xc[1] + xc[2] + xc[3]) & 1;
+        const double *xv = x + (size_t)t * 24;
+        double *yv = y + (size_t)t * 24;
+        Cx<double> v[12];
+        for (int c = 0; c < 12; ++c) v[c] = Cx<double>{xv[2 * c], xv[2 * c + 1]};
+        clover_mul(CL64, N / 2, par ? 2 : 0, s >> 1, v);
+        for (int c = 0; c < 12; ++c) {
+            yv[2 * c] += v[c].re - xv[2 * c];
+            yv[2 * c + 1] += v[c].im - xv[2 * c + 1];
+        }
+    }
+}
+
 extern "C" int pt_apply(pt_ctx *c, const pt_op *op, const double *x_dev, double *y_dev, int nrhs, int prec) {
     PT_CHECK_ARG(c && op && op->ctx == c, "pt_apply: bad context/operator");
     PT_CHECK_ARG(nrhs >= 0 && nrhs <= 65535, "pt_apply: nrhs must be in [0, 65535]");
     if (nrhs == 0) return PT_OK;
     PT_CHECK_ARG(x_dev && y_dev && x_dev != y_dev, "pt_apply: NULL or aliased fields");
     PT_CUDA(cudaSetDevice(c->device));
+    int rc;
     switch (prec) {
-        case PT_PREC_FP64: return apply_prec<double, double, double>(op, x_dev, y_dev, nrhs, op->U64);
-        case PT_PREC_MIXED_FP32: return apply_prec<float, float, float>(op, x_dev, y_dev, nrhs, op->U32);
+        case PT_PREC_FP64: rc = apply_prec<double, double, double>(op, x_dev, y_dev, nrhs, op->U64); break;
+        case PT_PREC_MIXED_FP32: rc = apply_prec<float, float, float>(op, x_dev, y_dev, nrhs, op->U32); break;
         case PT_PREC_MIXED_BF16:
-            return apply_prec<float, __nv_bfloat16, __nv_bfloat16>(op, x_dev, y_dev, nrhs, op->U16);
+            rc = apply_prec<float, __nv_bfloat16, __nv_bfloat16>(op, x_dev, y_dev, nrhs, op->U16);
+            break;
         default: PT_CHECK_ARG(false, "pt_apply: unknown precision %d", prec);
     }
+    if (rc != PT_OK || op->csw == 0.0) return rc;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)nrhs * op->g.N + 127) / 128,
+                                                                  16 * c->num_sms));
+    k_clover_add<<<grid, 128, 0, c->stream>>>(op->g, (const double2 *)op->CL64, x_dev, y_dev, nrhs);
+    ++pt_kernel_launch_count;
+    PT_CUDA(cudaGetLastError());
+    return PT_OK;
 }
 
 // ------------------------------------------------------------------ probes

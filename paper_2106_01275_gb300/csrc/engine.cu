@@ -71,6 +71,9 @@ struct EP {
     int antip;
     const void *U;             // links in the inner precision
     const double *U64;         // links in FP64
+    int clover;                // even-odd Wilson with a clover term: the packed chiral blocks below
+    const float4 *CL32;        // 1 + C (even), (1 + C)^{-1} (odd) for FP32 / BF16 inner storage
+    const double2 *CL64;       // the same in FP64 (and 1 + C on the odd sites)
     int mode;
     const int32_t *col;
     uint64_t seed;
@@ -1643,6 +1646,11 @@ __global__ void k_links_eo(Geom g, int n_chunk, const E *__restrict__ src, E *__
 // ||b - A x|| / ||b|| with |b|^2 over both parities (r_o = 0 once x_o is
 // rebuilt).  The contraction and the copy-out read x_o = b_o + kappa t64,
 // t64 = D_oe x64 of the final x64, where they read an odd site.
+// With a clover term (A = A_W + C, diagonal blocks A_ee = 1 + C_ee and
+// A_oo = 1 + C_oo) the same kernels form S = A_ee - kappa^2 D_eo A_oo^{-1}
+// D_oe, b'_e = b_e + kappa D_eo A_oo^{-1} b_o and x_o = A_oo^{-1} (b_o +
+// kappa D_oe x_e): the odd-site hops apply A_oo^{-1} before they store, the
+// even-site applies A_ee to their own entry.
 
 // One hop of the Wilson hopping term into acc at site idx (coordinates x):
 // forward (1 - g_mu) U_mu(x) psi(x + mu) or backward (1 + g_mu)
@@ -1754,9 +1762,17 @@ __device__ __forceinline__ bool source_may_be_nonzero(const EP &P, const Task &t
     return P.col[(size_t)tk.cidx * P.g.N + y] == tk.colour;
 }
 
-// h = D_oe p at the odd entries (WHICH 0: p = pv, the first apply; 1: p = s)
-template <typename S, typename LS, int WHICH>
-__global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 : PT_WIL_MINB) k_weo_hop(EP P) {
+// resident CTAs per SM the even-odd Wilson item kernels are compiled for
+// (FP64 storage and the clover variants need more registers per thread)
+template <typename S>
+constexpr int weo_minb(int clv) {
+    return std::is_same<S, double>::value ? (clv ? 1 : 2) : (clv ? 2 : PT_WIL_MINB);
+}
+
+// h = D_oe p at the odd entries (WHICH 0: p = pv, the first apply; 1: p = s);
+// with the clover term (CLV) h = A_oo^{-1} D_oe p
+template <typename S, typename LS, int WHICH, int CLV = 0>
+__global__ void __launch_bounds__(PT_BLOCK, weo_minb<S>(CLV)) k_weo_hop(EP P) {
     typedef typename ArithT<S>::T R;
     const int N = P.nsite;
     ITEM_LOOP(LIST_INNER)
@@ -1772,15 +1788,22 @@ __global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 :
                 P.g, [&](int y, int, int, Cx<R> ps[4][3]) { load_spinor<S, R>(src, N, y >> 1, ps); },
                 (const LS *)P.U, P.antip, s, xc, acc);
 #pragma unroll
-            for (int c = 0; c < 12; ++c) o[c] = Cx<R>{rnd<S, R>(acc[c / 3][c % 3].re), rnd<S, R>(acc[c / 3][c % 3].im)};
+            for (int c = 0; c < 12; ++c) o[c] = acc[c / 3][c % 3];
+            if constexpr (CLV) {
+                if constexpr (std::is_same<S, double>::value) clover_mul(P.CL64, N, 1, idx, o);
+                else clover_mul(P.CL32, N, 1, idx, o);
+            }
+#pragma unroll
+            for (int c = 0; c < 12; ++c) o[c] = Cx<R>{rnd<S, R>(o[c].re), rnd<S, R>(o[c].im)};
             store_spinor<S, R>(h, N, idx, o);
         SITE_LOOP_END
     ITEM_LOOP_END
 }
 
-// v = S p = p - kappa^2 D_eo h at the even entries;  partial (r0, v)
-template <typename S, typename LS>
-__global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 : PT_WIL_MINB) k_weo_apply1(EP P) {
+// v = S p = p - kappa^2 D_eo h at the even entries (clover: A_ee p - ...);
+// partial (r0, v)
+template <typename S, typename LS, int CLV = 0>
+__global__ void __launch_bounds__(PT_BLOCK, weo_minb<S>(CLV)) k_weo_apply1(EP P) {
     typedef typename ArithT<S>::T R;
     __shared__ double sh[32 * 2];
     const int N = P.nsite;
@@ -1801,6 +1824,15 @@ __global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 :
                 P.g, [&](int y, int, int, Cx<R> f[4][3]) { load_spinor<S, R>(h, N, y >> 1, f); },
                 (const LS *)P.U, P.antip, s, xc, acc);
             load_spinor<S, R>(pv, N, idx, ps);
+            if constexpr (CLV) {
+                Cx<R> v[12];
+#pragma unroll
+                for (int c = 0; c < 12; ++c) v[c] = ps[c / 3][c % 3];
+                if constexpr (std::is_same<S, double>::value) clover_mul(P.CL64, N, 0, idx, v);
+                else clover_mul(P.CL32, N, 0, idx, v);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) ps[c / 3][c % 3] = v[c];
+            }
             load_spinor<S, R>(r0, N, idx, z);
 #pragma unroll
             for (int c = 0; c < 12; ++c) {
@@ -1816,9 +1848,10 @@ __global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 :
     ITEM_LOOP_END
 }
 
-// t = S s = s - kappa^2 D_eo h at the even entries;  partials (t, s), |t|^2
-template <typename S, typename LS>
-__global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 : PT_WIL_MINB) k_weo_apply2(EP P) {
+// t = S s = s - kappa^2 D_eo h at the even entries (clover: A_ee s - ...);
+// partials (t, s), |t|^2
+template <typename S, typename LS, int CLV = 0>
+__global__ void __launch_bounds__(PT_BLOCK, weo_minb<S>(CLV)) k_weo_apply2(EP P) {
     typedef typename ArithT<S>::T R;
     __shared__ double sh[32 * 3];
     const int N = P.nsite;
@@ -1837,13 +1870,32 @@ __global__ void __launch_bounds__(PT_BLOCK, std::is_same<S, double>::value ? 2 :
             wilson_hop_fetch<R, LS, 0>(
                 P.g, [&](int y, int, int, Cx<R> f[4][3]) { load_spinor<S, R>(h, N, y >> 1, f); },
                 (const LS *)P.U, P.antip, s, xc, acc);
-            load_spinor<S, R>(sv, N, idx, sp);
+            if constexpr (CLV) {
+                Cx<R> v[12];
+                {
+                    Cx<R> f[4][3];
+                    load_spinor<S, R>(sv, N, idx, f);
 #pragma unroll
-            for (int c = 0; c < 12; ++c) {
-                const Cx<R> w = csub(sp[c / 3][c % 3], cscale(acc[c / 3][c % 3], k2));
-                av[c] = Cx<R>{rnd<S, R>(w.re), rnd<S, R>(w.im)};
+                    for (int c = 0; c < 12; ++c) v[c] = f[c / 3][c % 3];
+                }
+                if constexpr (std::is_same<S, double>::value) clover_mul(P.CL64, N, 0, idx, v);
+                else clover_mul(P.CL32, N, 0, idx, v);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) {
+                    const Cx<R> w = csub(v[c], cscale(acc[c / 3][c % 3], k2));
+                    av[c] = Cx<R>{rnd<S, R>(w.re), rnd<S, R>(w.im)};
+                }
+                store_spinor<S, R>(t, N, idx, av);
+                load_spinor<S, R>(sv, N, idx, sp);           // s itself, for the dot products
+            } else {
+                load_spinor<S, R>(sv, N, idx, sp);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) {
+                    const Cx<R> w = csub(sp[c / 3][c % 3], cscale(acc[c / 3][c % 3], k2));
+                    av[c] = Cx<R>{rnd<S, R>(w.re), rnd<S, R>(w.im)};
+                }
+                store_spinor<S, R>(t, N, idx, av);
             }
-            store_spinor<S, R>(t, N, idx, av);
 #pragma unroll
             for (int c = 0; c < 12; ++c) {
                 const Cx<R> tv = av[c], sc = sp[c / 3][c % 3];
@@ -1880,6 +1932,7 @@ __global__ void __launch_bounds__(PT_BLOCK) k_weo_outer_hop(EP P) {
                     P.U64, P.antip, s, xc, acc);
 #pragma unroll
                 for (int c = 0; c < 12; ++c) o[c] = acc[c / 3][c % 3];
+                if (P.clover) clover_mul(P.CL64, N, 1, idx, o);      // t64 = A_oo^{-1} D_oe x64
             }
             store_spinor<double, double>(t, N, idx, o);
         SITE_LOOP_END
@@ -1916,8 +1969,17 @@ __global__ void __launch_bounds__(PT_BLOCK) k_weo_outer_bprime(EP P) {
                     int y4[4];
                     nb_coords(P.g, xc, mu, dir, y4);
                     Cx<double> f[4][3];
+                    if (P.clover) {                           // A_oo^{-1} b_o at the neighbour
+                        Cx<double> v[12];
 #pragma unroll
-                    for (int c = 0; c < 12; ++c) f[c / 3][c % 3] = source_val<1>(P, tk, key, y, y4, c);
+                        for (int c = 0; c < 12; ++c) v[c] = source_val<1>(P, tk, key, y, y4, c);
+                        clover_mul(P.CL64, N, 1, y >> 1, v);
+#pragma unroll
+                        for (int c = 0; c < 12; ++c) f[c / 3][c % 3] = v[c];
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 12; ++c) f[c / 3][c % 3] = source_val<1>(P, tk, key, y, y4, c);
+                    }
                     wilson_hop_dir<double, double>(P.g, P.U64, P.antip, s, xc, mu, dir > 0, f, acc);
                 }
 #pragma unroll
@@ -1972,12 +2034,23 @@ __global__ void __launch_bounds__(PT_BLOCK) k_weo_outer_residual(EP P) {
                 wilson_hop_fetch<double, double>(
                     P.g, [&](int y, int, int, Cx<double> f[4][3]) { load_spinor<double, double>(t, N, y >> 1, f); },
                     P.U64, P.antip, s, xc, acc);
-                // r = b' - x + kappa^2 D_eo t64, component by component
+                if (P.clover) {
+                    // r = b' - A_ee x + kappa^2 D_eo t64
+                    Cx<double> xv[12];
 #pragma unroll
-                for (int c = 0; c < 12; ++c) {
-                    const Cx<double> bc = ld_cx<double, double>(bp, N, c, idx);
-                    const Cx<double> xcc = ld_cx<double, double>(x, N, c, idx);
-                    rv[c] = csub(bc, csub(xcc, cscale(acc[c / 3][c % 3], k2)));
+                    for (int c = 0; c < 12; ++c) xv[c] = ld_cx<double, double>(x, N, c, idx);
+                    clover_mul(P.CL64, N, 0, idx, xv);
+#pragma unroll
+                    for (int c = 0; c < 12; ++c)
+                        rv[c] = csub(ld_cx<double, double>(bp, N, c, idx), csub(xv[c], cscale(acc[c / 3][c % 3], k2)));
+                } else {
+                    // r = b' - x + kappa^2 D_eo t64, component by component
+#pragma unroll
+                    for (int c = 0; c < 12; ++c) {
+                        const Cx<double> bc = ld_cx<double, double>(bp, N, c, idx);
+                        const Cx<double> xcc = ld_cx<double, double>(x, N, c, idx);
+                        rv[c] = csub(bc, csub(xcc, cscale(acc[c / 3][c % 3], k2)));
+                    }
                 }
             }
             Cx<R> rs[12];
@@ -2002,7 +2075,8 @@ __global__ void __launch_bounds__(PT_BLOCK) k_weo_outer_residual(EP P) {
 // x at storage site y (coordinates xy), all 12 components: its even entry,
 // or on an odd site x_o = b_o + kappa D_oe x_e from the source and
 // t64 = D_oe x_e, which the outer step formed for the final x_e (zero for a
-// task that converged at its first step, where x = 0)
+// task that converged at its first step, where x = 0); with the clover term
+// x_o = A_oo^{-1} b_o + kappa t64, t64 = A_oo^{-1} D_oe x_e
 __device__ __forceinline__ void weo_x_at(const EP &P, const Task &tk, uint64_t key, const double *x,
                                          const double *t64, int y, const int xy[4], Cx<double> out[12]) {
     const int N = P.nsite;
@@ -2014,8 +2088,12 @@ __device__ __forceinline__ void weo_x_at(const EP &P, const Task &tk, uint64_t k
         return;
     }
     load_spinor<double, double>(t64, N, y >> 1, f);
+    Cx<double> bo[12];
 #pragma unroll
-    for (int c = 0; c < 12; ++c) out[c] = cadd(source_val<1>(P, tk, key, y, xy, c), cscale(f[c / 3][c % 3], P.kappa));
+    for (int c = 0; c < 12; ++c) bo[c] = source_val<1>(P, tk, key, y, xy, c);
+    if (P.clover && source_may_be_nonzero(P, tk, y)) clover_mul(P.CL64, N, 1, y >> 1, bo);   // A_oo^{-1} b_o
+#pragma unroll
+    for (int c = 0; c < 12; ++c) out[c] = cadd(bo[c], cscale(f[c / 3][c % 3], P.kappa));
 }
 
 // the contraction (trace mode) or the copy-out (solve mode) for even-odd
@@ -2427,6 +2505,9 @@ static void enqueue_iteration(const EngineRun &E, cudaStream_t st, const cudaEve
         if (P.rhs_block == WEO_G) {
             k_weo_hop_g<S, LS, 0><<<E.g_hop_g, PT_BLOCK, 0, st>>>(P);
             k_weo_apply1_g<S, LS><<<E.g_apply1_g, PT_BLOCK, 0, st>>>(P);
+        } else if (P.clover) {
+            k_weo_hop<S, LS, 0, 1><<<E.g_hop, P.bs, 0, st>>>(P);
+            k_weo_apply1<S, LS, 1><<<E.g_apply1, P.bs, 0, st>>>(P);
         } else {
             k_weo_hop<S, LS, 0><<<E.g_hop, P.bs, 0, st>>>(P);
             k_weo_apply1<S, LS><<<E.g_apply1, P.bs, 0, st>>>(P);
@@ -2438,6 +2519,9 @@ static void enqueue_iteration(const EngineRun &E, cudaStream_t st, const cudaEve
         if (P.rhs_block == WEO_G) {
             k_weo_hop_g<S, LS, 1><<<E.g_hop_g, PT_BLOCK, 0, st>>>(P);
             k_weo_apply2_g<S, LS><<<E.g_apply2_g, PT_BLOCK, 0, st>>>(P);
+        } else if (P.clover) {
+            k_weo_hop<S, LS, 1, 1><<<E.g_hop, P.bs, 0, st>>>(P);
+            k_weo_apply2<S, LS, 1><<<E.g_apply2, P.bs, 0, st>>>(P);
         } else {
             k_weo_hop<S, LS, 1><<<E.g_hop, P.bs, 0, st>>>(P);
             k_weo_apply2<S, LS><<<E.g_apply2, P.bs, 0, st>>>(P);
@@ -2552,7 +2636,12 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     const pt_ctx::Tune tn = engine_tuning(c, op, rq.prec);
     // even-odd (every side even) unless switched off; the gradient works on
     // full-lattice solutions and keeps the full system
-    const bool eo = tn.evenodd && rq.mode != MODE_GRAD && pt_evenodd_ok(op->dims);
+    const bool clv = KIND == 1 && op->csw != 0.0;
+    const bool eo = (tn.evenodd || clv) && rq.mode != MODE_GRAD && pt_evenodd_ok(op->dims);
+    if (clv && !eo) {
+        pt_set_error("the clover operator runs on the even-odd engine only (every side even; no gradient)");
+        return PT_ERR_ARG;
+    }
     const int nsite = eo ? g.N / 2 : g.N;
     const int64_t L = eo ? (int64_t)nsite * (KIND ? 24 : 1) : pt_field_reals(op);
     // inner vectors: CG e, r, p (two buffers), q (+ t on the odd sites); BiCGStab
@@ -2618,7 +2707,7 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
     // shared memory) in even-odd mode with 256-thread CTAs
     P.rhs_block = 1;
     if (KIND == 1 && !eo && !std::is_same<S, double>::value && tn.rhs_block == 2) P.rhs_block = 2;
-    if (KIND == 1 && eo && tn.rhs_block == WEO_G && bs == PT_BLOCK) P.rhs_block = WEO_G;
+    if (KIND == 1 && eo && tn.rhs_block == WEO_G && bs == PT_BLOCK && !clv) P.rhs_block = WEO_G;
     P.overlap = tn.overlap ? 1 : 0;
     // four sites (even-odd: four half entries of one x row) per thread
     P.vec4 = (KIND == 0 && g.D[0] % (eo ? 8 : 4) == 0) ? 1 : 0;
@@ -2631,6 +2720,9 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
               : std::is_same<S, float>::value ? (const void *)op->U32 : (const void *)op->U16;
     }
     P.U64 = op->U64;
+    P.clover = clv ? 1 : 0;
+    P.CL32 = (const float4 *)op->CL32;
+    P.CL64 = (const double2 *)op->CL64;
     P.mode = rq.mode;
     P.col = rq.col;
     P.seed = rq.seed;
@@ -2734,9 +2826,11 @@ static int run_engine_t(const pt_op *op, EngineRequest &rq, pt_stats *stats) {
         E.g_ores = persistent_grid(k_weo_outer_residual<S>, ns, bs);
         E.g_ohop = persistent_grid(k_weo_outer_hop, ns, bs);
         E.g_obp = persistent_grid(k_weo_outer_bprime, ns, bs);
-        E.g_hop = persistent_grid(k_weo_hop<S, LS, 0>, ns, bs);
-        E.g_apply1 = persistent_grid(k_weo_apply1<S, LS>, ns, bs);
-        E.g_apply2 = persistent_grid(k_weo_apply2<S, LS>, ns, bs);
+        E.g_hop = clv ? persistent_grid(k_weo_hop<S, LS, 0, 1>, ns, bs) : persistent_grid(k_weo_hop<S, LS, 0>, ns, bs);
+        E.g_apply1 = clv ? persistent_grid(k_weo_apply1<S, LS, 1>, ns, bs)
+                         : persistent_grid(k_weo_apply1<S, LS>, ns, bs);
+        E.g_apply2 = clv ? persistent_grid(k_weo_apply2<S, LS, 1>, ns, bs)
+                         : persistent_grid(k_weo_apply2<S, LS>, ns, bs);
         E.g_apply1_x2 = E.g_apply2_x2 = 0;
         E.g_hop_g = persistent_grid(k_weo_hop_g<S, LS, 0>, ns, PT_BLOCK);
         E.g_apply1_g = persistent_grid(k_weo_apply1_g<S, LS>, ns, PT_BLOCK);
@@ -3439,9 +3533,9 @@ extern "C" int pt_autotune(pt_ctx *c, const pt_op *op, const int32_t *col_dev, i
     if (op->kind == 1) groups = {1, 2, 4, 8, 16};
     const std::vector<int> iters = {4, 8, 16};
     std::vector<int> blocks;
-    if (op->kind == 1 && prec != PT_PREC_FP64) blocks = {1, 2, WEO_G};
+    if (op->kind == 1 && prec != PT_PREC_FP64 && op->csw == 0.0) blocks = {1, 2, WEO_G};
     std::vector<int> evenodds;
-    if (pt_evenodd_ok(op->dims)) evenodds = {0, 1};
+    if (pt_evenodd_ok(op->dims) && op->csw == 0.0) evenodds = {0, 1};     // the clover operator: even-odd only
     // item shape: CTA threads, and (Laplacian) sites per thread
     const std::vector<int> ctas = {64, 128, 256};
     std::vector<int> spts;

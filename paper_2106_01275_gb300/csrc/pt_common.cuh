@@ -328,6 +328,64 @@ __device__ __forceinline__ void load_link(const LS *U, int N, int mu, int idx, C
     }
 }
 
+// ------------------------------------------------------------------ clover blocks
+// The clover operator's site blocks 1 + C(x) and their inverses are, in the
+// chiral basis, two Hermitian 6 x 6 blocks (components 6q .. 6q + 5 for
+// chirality q; pt_op_set_clover packs them).  A block is 36 reals w: the six
+// real diagonal entries, then the upper entries u_ij (i < j, row-major) as
+// re, im; the lower entries are conj(u_ij).  v <- B v:
+template <typename R>
+__device__ __forceinline__ void herm6_mul(const R w[36], Cx<R> v[6]) {
+    Cx<R> o[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) o[i] = cscale(v[i], w[i]);
+    int k = 6;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = i + 1; j < 6; ++j) {
+            const Cx<R> u = Cx<R>{w[k], w[k + 1]};
+            k += 2;
+            o[i] = cadd(o[i], cmul(u, v[j]));
+            o[j] = cadd(o[j], cconjmul(u, v[i]));
+        }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) v[i] = o[i];
+}
+
+// v <- B v for the blocks of half entry h (Nh entries) in block array
+// `which` of a packed clover array: FP32 chunks [which][18][Nh] float4, FP64
+// [which][36][Nh] double2 (which 0: 1 + C on the even sites, 1: (1 + C)^{-1}
+// on the odd ones, 2 (FP64 only): 1 + C on the odd ones)
+__device__ __forceinline__ void clover_mul(const float4 *cl, int Nh, int which, int h, Cx<float> v[12]) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        float w[36];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float4 c = cl[((size_t)which * 18 + q * 9 + k) * Nh + h];
+            w[4 * k] = c.x;
+            w[4 * k + 1] = c.y;
+            w[4 * k + 2] = c.z;
+            w[4 * k + 3] = c.w;
+        }
+        herm6_mul<float>(w, v + 6 * q);
+    }
+}
+__device__ __forceinline__ void clover_mul(const double2 *cl, int Nh, int which, int h, Cx<double> v[12]) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        double w[36];
+#pragma unroll
+        for (int k = 0; k < 18; ++k) {
+            const double2 c = cl[((size_t)which * 36 + q * 18 + k) * Nh + h];
+            w[2 * k] = c.x;
+            w[2 * k + 1] = c.y;
+        }
+        herm6_mul<double>(w, v + 6 * q);
+    }
+}
+
 // (H psi)(x) for one site; psi is read through ld_cx from field f (N sites).
 // Returns acc = H psi at x.
 template <typename R, typename S, typename LS>
@@ -523,6 +581,12 @@ struct pt_op {
     double *U64;             // packed links complex [4][9][N], FP64
     float *U32;              // same, FP32
     __nv_bfloat16 *U16;      // same, BF16
+    // clover term (pt_op_set_clover; Wilson, every side even): c_sw (0: none)
+    // and the chiral 6 x 6 blocks of 1 + C per half-field entry, packed as 36
+    // reals per chirality (clover_mul in engine.cu reads them):
+    double csw;
+    double *CL64;            // [3][36][N/2] double2: 1 + C even, (1 + C)^{-1} odd, 1 + C odd
+    float *CL32;             // [2][18][N/2] float4: 1 + C even, (1 + C)^{-1} odd
 };
 
 // work-space helper: returns a device pointer of at least `bytes` (grow-only)

@@ -80,6 +80,7 @@ _SIGS = {
     "pt_op_laplacian": ([_P, ctypes.POINTER(_I), _D, ctypes.POINTER(_P)], _I),
     "pt_op_wilson": ([_P, ctypes.POINTER(_I), _P, _D, _I, ctypes.POINTER(_P)], _I),
     "pt_op_dof": ([_P], _I),
+    "pt_op_set_clover": ([_P, _D], _I),
     "pt_op_destroy": ([_P], _I),
     "pt_apply": ([_P, _P, _P, _P, _I, _I], _I),
     "pt_stencil": ([_I, ctypes.POINTER(_I), _I, _I, ctypes.POINTER(_I), _I, ctypes.POINTER(_I)], _I),
@@ -310,6 +311,15 @@ def wilson(ctx, dims, U, kappa, antiperiodic_t=True):
     op = Operator(ctx, h, dims, 12)
     op.kappa = float(kappa)
     ctx.synchronize()
+    return op
+
+
+def set_clover(op, csw):
+    """Give the Wilson operator op the clover term with coefficient csw (0
+    removes it): pt_apply then applies A_W + C and the batched solves and
+    traces use the clover operator on the even Schur complement."""
+    _check(lib().pt_op_set_clover(op._h, float(csw)))
+    op.csw = float(csw)
     return op
 
 
