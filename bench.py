@@ -960,8 +960,10 @@ def run_reference(args):
            "config": {"workload": W.desc + " (CPU oracle on a bounded sample per step)", "lattice": W.dims},
            "cpu_baseline": {"value": value, "unit": "site*RHS/s", "cores": pool.n, "kind": "oracle",
                             "cpu_model": cpu_model(), "nproc": os.cpu_count(),
-                            "sample": "%d RHS over %d steps of %.1f s on %d processes (one per core)"
-                                      % (n_rhs, args.steps, per_step, pool.n)},
+                            "sample": ("%d %s over %d steps of %.1f s on %d processes (one per core)"
+                                       % (n_rhs, "RHS solved and contracted" if W.kind == "lap" else
+                                          "FP64 %s operator applications" % ("clover Wilson" if W.csw else "Wilson"),
+                                          args.steps, per_step, pool.n))},
            "e2e": {"value": value, "unit": "site*RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

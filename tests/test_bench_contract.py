@@ -239,3 +239,18 @@ def test_multigrid_leg_json_line(monkeypatch, capsys):
             assert c["iters_plain"] is None and c["iters_evenodd_bicgstab"] > 0, c
         else:
             assert c["iters_multigrid"] < c["iters_plain"], c
+
+
+def test_reference_arm_clover_workload():
+    """The reference arm of the clover workload times the oracle's clover
+    Wilson operator (small case)."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "clover24", "--case", "small", "--steps", "1", "--warmup", "3", "--cpu-seconds", "1"],
+                       capture_output=True, text=True, timeout=900, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.strip().splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0
+    assert d["config"]["workload"].startswith("clover24") and "c_sw=1.0" in d["config"]["workload"]
+    assert "clover Wilson" in d["cpu_baseline"]["sample"]
