@@ -1762,11 +1762,12 @@ __device__ __forceinline__ bool source_may_be_nonzero(const EP &P, const Task &t
     return P.col[(size_t)tk.cidx * P.g.N + y] == tk.colour;
 }
 
-// resident CTAs per SM the even-odd Wilson item kernels are compiled for
-// (FP64 storage and the clover variants need more registers per thread)
+// resident CTAs per SM the even-odd Wilson item kernels are compiled for:
+// clv 0 plain, 1 a clover variant that fits the plain budget, 2 one that
+// needs more registers per thread (FP64 storage: every clover variant)
 template <typename S>
 constexpr int weo_minb(int clv) {
-    return std::is_same<S, double>::value ? (clv ? 1 : 2) : (clv ? 2 : PT_WIL_MINB);
+    return std::is_same<S, double>::value ? (clv ? 1 : 2) : (clv == 2 ? 2 : PT_WIL_MINB);
 }
 
 // h = D_oe p at the odd entries (WHICH 0: p = pv, the first apply; 1: p = s);
@@ -1851,7 +1852,7 @@ __global__ void __launch_bounds__(PT_BLOCK, weo_minb<S>(CLV)) k_weo_apply1(EP P)
 // t = S s = s - kappa^2 D_eo h at the even entries (clover: A_ee s - ...);
 // partials (t, s), |t|^2
 template <typename S, typename LS, int CLV = 0>
-__global__ void __launch_bounds__(PT_BLOCK, weo_minb<S>(CLV)) k_weo_apply2(EP P) {
+__global__ void __launch_bounds__(PT_BLOCK, weo_minb<S>(2 * CLV)) k_weo_apply2(EP P) {
     typedef typename ArithT<S>::T R;
     __shared__ double sh[32 * 3];
     const int N = P.nsite;
